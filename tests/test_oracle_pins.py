@@ -1,0 +1,467 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them compares the oracle with
+itself: they use closed forms, textbook special cases (HLLC for B = 0),
+invariants of the exact equations (conservation, div B, symmetry), exact
+discrete solutions (stationary contact / rotational discontinuity) and the
+convergence order the paper reports.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_05240_gb300 import inputs as I
+
+G = 5.0 / 3.0
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_state(rng, bn_scale=1.0):
+    return np.array([rng.uniform(0.5, 2.0), rng.normal(), rng.normal(), rng.normal(),
+                     rng.uniform(0.3, 2.0), rng.normal(), rng.normal()]), bn_scale * rng.normal()
+
+
+# ------------------------------------------------------------ primitives --
+def test_primitive_roundtrip():
+    """Sec. 2.1: U <-> W with E = P/(gamma-1) + rho v^2/2 + B^2/2, B_cc = face mean."""
+    box = I.Box(6, 5, 4)
+    rng = np.random.default_rng(1)
+    rho = rng.uniform(0.5, 2, box.shape)
+    vel = [rng.normal(size=box.shape) for _ in range(3)]
+    p = rng.uniform(0.2, 3, box.shape)
+    bf = [rng.normal(size=box.shape) for _ in range(3)]
+    U = I.assemble(box, rho, vel, p, bf)
+    W = O.Oracle(6, 5, 4).primitives(U)
+    np.testing.assert_allclose(W[0], rho, rtol=1e-15)
+    for a in range(3):
+        np.testing.assert_allclose(W[1 + a], vel[a], rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(W[4], p, rtol=1e-13)
+    np.testing.assert_allclose(W[5], 0.5 * (bf[0] + np.roll(bf[0], 1, axis=2)), rtol=1e-15)
+    np.testing.assert_allclose(W[6], 0.5 * (bf[1] + np.roll(bf[1], 1, axis=1)), rtol=1e-15)
+    np.testing.assert_allclose(W[7], 0.5 * (bf[2] + np.roll(bf[2], 1, axis=0)), rtol=1e-15)
+
+
+# ------------------------------------------------------------- wave speeds --
+def test_wave_speeds_linear_wave_background():
+    """Sec. 3.1.1 background with the Sec. 2.2.1 c_{f,s} formula: c_f = 2, c_s = 0.5, c_a = 1."""
+    g = json.load(open(os.path.join(GOLD, "linear_wave_background.json")))
+    w = np.array([g["rho"], 0, 0, 0, g["P"], g["B"][1], g["B"][2]])
+    lam, R, L = O.eigen(g["gamma"], w, g["B"][0])
+    np.testing.assert_allclose(lam, [-g["c_fast_x"], -g["c_alfven_x"], -g["c_slow_x"], 0,
+                                     g["c_slow_x"], g["c_alfven_x"], g["c_fast_x"]], atol=1e-14)
+    cf = O.fast_speed(g["gamma"], g["rho"], g["P"], g["B"][0], g["B"][1], g["B"][2])
+    assert abs(cf - g["c_fast_x"]) < 1e-14
+
+
+def test_dt_closed_form():
+    """Step 1 (Eq. dt): the config-0 background, evaluated with the paper's printed c_f form."""
+    g = json.load(open(os.path.join(GOLD, "config0_dt.json")))
+    n, gam, B = g["n"], g["gamma"], g["B"]
+    box = I.Box(n, n, n)
+    U = I.uniform(box, g["rho"], (0, 0, 0), 1.0 / gam, B, gam)
+    gp = 1.0  # gamma P with P = 1/gamma
+    b2 = sum(b * b for b in B)
+    best = min((1.0 / n) / math.sqrt((gp + b2 + math.sqrt((gp + b2) ** 2 - 4 * gp * bl * bl)) / 2.0) for bl in B)
+    dt = O.Oracle(n, n, n, gamma=gam).dt(U, g["cfl"])
+    assert abs(dt - g["cfl"] * best) <= 1e-15 * dt
+    # moving gas: |v_l| adds to the signal speed in direction l only
+    U2 = I.uniform(box, 1.0, (0.0, 0.0, 3.0), 1.0 / gam, B, gam)
+    dt2 = O.Oracle(n, n, n, gamma=gam).dt(U2, g["cfl"])
+    cz = math.sqrt((gp + b2 + math.sqrt((gp + b2) ** 2 - 4 * gp * B[2] ** 2)) / 2.0)
+    assert abs(dt2 - g["cfl"] * (1.0 / n) / (3.0 + cz)) <= 1e-15 * dt2
+
+
+# --------------------------------------------------------------------- HLLD --
+def physical_flux(w, bn, gamma=G):
+    """F_x of Sec. 2.1 (paper's flux vector) for primitive w = (rho,u,v,w,P,By,Bz)."""
+    rho, u, v, ww, p, by, bz = w
+    b2 = bn * bn + by * by + bz * bz
+    E = p / (gamma - 1) + 0.5 * rho * (u * u + v * v + ww * ww) + 0.5 * b2
+    pt = p + 0.5 * b2
+    return np.array([rho * u, rho * u * u + pt - bn * bn, rho * u * v - bn * by, rho * u * ww - bn * bz,
+                     u * (E + pt) - bn * (u * bn + v * by + ww * bz), by * u - bn * v, bz * u - bn * ww])
+
+
+def cons(w, bn, gamma=G):
+    rho, u, v, ww, p, by, bz = w
+    E = p / (gamma - 1) + 0.5 * rho * (u * u + v * v + ww * ww) + 0.5 * (bn * bn + by * by + bz * bz)
+    return np.array([rho, rho * u, rho * v, rho * ww, E, by, bz])
+
+
+def test_hlld_consistency():
+    """HLLD(W, W) = F(W) (Sec. 2.1 flux vector)."""
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        w, bn = rand_state(rng)
+        np.testing.assert_allclose(O.hlld(G, w, w, bn), physical_flux(w, bn), rtol=1e-14, atol=1e-14)
+
+
+def test_hlld_supersonic_upwind():
+    """S_L >= 0 selects F_L and S_R <= 0 selects F_R exactly."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        wl, bn = rand_state(rng)
+        wr, _ = rand_state(rng)
+        wl[1] = wr[1] = 30.0
+        assert np.array_equal(O.hlld(G, wl, wr, bn), physical_flux(wl, bn))
+        wl[1] = wr[1] = -30.0
+        assert np.array_equal(O.hlld(G, wl, wr, bn), physical_flux(wr, bn))
+
+
+def test_hlld_integral_consistency_and_star_invariants():
+    """Miyoshi & Kusano's construction: the intermediate states integrate to the
+    HLL average, S_R U_R - S_L U_L - (F_R - F_L); the normal velocity is S_M in
+    every intermediate state; rho** = rho*; B** and v_t** are shared."""
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        wl, bn = rand_state(rng)
+        wr, _ = rand_state(rng)
+        f, sp, st, fl, star = O.hlld_detail(G, wl, wr, bn)
+        if not star:
+            continue
+        SL, SsL, SM, SsR, SR = sp
+        UL, UsL, UssL, UssR, UsR, UR = st
+        lhs = (SsL - SL) * UsL + (SM - SsL) * UssL + (SsR - SM) * UssR + (SR - SsR) * UsR
+        rhs = SR * UR - SL * UL - (fl[1] - fl[0])
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12 * np.max(np.abs(rhs)))
+        for U in (UsL, UssL, UssR, UsR):
+            assert abs(U[1] / U[0] - SM) < 1e-12 * (1 + abs(SM))
+        assert UssL[0] == UsL[0] and UssR[0] == UsR[0]
+        np.testing.assert_allclose(UssL[5:], UssR[5:], rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(UssL[2:4] / UssL[0], UssR[2:4] / UssR[0], rtol=1e-13, atol=1e-13)
+        # Rankine-Hugoniot across the Alfven waves S*_L, S*_R (jump of the flux)
+        FsL = fl[0] + SL * (UsL - UL)
+        FssL = FsL + SsL * (UssL - UsL)
+        FsR = fl[1] + SR * (UsR - UR)
+        FssR = FsR + SsR * (UssR - UsR)
+        # the two routes to the contact flux agree: F**_L - F**_R = S_M (U**_L - U**_R)
+        np.testing.assert_allclose(FssL - FssR, SM * (UssL - UssR), rtol=1e-11,
+                                   atol=1e-11 * (1 + np.max(np.abs(FssL))))
+
+
+def hllc_toro(wl, wr, gamma=G):
+    """Textbook HLLC flux for the Euler equations (Toro, Riemann Solvers, Sec. 10.4),
+    with the same outer speed estimates; B = 0 reduces HLLD to this solver."""
+    def sound(w):
+        return math.sqrt(gamma * w[4] / w[0])
+    SL = min(wl[1], wr[1]) - max(sound(wl), sound(wr))
+    SR = max(wl[1], wr[1]) + max(sound(wl), sound(wr))
+    FL, FR = physical_flux(wl, 0.0), physical_flux(wr, 0.0)
+    UL, UR = cons(wl, 0.0), cons(wr, 0.0)
+    if SL >= 0:
+        return FL
+    if SR <= 0:
+        return FR
+    rl, ul, pl = wl[0], wl[1], wl[4]
+    rr, ur, pr = wr[0], wr[1], wr[4]
+    Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur))
+
+    def ustar(w, U, S):
+        r, u, p = w[0], w[1], w[4]
+        fac = r * (S - u) / (S - Ss)
+        return fac * np.array([1.0, Ss, w[2], w[3], U[4] / r + (Ss - u) * (Ss + p / (r * (S - u))), 0, 0])
+
+    if Ss >= 0:
+        return FL + SL * (ustar(wl, UL, SL) - UL)
+    return FR + SR * (ustar(wr, UR, SR) - UR)
+
+
+def test_hlld_reduces_to_hllc_without_field():
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        wl, _ = rand_state(rng)
+        wr, _ = rand_state(rng)
+        wl[5:] = 0
+        wr[5:] = 0
+        np.testing.assert_allclose(O.hlld(G, wl, wr, 0.0), hllc_toro(wl, wr), rtol=1e-13, atol=1e-13)
+
+
+def test_hlld_stationary_contact_exact():
+    """An isolated stationary contact (u = 0, equal P and B, density jump) has zero mass flux."""
+    wl = np.array([2.0, 0.0, 0.3, -0.2, 1.0, 0.4, 0.7])
+    wr = np.array([0.5, 0.0, 0.3, -0.2, 1.0, 0.4, 0.7])
+    for bn in (0.0, 0.9, -1.3):
+        f = O.hlld(G, wl, wr, bn)
+        np.testing.assert_allclose(f, physical_flux(wl, bn), atol=1e-15)
+        np.testing.assert_allclose(f, physical_flux(wr, bn), atol=1e-15)
+
+
+def test_hlld_rotational_discontinuity_exact():
+    """An isolated stationary rotational discontinuity: rho = P = B_n = 1, u = -1,
+    B_t (1,0) -> (0,1), v_t (0,0) -> (1,-1) satisfies the jump conditions, so
+    F(U_L) = F(U_R) and HLLD returns it."""
+    wl = np.array([1.0, -1.0, 0.0, 0.0, 1.0, 1.0, 0.0])
+    wr = np.array([1.0, -1.0, 1.0, -1.0, 1.0, 0.0, 1.0])
+    np.testing.assert_allclose(physical_flux(wl, 1.0), physical_flux(wr, 1.0), atol=1e-15)
+    np.testing.assert_allclose(O.hlld(G, wl, wr, 1.0), physical_flux(wl, 1.0), atol=1e-14)
+
+
+def test_hlld_mirror_symmetry():
+    """x -> -x maps (u, B_n) -> (-u, -B_n) and swaps the states; the flux
+    components odd under the reflection change sign."""
+    rng = np.random.default_rng(6)
+    M = np.array([1, -1, 1, 1, 1, 1, 1.0])        # primitive mirror: u -> -u
+    Fm = np.array([-1, 1, -1, -1, -1, -1, -1.0])  # flux mirror
+    for _ in range(50):
+        wl, bn = rand_state(rng)
+        wr, _ = rand_state(rng)
+        f = O.hlld(G, wl, wr, bn)
+        g = O.hlld(G, wr * M, wl * M, -bn)
+        np.testing.assert_allclose(g, Fm * f, rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------- eigen --
+def primitive_jacobian(w, bn, gamma=G):
+    """Primitive form of the 1-D ideal-MHD equations (Sec. 2.1)."""
+    rho, u, v, ww, p, by, bz = w
+    A = np.zeros((7, 7))
+    A[0, 0], A[0, 1] = u, rho
+    A[1, 1], A[1, 4], A[1, 5], A[1, 6] = u, 1 / rho, by / rho, bz / rho
+    A[2, 2], A[2, 5] = u, -bn / rho
+    A[3, 3], A[3, 6] = u, -bn / rho
+    A[4, 1], A[4, 4] = gamma * p, u
+    A[5, 1], A[5, 2], A[5, 5] = by, -bn, u
+    A[6, 1], A[6, 3], A[6, 6] = bz, -bn, u
+    return A
+
+
+@pytest.mark.parametrize("case", ["random", "bt0", "bn0", "a_eq_ca", "triple"])
+def test_eigensystem(case):
+    """Stone et al. (2008, App. A) eigenvectors: A R = R diag(lambda), L R = I,
+    and finite at the degeneracies (B_t = 0, B_n = 0, a = c_a)."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        w, bn = rand_state(rng)
+        if case == "bt0":
+            w[5:] = 0
+        elif case == "bn0":
+            bn = 0.0
+        elif case == "a_eq_ca":
+            bn = math.sqrt(G * w[4])
+        elif case == "triple":
+            w[5:] = 0
+            w[0] = 1.0
+            bn = math.sqrt(G * w[4])
+        lam, R, L = O.eigen(G, w, bn)
+        assert np.all(np.isfinite(R)) and np.all(np.isfinite(L))
+        assert np.all(np.diff(lam) >= -1e-12)
+        A = primitive_jacobian(w, bn)
+        scale = 1 + np.max(np.abs(A)) * np.max(np.abs(R))
+        assert np.max(np.abs(A @ R - R * lam[None, :])) < 1e-12 * scale
+        assert np.max(np.abs(L @ R - np.eye(7))) < 1e-12 * (1 + np.max(np.abs(L)) * np.max(np.abs(R)))
+
+
+# --------------------------------------------------------- reconstruction --
+def _wave_state(box, f_rho):
+    """rho varies along x; P, v, B uniform: a pure entropy (contact) mode."""
+    x, _, _ = box.centres()
+    rho = np.broadcast_to(f_rho(x), box.shape)
+    return I.assemble(box, rho, (0.2, -0.1, 0.3), 0.9, (0.6, 0.5, -0.4))
+
+
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_recon_uniform_has_zero_slope(recon):
+    box = I.Box(8, 6, 5)
+    U = I.uniform(box, 1.3, (0.2, -0.4, 0.1), 0.8, (0.7, -0.3, 0.5))
+    orc = O.Oracle(8, 6, 5, recon=recon)
+    for a in range(3):
+        WL, WR = orc.recon(U, a)
+        assert np.array_equal(WL, WR)
+        W0, _ = orc.recon(U, a, recon="pcm")
+        np.testing.assert_allclose(WL, W0, rtol=1e-15, atol=1e-16)
+
+
+def test_plmc_linear_entropy_profile_gives_centred_slope():
+    """Sec. 2.2.6: for monotone linear data in one characteristic field the
+    limiter returns the centred difference, so W_L(i+1/2) = (W_i + W_{i+1})/2."""
+    box = I.Box(16, 4, 4)
+    U = _wave_state(box, lambda x: 1.0 + 0.3 * x)
+    WL, WR = O.Oracle(16, 4, 4, recon="plmc").recon(U, 0)
+    rho = U[0, 0, 0, :]
+    for i in range(1, 14):
+        assert abs(WL[0, 0, 0, i] - 0.5 * (rho[i] + rho[i + 1])) < 1e-14
+        assert abs(WR[0, 0, 0, i] - 0.5 * (rho[i] + rho[i - 1])) < 1e-14
+        np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_recon_flat_at_extremum(recon):
+    """A local extremum of the cell averages gets no slope (Eq. limiter; MC11)."""
+    box = I.Box(16, 4, 4)
+    U = _wave_state(box, lambda x: 1.0 + 0.3 * np.exp(-((x - 0.5 + 1 / 32) / 0.1) ** 2))
+    WL, WR = O.Oracle(16, 4, 4, recon=recon).recon(U, 0)
+    i = 7  # the peak cell
+    rho = U[0, 0, 0, :]
+    assert rho[i] > rho[i - 1] and rho[i] > rho[i + 1]
+    if recon == "plmc":
+        assert WL[0, 0, 0, i] == rho[i] and WR[0, 0, 0, i] == rho[i]
+    else:  # the MC11 limiter may keep a bounded curvature; the state stays within the local range
+        assert min(rho[i - 1], rho[i + 1]) <= WL[0, 0, 0, i] <= rho[i] + 1e-15
+        assert min(rho[i - 1], rho[i + 1]) <= WR[0, 0, 0, i] <= rho[i] + 1e-15
+
+
+def test_ppmc_exact_for_cubics():
+    """Fourth-order interface values: exact for cell averages of a cubic when no
+    limiter is active (monotone profile)."""
+    box = I.Box(32, 4, 4)
+    c = (1.0, 0.5, 0.3, 0.2)
+
+    def prim(x):  # antiderivative of the cubic
+        return c[0] * x + c[1] * x ** 2 / 2 + c[2] * x ** 3 / 3 + c[3] * x ** 4 / 4
+
+    def cubic(x):
+        return c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+
+    dx = box.dx
+    x, _, _ = box.centres()
+    avg = (prim(x + dx / 2) - prim(x - dx / 2)) / dx
+    U = _wave_state(box, lambda _x: avg)
+    WL, WR = O.Oracle(32, 4, 4, recon="ppmc").recon(U, 0)
+    xi = (np.arange(32) + 0.5) * dx
+    for i in range(3, 28):
+        assert abs(WL[0, 0, 0, i] - cubic(xi[i] + dx / 2)) < 1e-13
+        assert abs(WR[0, 0, 0, i] - cubic(xi[i] - dx / 2)) < 1e-13
+
+
+# ------------------------------------------------------------------- CT --
+def test_edge_emf_exact_for_linear_fields():
+    """Eq. emf-edge with upwinded slopes (D-6) reproduces an electric field that
+    is linear in one transverse coordinate, face and reference alike."""
+    n = 8
+    box = I.Box(n, n, n)
+    orc = O.Oracle(n, n, n)
+    x, y, z = box.centres()
+    s = 0.7
+    for direction in ("x", "y"):
+        for sign in (1.0, -1.0, 0.0):
+            # reference E_z = -(vx By - vy Bx) with B = (0, 1, 0): E_z = -vx = f
+            if direction == "y":
+                f_cell = np.broadcast_to(1.0 + s * y, box.shape)
+            else:
+                f_cell = np.broadcast_to(1.0 + s * x, box.shape)
+            U = I.assemble(box, 1.0, (-f_cell, np.zeros(box.shape), np.zeros(box.shape)), 1.0, (0.0, 1.0, 0.0))
+            F = np.zeros((3, 7) + box.shape)
+            # x-face (i+1/2, j): E_z = -F_x[B_t1]; y-face (i, j+1/2): E_z = +F_y[B_t2]
+            xf = (1.0 + s * np.broadcast_to(y, box.shape)) if direction == "y" else (1.0 + s * np.broadcast_to(x + box.dx / 2, box.shape))
+            yf = (1.0 + s * np.broadcast_to(y + box.dy / 2, box.shape)) if direction == "y" else (1.0 + s * np.broadcast_to(x, box.shape))
+            F[0, 5] = -xf
+            F[1, 6] = yf
+            F[0, 0] = sign  # mass fluxes decide the upwinding
+            F[1, 0] = -sign
+            E = orc.edges(U, F)
+            exact = 1.0 + s * ((y + box.dy / 2) if direction == "y" else (x + box.dx / 2))
+            exact = np.broadcast_to(exact, box.shape)
+            sl = (slice(None), slice(1, n - 2), slice(1, n - 2))  # away from the periodic wrap
+            np.testing.assert_allclose(E[2][sl], exact[sl], rtol=1e-14, atol=1e-14)
+
+
+# ---------------------------------------------------------- full step --
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_uniform_state_bit_identical(recon):
+    box = I.Box(8, 7, 6)
+    U = I.uniform(box, 1.1, (0.4, -0.3, 0.2), 0.6, (0.8, -0.5, 0.3))
+    orc = O.Oracle(8, 7, 6, recon=recon)
+    V, _ = orc.run(U, 10, cfl=0.4)
+    assert np.array_equal(U, V)
+
+
+def _turb(n, seed=11):
+    return I.turbulent_box(I.Box(n, n, n), seed_v=seed, seed_b=seed + 1, kmax=4)
+
+
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_conservation_and_divb(recon):
+    """Periodic box: sums of rho, m, E and of each face-B component are conserved
+    to round-off (telescoping fluxes / EMF curl), and CT keeps div B at its
+    initial round-off level (Sec. 2.2, Steps 4-5, 8-9)."""
+    n = 12
+    U = _turb(n)
+    orc = O.Oracle(n, n, n, recon=recon)
+    d0, t0 = orc.diagnostics(U)
+    V, _ = orc.run(U, 10, cfl=0.3)
+    d1, t1 = orc.diagnostics(V)
+    scale = np.array([np.sum(np.abs(U[f])) for f in range(8)])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
+    bmax = np.max(np.abs(V[5:]))
+    assert d1 * (1.0 / n) / bmax < 1e-14
+    assert not np.array_equal(U, V)
+
+
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_cyclic_axis_permutation_invariance(recon):
+    """Relabelling x->y->z->x commutes with the step (Sec. 3.1.1, 'identical
+    results in all three directions'); not bitwise, summation order differs."""
+    n = 10
+    U = _turb(n, 21)
+    orc = O.Oracle(n, n, n, recon=recon)
+    dt = 0.5 * orc.dt(U, 0.3)
+    A = I.cycle_axes(orc.step(orc.step(U, dt), dt))
+    B = orc.step(orc.step(I.cycle_axes(U), dt), dt)
+    for f in range(8):
+        np.testing.assert_allclose(A[f], B[f], rtol=0, atol=1e-13 * np.max(np.abs(U[f])) + 1e-15)
+
+
+def test_stationary_contact_preserved():
+    box = I.Box(16, 4, 4)
+    U = I.shock_tube(box, (2.0, 0, 0.3, -0.2, 1.0, 0.5, 0.2), (0.5, 0, 0.3, -0.2, 1.0, 0.5, 0.2), 0.8)
+    for recon in ("plmc", "ppmc"):
+        orc = O.Oracle(16, 4, 4, recon=recon)
+        V, _ = orc.run(U, 10, cfl=0.4)
+        np.testing.assert_allclose(V, U, rtol=0, atol=1e-14)
+
+
+def test_stationary_rotational_discontinuity_preserved_pcm():
+    """Sec. 2.2.2 (PCM mode): HLLD resolves an isolated rotational discontinuity
+    exactly.  Both interfaces of the periodic box (L|R and R|L) satisfy the
+    same jump relation dv_t = -dB_t, so the whole state is steady."""
+    box = I.Box(16, 4, 4)
+    U = I.shock_tube(box, (1.0, -1.0, 0.0, 0.0, 1.0, 1.0, 0.0), (1.0, -1.0, 1.0, -1.0, 1.0, 0.0, 1.0), 1.0)
+    orc = O.Oracle(16, 4, 4, recon="pcm")
+    V, _ = orc.run(U, 10, cfl=0.3)
+    np.testing.assert_allclose(V, U, rtol=0, atol=1e-13)
+
+
+@pytest.mark.slow
+def test_linear_wave_second_order_and_ppm_more_accurate():
+    """Sec. 3.1.1: second-order convergence for linear waves, PPM more accurate than PLM."""
+    def err(recon, N):
+        box = I.Box(N, 4, 4)
+        U0, speed = I.linear_wave(box, amp=1e-6)
+        orc = O.Oracle(N, 4, 4, recon=recon)
+        T, t, U = 1.0 / abs(speed), 0.0, U0.copy()
+        while t < T * (1 - 1e-14):
+            dt = min(orc.dt(U, 0.4), T - t)
+            U = orc.step(U, dt)
+            t += dt
+        e = np.mean(np.abs(U - U0), axis=(1, 2, 3))
+        return math.sqrt(np.sum(e ** 2))
+
+    ep = [err("plmc", N) for N in (16, 32, 64)]
+    eq = [err("ppmc", N) for N in (16, 32, 64)]
+    assert 1.8 < math.log2(ep[1] / ep[2]) < 2.3
+    assert 1.8 < math.log2(eq[1] / eq[2]) < 2.3
+    assert all(q < p for p, q in zip(ep, eq))
+
+
+# ------------------------------------------------------------ dual numbers --
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_jvp_matches_central_difference(recon):
+    """The forward-mode derivative of one step equals a central finite
+    difference (eps small enough that no limiter or upwind switch is crossed)."""
+    n = 8
+    U = I.turbulent_box(I.Box(n, n, n), seed_v=31, seed_b=32, kmax=2)
+    orc = O.Oracle(n, n, n, recon=recon)
+    dt = orc.dt(U, 0.3)
+    rng = np.random.default_rng(8)
+    d = rng.normal(size=U.shape)
+    d[5:] = 0  # hydro directions keep div B = 0
+    V, JV = orc.step_jvp(U, d, dt)
+    assert np.array_equal(V, orc.step(U, dt))
+    eps = 1e-8
+    fd = (orc.step(U + eps * d, dt) - orc.step(U - eps * d, dt)) / (2 * eps)
+    err = np.max(np.abs(fd - JV)) / np.max(np.abs(JV))
+    assert err < 1e-6
