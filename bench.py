@@ -1,0 +1,336 @@
+"""Benchmark of the VL+CT ideal-MHD step on GB300 (cell-updates/s).
+
+Workload (default): the 256^3 periodic turbulent box (rho = 1, P = 1, k^-2
+velocity at rms Mach 1 over k = 1..16, B = (0.5, 0, 0) + divergence-free
+perturbation of rms 0.1), PLMC + HLLD, CFL 0.3, dt from the CFL reduction on
+the device every step.  The headline line is the FP64 step; the FP32-bulk
+step on the same workload is reported under "variants".
+
+Timing: W warm-up steps, then K steps bracketed by a barrier and a device
+synchronisation, CUDA events on the library's stream, max over ranks.  The
+state (1.07 GB) and workspace are far larger than L2, so no flush is needed.
+Per-stage device times come from the library's event tracing over the same
+timed region.  One process per GPU; ranks run independent replicas (weak
+scaling, no data-path collective).
+
+--impl reference times the CPU oracle (the plain FP64 reference) on the
+host cores on a bounded sample of the same recipe (128^3 per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-updates/s on 1 GB300 (FP64 vs FP32-bulk step, adjoint step); % HBM roofline"
+UNIT = "cell-updates/s"
+
+# Algorithmic HBM bytes per cell of one launch of each stage (reads + writes of
+# the arrays the stage must touch once; T = compute type size).  See the design doc.
+def stage_bytes(T: int) -> dict:
+    return {
+        "prim": 64 + 8 * T,                  # U in, W out
+        "flux_pcm": 8 * T + 24 + 21 * T,     # W, face B in; 3x7 fluxes out
+        "emf": (6 + 9) * T + 3 * T,          # v, B_cc, 2 EMF + mass flux per axis; 3 edges out
+        "update_half": 64 + 18 * T + 11 * T,  # U, 15 hydro fluxes + 3 edges in; W + 3 faces out
+        "recon": 8 * T + 14 * T,             # W in; W_L, W_R out (one axis)
+        "flux_hlld": 15 * T + 7 * T,         # W_L, W_R, face B in; 7 fluxes out (one axis)
+        "update_full": 64 + 18 * T + 64,     # U, fluxes, edges in; U out
+        "dt": 0,
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA rate of this GPU measured by an FMA-chain probe:
+# 601 G DFMA/s = 1.20 TFLOP/s.
+FP64_PEAK_GFLOPS = 1202.6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, s[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_state(n: int, recipe: str = "turbulent"):
+    from paper_2402_05240_gb300 import inputs
+    box = inputs.Box(n, n, n)
+    if recipe == "turbulent":
+        return inputs.turbulent_box(box, seed_v=1, seed_b=2)
+    raise ValueError(recipe)
+
+
+def time_gpu(mhd, torch, U0, n, steps, warmup, recon, precision, barrier):
+    """Times `steps` device-dt VL+CT steps; returns (ms_per_step, stage profile, launches)."""
+    stream = torch.cuda.current_stream()
+    sim = mhd.Sim(n, n, n, cfl=0.3, recon=recon, precision=precision, stream=stream.cuda_stream)
+    U = U0.clone()
+    sim.run(U, warmup)
+    torch.cuda.synchronize()
+    sim.status()
+    mhd.mhd_profile_enable(sim.ctx, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.run(U, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = mhd.mhd_profile_read(sim.ctx)
+    mhd.mhd_profile_enable(sim.ctx, False)
+    code, floors = mhd.mhd_status(sim.ctx)
+    if code != mhd.MHD_OK:
+        raise RuntimeError(f"device flags after the timed run: {code}")
+    launches = sum(v[1] for v in prof.values())
+    return ms / steps, prof, launches, sim, U
+
+
+def roofline_of(prof, precision, n3, hbm_peak, peak_kind, traffic=None):
+    T = 8 if precision == "fp64" else 4
+    sb = stage_bytes(T)
+    total = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms, launches) = dom
+    per_launch_ms = ms / max(launches, 1)
+    achieved = sb[name] * n3 / (per_launch_ms * 1e-3) / 1e9
+    shares = {k: round(v[0] / total, 4) for k, v in prof.items() if v[1]}
+    return {
+        "kernel": name,
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": hbm_peak,
+        "unit": "GB/s",
+        "frac": round(achieved / hbm_peak, 4),
+        "peak_source": peak_kind,
+        "traffic": traffic,
+        "per_launch_ms": round(per_launch_ms, 4),
+        "stage_share": shares,
+        "bytes_per_cell_counted": sum(sb[k] * v[1] for k, v in prof.items()) / max(1, prof["update_full"][1]),
+    }
+
+
+def cpu_baseline_sample(n_sample=128, steps=1):
+    """The oracle as it stands on the host cores: one step of the same recipe
+    at n_sample^3 (a bounded sample of the 256^3 workload)."""
+    import oracle
+    U = make_state(n_sample)
+    orc = oracle.Oracle(n_sample, n_sample, n_sample, recon="plmc")
+    dt = orc.dt(U, 0.3)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = orc.step(U, dt)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n_sample ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 PLMC step(s) of the turbulent-box recipe at {n_sample}^3 "
+                      f"({el:.1f} s wall)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    import oracle
+    U = make_state(n)
+    orc = oracle.Oracle(n, n, n, recon=args.recon)
+    dt = orc.dt(U, 0.3)
+    for _ in range(args.warmup):
+        orc.step(U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = orc.step(U, dt)
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"turbulent box {n}^3 sample of the 256^3 recipe, "
+                                                   f"{args.recon.upper()} + HLLD, FP64, CPU oracle",
+                                        "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n}^3 per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--recon", default="plmc", choices=["plmc", "ppmc"])
+    ap.add_argument("--ref-n", type=int, default=96)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+        def barrier():
+            dist.barrier()
+    else:
+        dist = None
+
+        def barrier():
+            pass
+
+    from paper_2402_05240_gb300 import build
+    build.build()
+    from paper_2402_05240_gb300 import mhd
+
+    n = args.n
+    n3 = n ** 3
+    U0 = torch.from_numpy(make_state(n)).cuda()
+    hbm_peak, peak_kind = load_peaks()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64, prof64, launches64, sim, U = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon, "fp64",
+                                                  barrier)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms64], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms64 = float(t.item())
+    value = world * n3 / (ms64 * 1e-3)
+    roof = roofline_of(prof64, "fp64", n3, hbm_peak, peak_kind)
+
+    # end to end through the public host-buffer entry point (copies inside)
+    host = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True)
+    host.copy_(U0.cpu())
+    mhd.mhd_run_host(sim.ctx, host, 1)  # warm the host-state buffer
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        mhd.mhd_run_host(sim.ctx, host, 1)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    sim.close()
+    del U, sim
+
+    variants = {}
+    if not args.no_variants:
+        ms32, prof32, launches32, sim32, U32 = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
+                                                        "fp32_bulk", barrier)
+        variants["fp32_bulk"] = {
+            "value": world * n3 / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32 (FP64 state)",
+            "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind), "gpu_launches": launches32}
+        sim32.close()
+        del U32, sim32
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"turbulent box {n}^3, {args.recon.upper()} + HLLD, FP64 step, CFL 0.3, device dt",
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (state 1.07 GB)"},
+        "roofline": roof,
+        "alu_fp64": {"peak_gflops": FP64_PEAK_GFLOPS, "note": "FP64 FMA rate measured by a probe"},
+        "e2e": {"value": n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3, "d2h_bytes_per_step": 64 * n3},
+        "gpu_launches": launches64,
+        "clocks": clk,
+        "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in prof64.items()},
+        "variants": variants,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/* mhd_api.h -- C ABI of the GB300 VL+CT ideal-MHD library (libmhd.so).
+ *
+ * Method: the Van Leer + Constrained Transport step of Caddy & Schneider,
+ * "Cholla-MHD" (arXiv:2402.05240), Sec. 2.2, Steps 1-10: CFL time step
+ * (Eq. dt), PCM predictor fluxes from the HLLD Riemann solver (Steps 2-3),
+ * edge electric fields (Eq. emf-edge, Steps 4 and 8), half-step update
+ * (Step 5), PLMC/PPMC characteristic reconstruction (Step 6, Sec. 2.2.6),
+ * corrector fluxes (Step 7) and full-step update (Step 9), on a periodic 3-D
+ * Cartesian mesh.
+ *
+ * State layout (all entry points): one contiguous float64 array
+ *   U[8][nz][ny][nx], x fastest, fields rho, mx, my, mz, E, Bx, By, Bz
+ * (the conserved vector U of Sec. 2.1).  Bx[k][j][i] is the face-centred
+ * field at x_{i+1/2} (the upper x-face of cell i; Sec. 2.2 "staggered grid");
+ * By at y_{j+1/2}, Bz at z_{k+1/2}.  There are no ghost cells: periodic
+ * neighbours are found by wrap-around indexing inside the kernels.
+ *
+ * Pointers: arguments named *_dev are device pointers (cudaMalloc / torch
+ * CUDA tensors), *_host host pointers.  The caller owns every state and
+ * gradient buffer; the library owns only the workspace it allocates in
+ * mhd_init and frees in mhd_destroy.  All device work is issued on the
+ * stream given to mhd_init (NULL = legacy default stream).
+ *
+ * Errors: every call returns an int status (MHD_OK = 0, negative on error);
+ * the library never exits, aborts or traps.  Device kernels raise flags
+ * (non-finite value, non-positive density) that the synchronising calls
+ * (mhd_dt, mhd_status, mhd_diagnostics, mhd_run_host) report.
+ */
+#ifndef MHD_API_H
+#define MHD_API_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHD_OK 0
+#define MHD_ERR_ARG (-1)       /* invalid argument (NULL, size, option)        */
+#define MHD_ERR_CUDA (-2)      /* a CUDA runtime call failed                   */
+#define MHD_ERR_OOM (-3)       /* workspace allocation failed                  */
+#define MHD_ERR_NONFINITE (-4) /* a kernel saw NaN/Inf or density <= 0         */
+#define MHD_ERR_DT (-5)        /* dt <= 0 or not finite                        */
+
+#define MHD_RECON_PCM 0  /* piecewise constant (Sec. 2.2.2)                   */
+#define MHD_RECON_PLMC 1 /* piecewise linear, characteristic (Sec. 2.2.6)     */
+#define MHD_RECON_PPMC 2 /* piecewise parabolic, characteristic (Felker & Stone 2018) */
+
+#define MHD_FP64 0      /* all arithmetic in float64                          */
+#define MHD_FP32_BULK 1 /* reconstruction, Riemann solver and EMFs in float32;
+                           state accumulation and pressure recovery in float64 */
+
+typedef struct mhd_config {
+  int nx, ny, nz;          /* cells per axis, each >= 4                       */
+  double dx, dy, dz;       /* cell widths (> 0)                               */
+  double gamma;            /* adiabatic index, P = (gamma-1) eps (Sec. 2.1)   */
+  double cfl;              /* Courant number C_CFL of Eq. dt (0 < cfl <= 0.5) */
+  int recon;               /* MHD_RECON_* for Step 6                          */
+  int precision;           /* MHD_FP64 or MHD_FP32_BULK                       */
+  double rho_floor;        /* density floor (use 1e-20 for "off")             */
+  double p_floor;          /* pressure floor (use 1e-20 for "off")            */
+} mhd_config;
+
+typedef struct mhd_ctx mhd_ctx; /* opaque; owns the workspace */
+
+/* Bytes of device workspace mhd_init will allocate for cfg. */
+int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes);
+
+/* Create a context for cfg on the current CUDA device; stream is a
+ * cudaStream_t (NULL = default stream).  Allocates the workspace. */
+int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream);
+
+/* Free the workspace and the context (NULL is ignored). */
+void mhd_destroy(mhd_ctx* ctx);
+
+/* Step 1, Eq. dt: dt = C_CFL * min over cells and directions l of
+ * d_l / (|v_l| + c_f,l), c_f from cell-centred values with longitudinal B_l.
+ * U_dev: state (read only).  Synchronous; writes the value to *dt_host. */
+int mhd_dt(mhd_ctx* ctx, const double* U_dev, double* dt_host);
+
+/* One VL+CT step (Steps 2-9) at the given dt, in place: U_dev holds U^n on
+ * entry and U^{n+1} on return.  Asynchronous on the context's stream. */
+int mhd_step(mhd_ctx* ctx, double* U_dev, double dt);
+
+/* nsteps VL+CT steps, each with dt from Step 1 computed on the device (the
+ * reduction of the full update of one step gives the dt of the next), in
+ * place.  dt_dev (device, may be NULL) receives the nsteps dt values used.
+ * Asynchronous. */
+int mhd_run(mhd_ctx* ctx, double* U_dev, int nsteps, double* dt_dev);
+
+/* As mhd_run on a HOST state: copies U_host to a device buffer owned by the
+ * context, runs nsteps, copies the result back and synchronises.  *t_host
+ * (may be NULL) receives the simulated time advanced. */
+int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
+
+/* Vector-Jacobian product of one mhd_step at fixed dt (not in the paper):
+ * gU_n = (dU^{n+1}/dU^n)^T gU_np1.  U_n_dev: the state the forward step
+ * started from (read only); gU_np1_dev: cotangent of U^{n+1}; gU_n_dev:
+ * output, same layout as U.  Recomputes the forward intermediates in the
+ * workspace.  Asynchronous. */
+int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const double* gU_np1_dev,
+                     double* gU_n_dev);
+
+/* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
+ * |div B| from face differences, and the sums of the 8 fields.  Synchronous. */
+int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, double totals_host[8]);
+
+/* Synchronise and read the device flags raised since the last call;
+ * counts_host[0..1] (may be NULL) receive the density / pressure floor
+ * triggers of the full updates since the last call.  Returns MHD_OK or
+ * MHD_ERR_NONFINITE. */
+int mhd_status(mhd_ctx* ctx, long long counts_host[2]);
+
+/* Static message for a status code. */
+const char* mhd_strerror(int code);
+
+/* ---- tracing: per-stage CUDA-event timing -----------------------------
+ * With profiling on, every kernel launch of mhd_run / mhd_step is bracketed
+ * by CUDA events on the context's stream; mhd_profile_read synchronises and
+ * returns, per stage, the summed device milliseconds and the launch count
+ * since the last enable/read (then clears them).  Stage ids: */
+#define MHD_STAGE_PRIM 0        /* primitives, floors, dt reduction (Step 1) */
+#define MHD_STAGE_FLUX_PCM 1    /* PCM + HLLD predictor fluxes (Steps 2-3)    */
+#define MHD_STAGE_EMF 2         /* edge electric fields (Steps 4, 8)          */
+#define MHD_STAGE_UPDATE_HALF 3 /* half-step update (Step 5)                  */
+#define MHD_STAGE_RECON 4       /* PLMC / PPMC states (Step 6)                */
+#define MHD_STAGE_FLUX_HLLD 5   /* corrector HLLD fluxes (Step 7)             */
+#define MHD_STAGE_UPDATE_FULL 6 /* full-step update (Step 9)                  */
+#define MHD_STAGE_DT 7          /* dt finalisation                            */
+#define MHD_NUM_STAGES 8
+
+int mhd_profile_enable(mhd_ctx* ctx, int on);
+int mhd_profile_read(mhd_ctx* ctx, double ms_host[MHD_NUM_STAGES], long long launches_host[MHD_NUM_STAGES]);
+const char* mhd_stage_name(int stage);
+
+/* ---- per-stage entry points (for stage-by-stage parity checks) ---------
+ * All outputs are float64 device arrays in the oracle's layouts; in
+ * MHD_FP32_BULK mode the float32 intermediates are widened on output. */
+
+/* W_dev[8][N]: rho, vx, vy, vz, P, Bcc_x, Bcc_y, Bcc_z (Sec. 2.2.1). */
+int mhd_stage_primitives(mhd_ctx* ctx, const double* U_dev, double* W_dev);
+
+/* F_dev[3][7][N]: HLLD flux through the upper face of every cell per axis
+ * a, in the solver frame (rho, m_n, m_t1, m_t2, E, B_t1, B_t2) with
+ * (n, t1, t2) = (a, a+1, a+2) cyclically; states from recon (Steps 2-3, 6-7). */
+int mhd_stage_fluxes(mhd_ctx* ctx, const double* U_dev, int recon, double* F_dev);
+
+/* E_dev[3][N]: edge field E_a of every cell at p + e_b/2 + e_c/2 from the
+ * fluxes F_dev and the reference fields of U_dev (Eq. emf-edge, Step 4). */
+int mhd_stage_edges(mhd_ctx* ctx, const double* U_dev, const double* F_dev, double* E_dev);
+
+/* WL_dev/WR_dev[7][N]: W_{L,p+1/2} and W_{R,p-1/2} of every cell along axis
+ * (Step 6), solver frame, for recon = MHD_RECON_*. */
+int mhd_stage_recon(mhd_ctx* ctx, const double* U_dev, int axis, int recon, double* WL_dev, double* WR_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHD_API_H */

@@ -1,0 +1,18 @@
+// Instantiation of the step kernels for the FP64 step.
+#define MHD_SCALAR_KERNELS  // dt and diagnostics kernels live in this unit only
+#include "mhd_kernels.cuh"
+
+namespace mhd {
+template struct Launch<double>;
+
+void launch_set_dt(double* dt_cur, double value, cudaStream_t s) { k_set_dt<<<1, 1, 0, s>>>(dt_cur, value); }
+void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
+                      unsigned* flags, cudaStream_t s) {
+  k_finish_dt<<<1, 1, 0, s>>>(cfl, dtbits, dt_cur, dt_log, step, flags);
+}
+void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s) {
+  // partials live after the 9 final values
+  k_diag_partial<<<nb, DIAG_T, 0, s>>>(g, U, red + 9, nb);
+  k_diag_final<<<1, DIAG_T, 0, s>>>(red + 9, red, nb);
+}
+}  // namespace mhd

@@ -1,0 +1,466 @@
+// mhd_api.cu -- the C ABI (include/mhd_api.h): context, workspace, step
+// sequencing.  Every numerical stage runs in the kernels of mhd_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mhd_api.h"
+#include "mhd_launch.h"
+
+using mhd::Grid;
+using mhd::Launch;
+
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+struct mhd_ctx {
+  mhd_config cfg;
+  Grid g;
+  cudaStream_t stream;
+  size_t ts;            // bytes of the compute type
+  void* ws;             // one workspace allocation
+  size_t ws_bytes;
+  // typed views into ws (element type = compute type)
+  void *W, *F, *E, *WL, *WR, *Bh;
+  double* scal;                 // [0] dt_cur
+  unsigned long long* dtbits;   // [0] dt reduction word
+  unsigned long long* floors;   // [0..1] floor counters
+  unsigned* flags;              // [0] error flags
+  double* red;                  // diagnostics partials
+  double* host_state;           // lazily allocated device copy for mhd_run_host
+  size_t red_count;
+  // optional per-stage CUDA-event timing (mhd_profile_enable)
+  int prof_on;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t W, F, E, WL, WR, Bh, scal, dtbits, floors, flags, red, total;
+};
+
+size_t red_blocks(long long N) {
+  long long b = (N + 1023) / 1024;
+  return (size_t)(b < 1 ? 1 : b);
+}
+
+Layout layout_of(const mhd_config& c) {
+  const size_t N = (size_t)c.nx * c.ny * c.nz;
+  const size_t ts = c.precision == MHD_FP32_BULK ? 4 : 8;
+  Layout L;
+  size_t off = 0;
+  L.W = off;
+  off += up(8 * N * ts);
+  L.F = off;
+  off += up(21 * N * ts);
+  L.E = off;
+  off += up(3 * N * ts);
+  L.WL = off;
+  off += up(7 * N * ts);
+  L.WR = off;
+  off += up(7 * N * ts);
+  L.Bh = off;
+  off += up(3 * N * ts);
+  L.scal = off;
+  off += up(8 * sizeof(double));
+  L.dtbits = off;
+  off += up(sizeof(unsigned long long));
+  L.floors = off;
+  off += up(2 * sizeof(unsigned long long));
+  L.flags = off;
+  off += up(sizeof(unsigned));
+  L.red = off;
+  off += up((9 + 9 * red_blocks((long long)N)) * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+int check_cfg(const mhd_config* c) {
+  if (!c) return MHD_ERR_ARG;
+  if (c->nx < 4 || c->ny < 4 || c->nz < 4) return MHD_ERR_ARG;
+  if ((long long)c->nx * c->ny > (1ll << 31) || c->nz > 65535) return MHD_ERR_ARG;
+  if (!(c->dx > 0) || !(c->dy > 0) || !(c->dz > 0)) return MHD_ERR_ARG;
+  if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) return MHD_ERR_ARG;
+  if (!(c->cfl > 0.0) || c->cfl > 1.0) return MHD_ERR_ARG;
+  if (c->recon < MHD_RECON_PCM || c->recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
+  if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK) return MHD_ERR_ARG;
+  if (!(c->rho_floor > 0) || !(c->p_floor > 0)) return MHD_ERR_ARG;
+  return MHD_OK;
+}
+
+int cuda_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MHD_OK : MHD_ERR_CUDA;
+}
+
+template <class T> T* as(void* p) { return static_cast<T*>(p); }
+
+cudaEvent_t next_event(mhd_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+// Runs one launch; with profiling on, brackets it with events on the stream.
+template <class Fn> void prof(mhd_ctx* c, int stage, Fn&& fn) {
+  if (!c->prof_on) {
+    fn();
+    return;
+  }
+  ProfRec r;
+  r.stage = stage;
+  r.a = next_event(c);
+  r.b = next_event(c);
+  cudaEventRecord(r.a, c->stream);
+  fn();
+  cudaEventRecord(r.b, c->stream);
+  c->prof.push_back(r);
+}
+
+// Steps 2-9 given W^n (in ctx->W) and dt in scal[0]; U in place.
+template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  T* W = as<T>(c->W);
+  T* F = as<T>(c->F);
+  T* E = as<T>(c->E);
+  prof(c, MHD_STAGE_FLUX_PCM, [&] { Launch<T>::flux_pcm(g, W, U, F, s); });  // Steps 2-3
+  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 4
+  prof(c, MHD_STAGE_UPDATE_HALF,
+       [&] { Launch<T>::update_half(g, U, F, E, c->scal, W, as<T>(c->Bh), c->flags, s); });  // Step 5
+  for (int a = 0; a < 3; ++a) {                                               // Steps 6-7
+    prof(c, MHD_STAGE_RECON, [&] { Launch<T>::recon(g, recon, a, W, as<T>(c->WL), as<T>(c->WR), s); });
+    prof(c, MHD_STAGE_FLUX_HLLD,
+         [&] { Launch<T>::flux_hlld(g, a, as<T>(c->WL), as<T>(c->WR), as<T>(c->Bh), F, s); });
+  }
+  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 8
+  prof(c, MHD_STAGE_UPDATE_FULL, [&] { Launch<T>::update_full(g, U, F, E, c->scal, s); });  // Step 9
+}
+
+template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  // arm the reduction word (bytes 0x7f: a huge positive double), then W^0 and dt^0
+  cudaMemsetAsync(c->dtbits, 0x7f, sizeof(unsigned long long), s);
+  cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);  // simulated time of this run
+  Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+  for (int n = 0; n < nsteps; ++n) {
+    prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, s); });
+    step_body<T>(c, U, c->cfg.recon);
+    prof(c, MHD_STAGE_PRIM,
+         [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });  // floors, W^{n+1}, next dt
+  }
+  return cuda_status();
+}
+
+template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  mhd::launch_set_dt(c->scal, dt, s);
+  Launch<T>::prim(g, U, as<T>(c->W), nullptr, c->flags, nullptr, s);
+  step_body<T>(c, U, c->cfg.recon);
+  Launch<T>::prim(g, U, as<T>(c->W), nullptr, c->flags, c->floors, s);
+  return cuda_status();
+}
+
+// ---- stage entry points ---------------------------------------------------
+template <class T> int stage_prims(mhd_ctx* c, const double* U, double* Wout) {
+  Launch<T>::prim(c->g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, c->stream);
+  Launch<T>::widen(as<T>(c->W), Wout, 8 * c->g.N, c->stream);
+  return cuda_status();
+}
+
+template <class T> int stage_fluxes(mhd_ctx* c, const double* U, int recon, double* Fout) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  Launch<T>::prim(g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, s);
+  if (recon == MHD_RECON_PCM) {
+    Launch<T>::flux_pcm(g, as<T>(c->W), U, as<T>(c->F), s);
+  } else {
+    Launch<T>::narrow(U + 5 * g.N, as<T>(c->Bh), 3 * g.N, s);
+    for (int a = 0; a < 3; ++a) {
+      Launch<T>::recon(g, recon, a, as<T>(c->W), as<T>(c->WL), as<T>(c->WR), s);
+      Launch<T>::flux_hlld(g, a, as<T>(c->WL), as<T>(c->WR), as<T>(c->Bh), as<T>(c->F), s);
+    }
+  }
+  Launch<T>::widen(as<T>(c->F), Fout, 21 * g.N, s);
+  return cuda_status();
+}
+
+template <class T> int stage_edges(mhd_ctx* c, const double* U, const double* Fin, double* Eout) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  Launch<T>::prim(g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, s);
+  Launch<T>::narrow(Fin, as<T>(c->F), 21 * g.N, s);
+  Launch<T>::emf(g, as<T>(c->W), as<T>(c->F), as<T>(c->E), s);
+  Launch<T>::widen(as<T>(c->E), Eout, 3 * g.N, s);
+  return cuda_status();
+}
+
+template <class T> int stage_recon(mhd_ctx* c, const double* U, int axis, int recon, double* WL, double* WR) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  Launch<T>::prim(g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, s);
+  Launch<T>::recon(g, recon, axis, as<T>(c->W), as<T>(c->WL), as<T>(c->WR), s);
+  Launch<T>::widen(as<T>(c->WL), WL, 7 * g.N, s);
+  Launch<T>::widen(as<T>(c->WR), WR, 7 * g.N, s);
+  return cuda_status();
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
+  int st = check_cfg(cfg);
+  if (st != MHD_OK) return st;
+  if (!bytes) return MHD_ERR_ARG;
+  *bytes = layout_of(*cfg).total;
+  return MHD_OK;
+}
+
+int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
+  if (!out) return MHD_ERR_ARG;
+  *out = nullptr;
+  int st = check_cfg(cfg);
+  if (st != MHD_OK) return st;
+  mhd_ctx* c = new (std::nothrow) mhd_ctx();
+  if (!c) return MHD_ERR_OOM;
+  c->cfg = *cfg;
+  c->g.n[0] = cfg->nx;
+  c->g.n[1] = cfg->ny;
+  c->g.n[2] = cfg->nz;
+  c->g.N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  c->g.d[0] = cfg->dx;
+  c->g.d[1] = cfg->dy;
+  c->g.d[2] = cfg->dz;
+  c->g.gamma = cfg->gamma;
+  c->g.rho_floor = cfg->rho_floor;
+  c->g.p_floor = cfg->p_floor;
+  c->g.cfl = cfg->cfl;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ts = cfg->precision == MHD_FP32_BULK ? 4 : 8;
+  const Layout L = layout_of(*cfg);
+  c->ws_bytes = L.total;
+  cudaGetLastError();
+  if (cudaMalloc(&c->ws, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MHD_ERR_OOM;
+  }
+  char* b = static_cast<char*>(c->ws);
+  c->W = b + L.W;
+  c->F = b + L.F;
+  c->E = b + L.E;
+  c->WL = b + L.WL;
+  c->WR = b + L.WR;
+  c->Bh = b + L.Bh;
+  c->scal = reinterpret_cast<double*>(b + L.scal);
+  c->dtbits = reinterpret_cast<unsigned long long*>(b + L.dtbits);
+  c->floors = reinterpret_cast<unsigned long long*>(b + L.floors);
+  c->flags = reinterpret_cast<unsigned*>(b + L.flags);
+  c->red = reinterpret_cast<double*>(b + L.red);
+  c->red_count = red_blocks(c->g.N);
+  cudaMemsetAsync(c->ws, 0, L.total, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return MHD_ERR_CUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+void mhd_destroy(mhd_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->host_state) cudaFree(c->host_state);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int mhd_profile_enable(mhd_ctx* c, int on) {
+  if (!c) return MHD_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return MHD_ERR_CUDA;
+  c->prof_on = on ? 1 : 0;
+  c->prof.clear();
+  c->ev_used = 0;
+  return MHD_OK;
+}
+
+int mhd_profile_read(mhd_ctx* c, double ms[MHD_NUM_STAGES], long long launches[MHD_NUM_STAGES]) {
+  if (!c || !ms || !launches) return MHD_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return MHD_ERR_CUDA;
+  for (int i = 0; i < MHD_NUM_STAGES; ++i) {
+    ms[i] = 0;
+    launches[i] = 0;
+  }
+  for (const ProfRec& r : c->prof) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return MHD_ERR_CUDA;
+    ms[r.stage] += t;
+    launches[r.stage] += 1;
+  }
+  c->prof.clear();
+  c->ev_used = 0;
+  return MHD_OK;
+}
+
+const char* mhd_stage_name(int stage) {
+  static const char* names[MHD_NUM_STAGES] = {"prim", "flux_pcm", "emf", "update_half", "recon",
+                                              "flux_hlld", "update_full", "dt"};
+  if (stage < 0 || stage >= MHD_NUM_STAGES) return "unknown";
+  return names[stage];
+}
+
+int mhd_step(mhd_ctx* c, double* U, double dt) {
+  if (!c || !U) return MHD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
+  return c->cfg.precision == MHD_FP32_BULK ? one_step<float>(c, U, dt) : one_step<double>(c, U, dt);
+}
+
+int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {
+  if (!c || !U || nsteps < 0) return MHD_ERR_ARG;
+  if (nsteps == 0) return MHD_OK;
+  return c->cfg.precision == MHD_FP32_BULK ? run_steps<float>(c, U, nsteps, dt_dev)
+                                            : run_steps<double>(c, U, nsteps, dt_dev);
+}
+
+int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
+  if (!c || !U || !dt_host) return MHD_ERR_ARG;
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->dtbits, 0x7f, sizeof(unsigned long long), s);
+  double* Um = const_cast<double*>(U);  // k_prim writes U only when floors are requested
+  if (c->cfg.precision == MHD_FP32_BULK)
+    Launch<float>::prim(c->g, Um, as<float>(c->W), c->dtbits, c->flags, nullptr, s);
+  else
+    Launch<double>::prim(c->g, Um, as<double>(c->W), c->dtbits, c->flags, nullptr, s);
+  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, s);
+  double v = 0;
+  unsigned fl = 0;
+  if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  *dt_host = v;
+  if (fl & 1u) return MHD_ERR_NONFINITE;
+  if (!(v > 0.0) || !std::isfinite(v)) return MHD_ERR_DT;
+  return MHD_OK;
+}
+
+int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
+  if (!c || !U_host || nsteps < 0) return MHD_ERR_ARG;
+  const size_t bytes = 8 * (size_t)c->g.N * sizeof(double);
+  if (!c->host_state) {
+    if (cudaMalloc(&c->host_state, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->host_state = nullptr;
+      return MHD_ERR_OOM;
+    }
+  }
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
+  int st = mhd_run(c, c->host_state, nsteps, nullptr);
+  if (st != MHD_OK) return st;
+  if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  double t = 0;
+  if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (t_host) *t_host = t;
+  return mhd_status(c, nullptr);
+}
+
+int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {
+  if (!c || !U_n || !gU_np1 || !gU_n) return MHD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
+  return MHD_ERR_ARG;  // not built in this configuration
+}
+
+int mhd_status(mhd_ctx* c, long long counts[2]) {
+  if (!c) return MHD_ERR_ARG;
+  unsigned fl = 0;
+  unsigned long long fc[2] = {0, 0};
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaMemcpyAsync(fc, c->floors, sizeof(fc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  cudaMemsetAsync(c->flags, 0, sizeof(unsigned), s);
+  cudaMemsetAsync(c->floors, 0, 2 * sizeof(unsigned long long), s);
+  if (counts) {
+    counts[0] = (long long)fc[0];
+    counts[1] = (long long)fc[1];
+  }
+  if (fl & 1u) return MHD_ERR_NONFINITE;
+  if (fl & 2u) return MHD_ERR_DT;
+  return MHD_OK;
+}
+
+const char* mhd_strerror(int code) {
+  switch (code) {
+    case MHD_OK: return "ok";
+    case MHD_ERR_ARG: return "invalid argument";
+    case MHD_ERR_CUDA: return "CUDA runtime error";
+    case MHD_ERR_OOM: return "out of device memory";
+    case MHD_ERR_NONFINITE: return "non-finite value or non-positive density in the state";
+    case MHD_ERR_DT: return "time step not positive or not finite";
+    default: return "unknown status";
+  }
+}
+
+int mhd_diagnostics(mhd_ctx* c, const double* U, double* divb_max, double totals[8]) {
+  if (!c || !U || !divb_max || !totals) return MHD_ERR_ARG;
+  cudaStream_t s = c->stream;
+  mhd::launch_diagnostics(c->g, U, c->red, (int)c->red_count, s);
+  double out[9];
+  if (cudaMemcpyAsync(out, c->red, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  *divb_max = out[8];
+  for (int f = 0; f < 8; ++f) totals[f] = out[f];
+  return MHD_OK;
+}
+
+
+int mhd_stage_primitives(mhd_ctx* c, const double* U, double* W) {
+  if (!c || !U || !W) return MHD_ERR_ARG;
+  return c->cfg.precision == MHD_FP32_BULK ? stage_prims<float>(c, U, W) : stage_prims<double>(c, U, W);
+}
+
+
+
+int mhd_stage_fluxes(mhd_ctx* c, const double* U, int recon, double* F) {
+  if (!c || !U || !F || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
+  return c->cfg.precision == MHD_FP32_BULK ? stage_fluxes<float>(c, U, recon, F) : stage_fluxes<double>(c, U, recon, F);
+}
+
+
+
+int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
+  if (!c || !U || !F || !E) return MHD_ERR_ARG;
+  return c->cfg.precision == MHD_FP32_BULK ? stage_edges<float>(c, U, F, E) : stage_edges<double>(c, U, F, E);
+}
+
+
+
+int mhd_stage_recon(mhd_ctx* c, const double* U, int axis, int recon, double* WL, double* WR) {
+  if (!c || !U || !WL || !WR || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
+    return MHD_ERR_ARG;
+  return c->cfg.precision == MHD_FP32_BULK ? stage_recon<float>(c, U, axis, recon, WL, WR)
+                                            : stage_recon<double>(c, U, axis, recon, WL, WR);
+}
+
+
+}  // extern "C"

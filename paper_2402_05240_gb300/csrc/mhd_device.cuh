@@ -1,0 +1,401 @@
+// mhd_device.cuh -- device arithmetic of the VL+CT ideal-MHD step (sm_103a).
+//
+// Templated on the compute type T (double for the FP64 step, float for the
+// FP32-bulk step).  Pressure recovery from the conserved state is always done
+// in double (the cancellation E - KE - B^2/2 sets the pressure floor).
+//
+// Method: Caddy & Schneider (arXiv:2402.05240) Sec. 2.1-2.2; HLLD of Miyoshi
+// & Kusano (2005); primitive eigenvectors in the normalisation of Stone et
+// al. (2008, App. A) with the left eigenvectors in closed form; PPM limiters
+// of Colella & Sekora (2008) and McCorquodale & Colella (2011) applied in the
+// characteristic variables (Felker & Stone 2018).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhd_launch.h"
+
+namespace mhd {
+
+// ------------------------------------------------------------ grid helpers --
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ long long cidx(const Grid& g, int i, int j, int k) {
+  return ((long long)k * g.n[1] + j) * g.n[0] + i;
+}
+
+// index of cell (i,j,k) + s e_a, |s| < n[a]
+template <int A>
+__device__ __forceinline__ long long nb(const Grid& g, int i, int j, int k, int s) {
+  if (A == 0) return cidx(g, wrapi(i + s, g.n[0]), j, k);
+  if (A == 1) return cidx(g, i, wrapi(j + s, g.n[1]), k);
+  return cidx(g, i, j, wrapi(k + s, g.n[2]));
+}
+
+template <class T> __device__ __forceinline__ T tsqrt(T x);
+template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+
+template <class T> struct Eps;
+template <> struct Eps<double> { static constexpr double hlld = 1e-8; };
+template <> struct Eps<float> { static constexpr float hlld = 1e-4f; };
+
+// ------------------------------------------------- primitives (Sec. 2.2.1) --
+// Cell primitives: rho, v, P (pressure recovered in double) and B_cc, the mean
+// of the two faces of each component.
+struct PrimD {
+  double rho, v[3], p, b[3];
+};
+
+// ----------------------------------------------------- fast speed (Eq. c_f) --
+// c_f^2 = (a2 + b2 + sqrt((a2 - b2)^2 + 4 a2 bt2)) / 2 with a2 = gamma P / rho,
+// b2 = |B|^2 / rho, bt2 = |B_t|^2 / rho: the printed discriminant
+// (gamma P + B^2)^2 - 4 gamma P B_l^2 (over rho^2) as a sum of non-negative terms.
+template <class T>
+__device__ __forceinline__ T fast_speed(T gamma, T rho, T p, T bl, T bt1, T bt2) {
+  T ir = T(1) / rho;
+  T a2 = gamma * p * ir;
+  T t2 = (bt1 * bt1 + bt2 * bt2) * ir;
+  T b2 = bl * bl * ir + t2;
+  T dd = a2 - b2;
+  return tsqrt<T>(T(0.5) * (a2 + b2 + tsqrt<T>(dd * dd + T(4) * a2 * t2)));
+}
+
+// ------------------------------------------------------------------- HLLD --
+// Miyoshi & Kusano (2005) in the solver frame; w = (rho, u, v, w, P, By, Bz),
+// bn = longitudinal face field.  Outer speeds S_L = min(u) - max(c_f),
+// S_R = max(u) + max(c_f); degenerate star / double-star states below
+// Eps<T>::hlld * p_T*; flux selection with ties to the left.
+template <class T>
+__device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T* f) {
+  const T bn2 = bn * bn;
+  const T gm1i = T(1) / (gamma - T(1));
+  // left / right conserved energy, total pressure, physical flux
+  T eL, eR, ptL, ptR;
+  {
+    T bb = bn2 + wl[5] * wl[5] + wl[6] * wl[6];
+    eL = wl[4] * gm1i + T(0.5) * wl[0] * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) + T(0.5) * bb;
+    ptL = wl[4] + T(0.5) * bb;
+    bb = bn2 + wr[5] * wr[5] + wr[6] * wr[6];
+    eR = wr[4] * gm1i + T(0.5) * wr[0] * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) + T(0.5) * bb;
+    ptR = wr[4] + T(0.5) * bb;
+  }
+  const T cfL = fast_speed<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
+  const T cfR = fast_speed<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
+  const T cmax = fmax(cfL, cfR);
+  const T SL = fmin(wl[1], wr[1]) - cmax;
+  const T SR = fmax(wl[1], wr[1]) + cmax;
+
+  auto phys = [&](const T* w, T e, T pt, T* F) {
+    const T mu = w[0] * w[1];
+    F[0] = mu;
+    F[1] = mu * w[1] + pt - bn2;
+    F[2] = mu * w[2] - bn * w[5];
+    F[3] = mu * w[3] - bn * w[6];
+    F[4] = (e + pt) * w[1] - bn * (w[1] * bn + w[2] * w[5] + w[3] * w[6]);
+    F[5] = w[5] * w[1] - bn * w[2];
+    F[6] = w[6] * w[1] - bn * w[3];
+  };
+  if (SL >= T(0)) {
+    phys(wl, eL, ptL, f);
+    return;
+  }
+  if (SR <= T(0)) {
+    phys(wr, eR, ptR, f);
+    return;
+  }
+  const T dL = SL - wl[1], dR = SR - wr[1];
+  const T rdL = wl[0] * dL, rdR = wr[0] * dR;
+  const T iden = T(1) / (rdR - rdL);
+  const T SM = (rdR * wr[1] - rdL * wl[1] - ptR + ptL) * iden;
+  const T pts = (rdR * ptL - rdL * ptR + rdL * rdR * (wr[1] - wl[1])) * iden;
+
+  // single-star states of one side: returns rho*, v*, w*, By*, Bz*, E*
+  struct Star {
+    T r, v, w, by, bz, e, sq;
+  };
+  auto star = [&](const T* w, T e, T pt, T S, T d, T rd) {
+    Star s;
+    const T iSM = T(1) / (S - SM);
+    s.r = rd * iSM;
+    const T D = rd * (S - SM) - bn2;
+    if (fabs(D) < Eps<T>::hlld * pts) {
+      s.v = w[2];
+      s.w = w[3];
+      s.by = w[5];
+      s.bz = w[6];
+    } else {
+      const T iD = T(1) / D;
+      const T t = bn * (SM - w[1]) * iD;
+      s.v = w[2] - w[5] * t;
+      s.w = w[3] - w[6] * t;
+      const T q = (rd * d - bn2) * iD;
+      s.by = w[5] * q;
+      s.bz = w[6] * q;
+    }
+    const T vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
+    const T vbs = SM * bn + s.v * s.by + s.w * s.bz;
+    s.e = (d * e - pt * w[1] + pts * SM + bn * (vb - vbs)) * iSM;
+    s.sq = tsqrt<T>(s.r);
+    return s;
+  };
+  const Star sL = star(wl, eL, ptL, SL, dL, rdL);
+  const Star sR = star(wr, eR, ptR, SR, dR, rdR);
+
+  // double-star (rotational) states
+  T SsL = SM, SsR = SM;
+  T vss, wss, byss, bzss, essL, essR;
+  const bool dbl = !(T(0.5) * bn2 < Eps<T>::hlld * pts);
+  if (dbl) {
+    const T sg = bn > T(0) ? T(1) : T(-1);
+    const T abn = fabs(bn);
+    SsL = SM - abn / sL.sq;
+    SsR = SM + abn / sR.sq;
+    const T inv = T(1) / (sL.sq + sR.sq);
+    vss = (sL.sq * sL.v + sR.sq * sR.v + (sR.by - sL.by) * sg) * inv;
+    wss = (sL.sq * sL.w + sR.sq * sR.w + (sR.bz - sL.bz) * sg) * inv;
+    byss = (sL.sq * sR.by + sR.sq * sL.by + sL.sq * sR.sq * (sR.v - sL.v) * sg) * inv;
+    bzss = (sL.sq * sR.bz + sR.sq * sL.bz + sL.sq * sR.sq * (sR.w - sL.w) * sg) * inv;
+    const T vbss = SM * bn + vss * byss + wss * bzss;
+    essL = sL.e - sL.sq * (SM * bn + sL.v * sL.by + sL.w * sL.bz - vbss) * sg;
+    essR = sR.e + sR.sq * (SM * bn + sR.v * sR.by + sR.w * sR.bz - vbss) * sg;
+  }
+  // select the region containing x/t = 0
+  const bool left = SM >= T(0);
+  const T* w = left ? wl : wr;
+  const Star& s = left ? sL : sR;
+  const T S = left ? SL : SR;
+  T F[7];
+  phys(w, left ? eL : eR, left ? ptL : ptR, F);
+  const T U0[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], left ? eL : eR, w[5], w[6]};
+  const T Us[7] = {s.r, s.r * SM, s.r * s.v, s.r * s.w, s.e, s.by, s.bz};
+  // F* = F + S (U* - U)
+  for (int q = 0; q < 7; ++q) f[q] = F[q] + S * (Us[q] - U0[q]);
+  const T Ss = left ? SsL : SsR;
+  const bool inner = left ? (SsL < T(0)) : (SsR >= T(0));
+  if (dbl && inner) {
+    const T Uss[7] = {s.r, s.r * SM, s.r * vss, s.r * wss, left ? essL : essR, byss, bzss};
+    for (int q = 0; q < 7; ++q) f[q] = f[q] + Ss * (Uss[q] - Us[q]);
+  }
+}
+
+// ------------------------------------------------ characteristic projection --
+// Primitive eigen-system (rho, u, v, w, P, B_t1, B_t2) of one cell with its
+// cell-centred longitudinal field bn.  Waves ordered u-cf, u-ca, u-cs, u,
+// u+cs, u+ca, u+cf.  beta = (1,1)/sqrt2 for B_t = 0; alpha_f = 1, alpha_s = 0
+// when cf2 = cs2; S = sgn(bn) with sgn(0) = +1.  The left eigenvectors are the
+// closed-form inverse of the right ones (rows scaled by 1/(2 a^2) for the
+// magnetosonic waves, 1/2 for the Alfven waves).
+template <class T> struct Eig {
+  T rho, sr, isr, a, a2, ia2, af, as, cf, cs, Qf, Qs, Af, As, b1, b2, sg;
+};
+
+template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w, T bn, Eig<T>& E) {
+  E.rho = w[0];
+  const T ir = T(1) / w[0];
+  E.a2 = gamma * w[4] * ir;
+  E.ia2 = T(1) / E.a2;
+  const T ca2 = bn * bn * ir;
+  const T bt2r = w[5] * w[5] + w[6] * w[6];
+  const T bt2 = bt2r * ir;
+  const T b2 = ca2 + bt2;
+  const T D = E.a2 - b2;
+  const T sd = tsqrt<T>(D * D + T(4) * E.a2 * bt2);
+  const T cf2 = T(0.5) * (E.a2 + b2 + sd);
+  const T cs2 = E.a2 * ca2 / cf2;
+  E.cf = tsqrt<T>(cf2);
+  E.cs = tsqrt<T>(cs2);
+  if (sd == T(0)) {
+    E.af = T(1);
+    E.as = T(0);
+  } else if (D >= T(0)) {
+    E.af = tsqrt<T>((sd + D) / (T(2) * sd));
+    E.as = tsqrt<T>(T(2) * E.a2 * bt2 / (sd * (sd + D)));
+  } else {
+    E.af = tsqrt<T>(T(2) * E.a2 * bt2 / (sd * (sd - D)));
+    E.as = tsqrt<T>((sd - D) / (T(2) * sd));
+  }
+  const T bt = tsqrt<T>(bt2r);
+  if (bt == T(0)) {
+    E.b1 = T(0.70710678118654752440);
+    E.b2 = T(0.70710678118654752440);
+  } else {
+    const T ibt = T(1) / bt;
+    E.b1 = w[5] * ibt;
+    E.b2 = w[6] * ibt;
+  }
+  E.sg = bn >= T(0) ? T(1) : T(-1);
+  E.sr = tsqrt<T>(w[0]);
+  E.isr = T(1) / E.sr;
+  E.a = tsqrt<T>(E.a2);
+  const T a = E.a;
+  E.Qf = E.cf * E.af * E.sg;
+  E.Qs = E.cs * E.as * E.sg;
+  E.Af = a * E.af * E.sr;
+  E.As = a * E.as * E.sr;
+}
+
+// characteristic amplitudes q = L dw
+template <class T> __device__ __forceinline__ void eig_left(const Eig<T>& E, const T* dw, T* q) {
+  const T n = T(0.5) * E.ia2;
+  const T ir = T(1) / E.rho;
+  const T bv = E.b1 * dw[2] + E.b2 * dw[3];
+  const T bb = (E.b1 * dw[5] + E.b2 * dw[6]) * E.isr;
+  const T sa = E.a;
+  const T Xf = E.af * dw[4] * ir + E.as * sa * bb;
+  const T Yf = -E.af * E.cf * dw[1] + E.Qs * bv;
+  const T Xs = E.as * dw[4] * ir - E.af * sa * bb;
+  const T Ys = -E.as * E.cs * dw[1] - E.Qf * bv;
+  const T Z = T(0.5) * (-E.b2 * dw[2] + E.b1 * dw[3]);
+  const T Zb = T(0.5) * E.sg * (-E.b2 * dw[5] + E.b1 * dw[6]) * E.isr;
+  q[0] = n * (Xf + Yf);
+  q[1] = Z + Zb;
+  q[2] = n * (Xs + Ys);
+  q[3] = dw[0] - dw[4] * E.ia2;
+  q[4] = n * (Xs - Ys);
+  q[5] = Z - Zb;
+  q[6] = n * (Xf - Yf);
+}
+
+// primitive increments dw = R q
+template <class T> __device__ __forceinline__ void eig_right(const Eig<T>& E, const T* q, T* dw) {
+  const T fp = q[0] + q[6], fm = q[0] - q[6];
+  const T sp = q[2] + q[4], sm = q[2] - q[4];
+  const T ap = q[1] + q[5], am = q[1] - q[5];
+  const T cfa = E.cf * E.af, csa = E.cs * E.as;
+  dw[0] = E.rho * (E.af * fp + E.as * sp) + q[3];
+  dw[1] = -cfa * fm - csa * sm;
+  dw[2] = E.b1 * (E.Qs * fm - E.Qf * sm) - E.b2 * ap;
+  dw[3] = E.b2 * (E.Qs * fm - E.Qf * sm) + E.b1 * ap;
+  dw[4] = E.rho * E.a2 * (E.af * fp + E.as * sp);
+  const T ms = E.As * fp - E.Af * sp;
+  const T ssr = E.sg * E.sr * am;
+  dw[5] = E.b1 * ms - E.b2 * ssr;
+  dw[6] = E.b2 * ms + E.b1 * ssr;
+}
+
+template <class T> __device__ __forceinline__ T sgn0(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+
+// ------------------------------------------------------- PLMC (Sec. 2.2.6) --
+// wm, w0, wp: primitive 7-vectors of cells i-1, i, i+1; bn: cell-centred
+// longitudinal field of cell i.  Outputs W_{L,i+1/2} and W_{R,i-1/2}.
+template <class T>
+__device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T* wp, T bn, T* wl, T* wr) {
+  T dL[7], dR[7], dC[7], dG[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    dL[q] = w0[q] - wm[q];
+    dR[q] = wp[q] - w0[q];
+    dC[q] = T(0.5) * (wp[q] - wm[q]);
+    const T pr = dL[q] * dR[q];
+    dG[q] = pr > T(0) ? T(2) * pr / (dL[q] + dR[q]) : T(0);
+  }
+  Eig<T> E;
+  eig_build<T>(gamma, w0, bn, E);
+  T aL[7], aR[7], aC[7], aG[7], am[7], dW[7];
+  eig_left<T>(E, dL, aL);
+  eig_left<T>(E, dR, aR);
+  eig_left<T>(E, dC, aC);
+  eig_left<T>(E, dG, aG);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    if (aL[q] * aR[q] > T(0)) {
+      const T m = fmin(fmin(T(2) * fabs(aL[q]), T(2) * fabs(aR[q])), fmin(fabs(aC[q]), fabs(aG[q])));
+      am[q] = sgn0<T>(aC[q]) * m;
+    } else {
+      am[q] = T(0);
+    }
+  }
+  eig_right<T>(E, am, dW);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    wl[q] = w0[q] + T(0.5) * dW[q];
+    wr[q] = w0[q] - T(0.5) * dW[q];
+  }
+}
+
+// ------------------------------------------------------- PPMC (Sec. 2.2.6) --
+// Fourth-order interface values, Colella & Sekora (2008) interface limiter,
+// McCorquodale & Colella (2011) cell limiter (C = 1.25), in characteristic
+// deviations q_m - q_0 = L (W_m - W_0) of cell i.
+template <class T> __device__ __forceinline__ T d2lim3(T x, T y, T z) {
+  const T sx = sgn0<T>(x);
+  if (sx != T(0) && sx == sgn0<T>(y) && sx == sgn0<T>(z))
+    return sx * fmin(fabs(x), fmin(T(1.25) * fabs(y), T(1.25) * fabs(z)));
+  return T(0);
+}
+template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
+  const T sx = sgn0<T>(x);
+  if (sx != T(0) && sx == sgn0<T>(y) && sx == sgn0<T>(z) && sx == sgn0<T>(t))
+    return sx * fmin(fmin(fabs(x), T(1.25) * fabs(y)), fmin(T(1.25) * fabs(z), T(1.25) * fabs(t)));
+  return T(0);
+}
+
+// q[0..4] = characteristic deviations of cells i-2..i+2 from cell i (q[2] = 0);
+// returns the limited deviations of the two interface values.
+template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T& qp) {
+  const T c7 = T(7) / T(12), c1 = T(1) / T(12);
+  qm = c7 * (q[1] + q[2]) - c1 * (q[0] + q[3]);
+  qp = c7 * (q[2] + q[3]) - c1 * (q[1] + q[4]);
+  const T d2m1 = q[0] - T(2) * q[1] + q[2];
+  const T d20 = q[1] - T(2) * q[2] + q[3];
+  const T d2p1 = q[2] - T(2) * q[3] + q[4];
+  if ((qm - q[1]) * (q[2] - qm) < T(0)) {
+    const T d2c = T(3) * (q[1] - T(2) * qm + q[2]);
+    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) / T(6);
+  }
+  if ((qp - q[2]) * (q[3] - qp) < T(0)) {
+    const T d2c = T(3) * (q[2] - T(2) * qp + q[3]);
+    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) / T(6);
+  }
+  const T dqm = q[2] - qm, dqp = qp - q[2];
+  if (dqm * dqp <= T(0) || (q[2] - q[1]) * (q[3] - q[2]) <= T(0)) {
+    const T d2f = T(6) * (qm - T(2) * q[2] + qp);
+    T r = T(0);
+    if (d2f != T(0)) r = d2lim4<T>(d2f, d2m1, d20, d2p1) / d2f;
+    qm = q[2] - r * dqm;
+    qp = q[2] + r * dqp;
+  } else {
+    if (fabs(dqm) >= T(2) * fabs(dqp)) qm = q[2] - T(2) * dqp;
+    if (fabs(dqp) >= T(2) * fabs(dqm)) qp = q[2] + T(2) * dqm;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ppmc(T gamma, const T (*w)[7], T bn, T* wl, T* wr) {
+  Eig<T> E;
+  eig_build<T>(gamma, w[2], bn, E);
+  T qs[5][7];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    if (m == 2) {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) qs[2][c] = T(0);
+      continue;
+    }
+    T d[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) d[c] = w[m][c] - w[2][c];
+    eig_left<T>(E, d, qs[m]);
+  }
+  T dm[7], dp[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[3][c], qs[4][c]};
+    T qm, qp;
+    ppm_one<T>(col, qm, qp);
+    dm[c] = qm;
+    dp[c] = qp;
+  }
+  T Wm[7], Wp[7];
+  eig_right<T>(E, dm, Wm);
+  eig_right<T>(E, dp, Wp);
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    wl[c] = w[2][c] + Wp[c];
+    wr[c] = w[2][c] + Wm[c];
+  }
+}
+
+}  // namespace mhd

@@ -1,0 +1,543 @@
+// mhd_kernels.cuh -- the kernels of one VL+CT step and their launchers.
+//
+// Schedule of one step (Caddy & Schneider, arXiv:2402.05240, Sec. 2.2):
+//   k_prim          Step 1: primitives W^n (+ CFL dt min-reduction)
+//   k_flux_pcm      Steps 2-3: PCM states + HLLD on x, y, z faces
+//   k_emf           Step 4: edge electric fields (reference fields of W^n)
+//   k_update_half   Step 5: U^{n+1/2}, B^{n+1/2}; emits W^{n+1/2} and the
+//                   half-step face fields (the hydro U^{n+1/2} is never stored)
+//   k_recon<DIR>    Step 6: PLMC / PPMC interface states per axis
+//   k_flux_hlld     Step 7: HLLD on the reconstructed states
+//   k_emf           Step 8: edge fields with the half-step reference fields
+//   k_update_full   Step 9: U^{n+1}, B^{n+1} in place
+//   k_prim (floors) end of step: floors, W^{n+1} and the dt of the next step
+// Periodic boundaries are wrap-around indices inside every kernel; no ghost
+// cells exist.  Threads map to cells with x fastest (coalesced rows).
+#pragma once
+
+#include "mhd_device.cuh"
+
+namespace mhd {
+
+constexpr int BX = 32, BY = 4;
+
+struct CellIdx {
+  int i, j, k;
+  bool ok;
+};
+
+__device__ __forceinline__ CellIdx cell_of_thread(const Grid& g) {
+  CellIdx c;
+  c.i = blockIdx.x * BX + threadIdx.x;
+  c.j = blockIdx.y * BY + threadIdx.y;
+  c.k = blockIdx.z;
+  c.ok = c.i < g.n[0] && c.j < g.n[1];
+  return c;
+}
+
+inline dim3 grid_of(const Grid& g) { return dim3((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, g.n[2]); }
+
+// positive doubles order like their bit patterns: min via integer atomicMin
+__device__ __forceinline__ void block_min_to(double v, unsigned long long* dst) {
+  __shared__ double red[BX * BY / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double m = red[0];
+    for (int w = 1; w < BX * BY / 32; ++w) m = fmin(m, red[w]);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    if (bits < *(volatile unsigned long long*)dst) atomicMin(dst, bits);
+  }
+}
+
+// crossing time min over l of d_l / (|v_l| + c_f,l) of one cell (Eq. dt)
+template <class T> __device__ __forceinline__ double cell_crossing(const Grid& g, const T* w8) {
+  double best = 1e300;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const T cf = fast_speed<T>(T(g.gamma), w8[0], w8[4], w8[5 + l], w8[5 + (l + 1) % 3], w8[5 + (l + 2) % 3]);
+    const T s = fabs(w8[1 + l]) + cf;
+    best = fmin(best, g.d[l] / (double)s);
+  }
+  return best;
+}
+
+// primitives from a double state of one cell (same arithmetic as the double-precision recovery)
+__device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, double m1, double m2, double e,
+                                           const double* b) {
+  PrimD w;
+  w.b[0] = b[0];
+  w.b[1] = b[1];
+  w.b[2] = b[2];
+  w.rho = fmax(r, g.rho_floor);
+  const double ir = 1.0 / w.rho;
+  w.v[0] = m0 * ir;
+  w.v[1] = m1 * ir;
+  w.v[2] = m2 * ir;
+  const double ke = 0.5 * (m0 * w.v[0] + m1 * w.v[1] + m2 * w.v[2]);
+  const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  w.p = fmax((g.gamma - 1.0) * (e - ke - me), g.p_floor);
+  return w;
+}
+
+template <class T>
+__device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
+  w8[0] = T(p.rho);
+  w8[1] = T(p.v[0]);
+  w8[2] = T(p.v[1]);
+  w8[3] = T(p.v[2]);
+  w8[4] = T(p.p);
+  w8[5] = T(p.b[0]);
+  w8[6] = T(p.b[1]);
+  w8[7] = T(p.b[2]);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
+}
+
+// ------------------------------------------------------------------ Step 1 --
+// Primitives W of a state, and optionally (floors != nullptr) the end-of-step
+// floors of the conserved state (D-12): rho < rho_floor is raised; if the
+// recovered P < p_floor, E is reset so that P = p_floor.  Only the cell's own
+// rho and E are written, so this is race-free in place.
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
+                                                 unsigned* flags, unsigned long long* floors) {
+  const CellIdx ci = cell_of_thread(g);
+  double cross = 1e300;
+  if (ci.ok) {
+    const int i = ci.i, j = ci.j, k = ci.k;
+    const long long c = cidx(g, i, j, k), N = g.N;
+    double b[3];
+    b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
+    b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
+    b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
+    double r = U[c], e = U[4 * N + c];
+    const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
+    if (!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) atomicOr(flags, 1u);
+    if (floors) {
+      if (r < g.rho_floor) {
+        r = g.rho_floor;
+        U[c] = r;
+        atomicAdd(&floors[0], 1ull);
+      }
+      const double ir = 1.0 / r;
+      const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
+      const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+      if ((g.gamma - 1.0) * (e - ke - me) < g.p_floor) {
+        e = g.p_floor / (g.gamma - 1.0) + ke + me;
+        U[4 * N + c] = e;
+        atomicAdd(&floors[1], 1ull);
+      }
+    }
+    const PrimD p = prim_core(g, r, m0, m1, m2, e, b);
+    T w8[8];
+    store_w<T>(g, W, c, p, w8);
+    if (dtbits) cross = cell_crossing<T>(g, w8);
+  }
+  if (dtbits) block_min_to(cross, dtbits);
+}
+
+// directional 7-vector (rho, v_n, v_t1, v_t2, P, B_t1, B_t2) of cell q
+template <int A, class T> __device__ __forceinline__ void load_dir(const T* __restrict__ W, long long N, long long q, T* w) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  w[0] = W[q];
+  w[1] = W[(1 + A) * N + q];
+  w[2] = W[(1 + B) * N + q];
+  w[3] = W[(1 + C) * N + q];
+  w[4] = W[4 * N + q];
+  w[5] = W[(5 + B) * N + q];
+  w[6] = W[(5 + C) * N + q];
+}
+
+// -------------------------------------------------------------- Steps 2-3 --
+template <class T, int A>
+__device__ __forceinline__ void pcm_face(const Grid& g, const T* __restrict__ W, const double* __restrict__ U,
+                                         T* __restrict__ F, int i, int j, int k) {
+  const long long N = g.N, c = cidx(g, i, j, k), cn = nb<A>(g, i, j, k, 1);
+  T wl[7], wr[7], f[7];
+  load_dir<A>(W, N, c, wl);
+  load_dir<A>(W, N, cn, wr);
+  hlld<T>(T(g.gamma), wl, wr, T(U[(5 + A) * N + c]), f);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, const T* __restrict__ W, const double* __restrict__ U,
+                                                     T* __restrict__ F) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  pcm_face<T, 0>(g, W, U, F, ci.i, ci.j, ci.k);
+  pcm_face<T, 1>(g, W, U, F, ci.i, ci.j, ci.k);
+  pcm_face<T, 2>(g, W, U, F, ci.i, ci.j, ci.k);
+}
+
+// ------------------------------------------------------------------ Step 6 --
+template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* w) {
+  w[0] = fmax(w[0], T(g.rho_floor));
+  w[4] = fmax(w[4], T(g.p_floor));
+}
+
+template <class T, int RECON, int A>
+__global__ void __launch_bounds__(BX* BY) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
+                                                  T* __restrict__ WR) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T wl[7], wr[7];
+  const T bn = W[(5 + A) * N + c];
+  if (RECON == 0) {
+    load_dir<A>(W, N, c, wl);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) wr[q] = wl[q];
+  } else if (RECON == 1) {
+    T wm[7], w0[7], wp[7];
+    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
+    load_dir<A>(W, N, c, w0);
+    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
+    plmc<T>(T(g.gamma), wm, w0, wp, bn, wl, wr);
+  } else {
+    T w[5][7];
+#pragma unroll
+    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
+    ppmc<T>(T(g.gamma), w, bn, wl, wr);
+  }
+  floor_face<T>(g, wl);
+  floor_face<T>(g, wr);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    WL[q * N + c] = wl[q];
+    WR[q * N + c] = wr[q];
+  }
+}
+
+// ------------------------------------------------------------------ Step 7 --
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
+                                                      const T* __restrict__ Bf, T* __restrict__ F) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k), cn = nb<A>(g, ci.i, ci.j, ci.k, 1);
+  T wl[7], wr[7], f[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    wl[q] = WL[q * N + c];
+    wr[q] = WR[q * N + cn];
+  }
+  hlld<T>(T(g.gamma), wl, wr, Bf[A * N + c], f);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+}
+
+// ------------------------------------------------------------ Steps 4, 8 --
+// Edge A of cell p at p + e_B/2 + e_C/2, (B, C) = (A+1, A+2): mean of the four
+// face fields plus the upwinded "face minus reference" slopes (Eq. emf-edge,
+// Eqs. emf-upwind-slope, emf-slope), upwinded by the sign of the mass flux of
+// the face the slope sits on (mean when it is exactly zero).
+template <class T> __device__ __forceinline__ T upwind(T m, T lo, T hi) {
+  return m > T(0) ? lo : (m < T(0) ? hi : T(0.5) * (lo + hi));
+}
+
+template <class T, int A>
+__device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, const T* __restrict__ F, int i,
+                                        int j, int k) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  const long long N = g.N;
+  int p[3] = {i, j, k};
+  int pb[3] = {i, j, k}, pc[3] = {i, j, k}, pbc[3] = {i, j, k};
+  pb[B] = wrapi(pb[B] + 1, g.n[B]);
+  pc[C] = wrapi(pc[C] + 1, g.n[C]);
+  pbc[B] = pb[B];
+  pbc[C] = pc[C];
+  const long long q00 = cidx(g, p[0], p[1], p[2]), qb = cidx(g, pb[0], pb[1], pb[2]);
+  const long long qc = cidx(g, pc[0], pc[1], pc[2]), qbc = cidx(g, pbc[0], pbc[1], pbc[2]);
+  const T* Fb = F + (long long)B * 7 * N;
+  const T* Fc = F + (long long)C * 7 * N;
+  auto ref = [&](long long q) { return -(W[(1 + B) * N + q] * W[(5 + C) * N + q] - W[(1 + C) * N + q] * W[(5 + B) * N + q]); };
+  const T bf0 = -Fb[5 * N + q00], bfc = -Fb[5 * N + qc];
+  const T cf0 = Fc[6 * N + q00], cfb = Fc[6 * N + qb];
+  const T r00 = ref(q00), rb = ref(qb), rc = ref(qc), rbc = ref(qbc);
+  const T avg = T(0.25) * (bfc + bf0 + cfb + cf0);
+  const T Dcp = upwind<T>(Fb[qc], cf0 - rc, cfb - rbc);
+  const T Dcm = upwind<T>(Fb[q00], cf0 - r00, cfb - rb);
+  const T Dbp = upwind<T>(Fc[qb], bf0 - rb, bfc - rbc);
+  const T Dbm = upwind<T>(Fc[q00], bf0 - r00, bfc - rc);
+  return avg + T(0.25) * (Dcp + Dcm + Dbp + Dbm);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_emf(Grid g, const T* __restrict__ W, const T* __restrict__ F,
+                                                T* __restrict__ E) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  E[c] = edge_field<T, 0>(g, W, F, ci.i, ci.j, ci.k);
+  E[N + c] = edge_field<T, 1>(g, W, F, ci.i, ci.j, ci.k);
+  E[2 * N + c] = edge_field<T, 2>(g, W, F, ci.i, ci.j, ci.k);
+}
+
+// ------------------------------------------------------------ Steps 5, 9 --
+// curl term of face A of cell (i,j,k): (E_C(p) - E_C(p-e_B))/d_B - (E_B(p) - E_B(p-e_C))/d_C.
+// EXACT: the edge values are widened to double before differencing, so the
+// discrete divergence of the update telescopes to double round-off whatever
+// the compute type (the FP32-bulk full update keeps div B at FP64 round-off).
+template <class T, bool EXACT, int A>
+__device__ __forceinline__ double face_curl(const Grid& g, const T* __restrict__ E, int i, int j, int k) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  const long long N = g.N, c = cidx(g, i, j, k);
+  const T* EB = E + (long long)B * N;
+  const T* EC = E + (long long)C * N;
+  if (EXACT) {
+    return ((double)EC[c] - (double)EC[nb<B>(g, i, j, k, -1)]) / g.d[B] -
+           ((double)EB[c] - (double)EB[nb<C>(g, i, j, k, -1)]) / g.d[C];
+  }
+  return (double)((EC[c] - EC[nb<B>(g, i, j, k, -1)]) / T(g.d[B]) - (EB[c] - EB[nb<C>(g, i, j, k, -1)]) / T(g.d[C]));
+}
+
+// solver-frame component of the global field f (0 rho, 1-3 m, 4 E) in the flux of axis a
+__device__ __forceinline__ int comp_of(int f, int a) {
+  return (f == 0 || f == 4) ? f : 1 + ((f - 1 - a + 3) % 3);
+}
+
+// new hydro state of one cell: U0 - h sum_a (F_a(p) - F_a(p - e_a)) / d_a.
+// EXACT: fluxes widened to double before differencing (a difference of two
+// floats is exact in double), so sums over the periodic box telescope to
+// double round-off: the FP32-bulk full update conserves rho, m, E like FP64.
+// Otherwise (FP32-bulk half step) the increment is formed in T and added to
+// the double state.
+template <class T, bool EXACT>
+__device__ __forceinline__ void hydro_update(const Grid& g, const double* __restrict__ U0, const T* __restrict__ F,
+                                             double h, int i, int j, int k, double* out5) {
+  const long long N = g.N, c = cidx(g, i, j, k);
+  const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    if (EXACT) {
+      double acc = U0[f * N + c];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
+        acc -= (h / g.d[a]) * ((double)Fa[c] - (double)Fa[cm[a]]);
+      }
+      out5[f] = acc;
+    } else {
+      T inc = T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
+        inc -= T(h / g.d[a]) * (Fa[c] - Fa[cm[a]]);
+      }
+      out5[f] = U0[f * N + c] + (double)inc;
+    }
+  }
+}
+
+// new face B_A of cell (ii, jj, kk) (upper face): B0 - h curl
+template <class T, bool EXACT, int A>
+__device__ __forceinline__ double face_update(const Grid& g, const double* __restrict__ U0, const T* __restrict__ E,
+                                              double h, int ii, int jj, int kk) {
+  const double cu = face_curl<T, EXACT, A>(g, E, ii, jj, kk);
+  return U0[(5 + A) * g.N + cidx(g, ii, jj, kk)] - h * cu;
+}
+
+// Step 5: W^{n+1/2} (from U^{n+1/2}) and the half-step faces; h = dt/2 (D-1)
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __restrict__ U0, const T* __restrict__ F,
+                                                        const T* __restrict__ E, const double* __restrict__ dtp,
+                                                        T* __restrict__ W, T* __restrict__ Bh, unsigned* flags) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const double h = 0.5 * dtp[0];
+  const long long N = g.N, c = cidx(g, i, j, k);
+  constexpr bool X = sizeof(T) == 8;  // FP64: double differences; FP32-bulk half step: T increments
+  double u5[5];
+  hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
+  const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
+  const double by = face_update<T, X, 1>(g, U0, E, h, i, j, k);
+  const double bz = face_update<T, X, 2>(g, U0, E, h, i, j, k);
+  const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
+  const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
+  const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
+  Bh[c] = T(bx);
+  Bh[N + c] = T(by);
+  Bh[2 * N + c] = T(bz);
+  const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
+  if (!(u5[0] > 0.0) || !isfinite(u5[4])) atomicOr(flags, 1u);
+  const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
+  T w8[8];
+  store_w<T>(g, W, c, p, w8);
+}
+
+// Step 9: U^{n+1} in place.  Each thread reads and writes only its own cell of
+// U (hydro fields and its three upper faces), so the update is race-free in
+// place; floors, W^{n+1} and the next dt follow in k_prim with floors on.
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_update_full(Grid g, double* U, const T* __restrict__ F,
+                                                        const T* __restrict__ E, const double* __restrict__ dtp) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const double h = dtp[0];
+  const long long N = g.N, c = cidx(g, i, j, k);
+  double u5[5];
+  hydro_update<T, true>(g, U, F, h, i, j, k, u5);
+  const double bx = face_update<T, true, 0>(g, U, E, h, i, j, k);
+  const double by = face_update<T, true, 1>(g, U, E, h, i, j, k);
+  const double bz = face_update<T, true, 2>(g, U, E, h, i, j, k);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) U[f * N + c] = u5[f];
+  U[5 * N + c] = bx;
+  U[6 * N + c] = by;
+  U[7 * N + c] = bz;
+}
+
+template <class T> __global__ void k_widen(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (double)src[q];
+}
+
+template <class T> __global__ void k_narrow(const double* __restrict__ src, T* __restrict__ dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (T)src[q];
+}
+
+#ifdef MHD_SCALAR_KERNELS
+// --------------------------------------------------------- small kernels --
+__global__ void k_set_dt(double* dt_cur, double value) { dt_cur[0] = value; }
+
+// dt = cfl * min crossing; records it and re-arms the reduction word
+__global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int s,
+                            unsigned* flags) {
+  const double m = __longlong_as_double((long long)dtbits[0]);
+  const double dt = cfl * m;
+  if (!(dt > 0.0) || !isfinite(dt)) atomicOr(flags, 2u);
+  dt_cur[0] = dt;
+  dt_cur[1] += dt;  // simulated time of the current run
+  if (dt_log) dt_log[s] = dt;
+  dtbits[0] = 0x7ff0000000000000ull;  // +inf
+}
+
+// ------------------------------------------------------------ diagnostics --
+// Per-block partial sums of the 8 fields and max |div B| over 1024 cells, then
+// one block combines the partials in a fixed order: deterministic results.
+constexpr int DIAG_T = 1024;
+
+__global__ void __launch_bounds__(DIAG_T) k_diag_partial(Grid g, const double* __restrict__ U, double* red, int nblk) {
+  __shared__ double sh[DIAG_T / 32][9];
+  const long long N = g.N;
+  const long long c = (long long)blockIdx.x * DIAG_T + threadIdx.x;
+  double v[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) v[f] = 0.0;
+  if (c < N) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((long long)g.n[0] * g.n[1]));
+#pragma unroll
+    for (int f = 0; f < 8; ++f) v[f] = U[f * N + c];
+    const double dv = (U[5 * N + c] - U[5 * N + nb<0>(g, i, j, k, -1)]) / g.d[0] +
+                      (U[6 * N + c] - U[6 * N + nb<1>(g, i, j, k, -1)]) / g.d[1] +
+                      (U[7 * N + c] - U[7 * N + nb<2>(g, i, j, k, -1)]) / g.d[2];
+    v[8] = fabs(dv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int f = 0; f < 8; ++f) v[f] += __shfl_xor_sync(0xffffffffu, v[f], o);
+    v[8] = fmax(v[8], __shfl_xor_sync(0xffffffffu, v[8], o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int f = 0; f < 9; ++f) sh[w][f] = v[f];
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    const int f = threadIdx.x;
+    double a = sh[0][f];
+    for (int q = 1; q < DIAG_T / 32; ++q) a = (f == 8) ? fmax(a, sh[q][f]) : a + sh[q][f];
+    red[(long long)f * nblk + blockIdx.x] = a;
+  }
+}
+
+__global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, double* out, int nblk) {
+  __shared__ double sh[DIAG_T];
+  for (int f = 0; f < 9; ++f) {
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += DIAG_T) {
+      const double x = red_in[(long long)f * nblk + q];
+      a = (f == 8) ? fmax(a, x) : a + x;
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = DIAG_T / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] = (f == 8) ? fmax(sh[threadIdx.x], sh[threadIdx.x + o]) : sh[threadIdx.x] + sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = sh[0];
+    __syncthreads();
+  }
+}
+
+#endif  // MHD_SCALAR_KERNELS
+
+// --------------------------------------------------------------- launchers --
+
+template <class T>
+void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
+                   unsigned long long* floors, cudaStream_t s) {
+    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors);
+  }
+template <class T>
+void Launch<T>::flux_pcm(const Grid& g, const T* W, const double* U, T* F, cudaStream_t s) {
+    k_flux_pcm<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, U, F);
+  }
+template <class T>
+void Launch<T>::recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (rc == 0) {
+      if (a == 0) k_recon<T, 0, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 1) k_recon<T, 0, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 2) k_recon<T, 0, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
+    } else if (rc == 1) {
+      if (a == 0) k_recon<T, 1, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 1) k_recon<T, 1, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 2) k_recon<T, 1, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
+    } else {
+      if (a == 0) k_recon<T, 2, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 1) k_recon<T, 2, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 2) k_recon<T, 2, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
+    }
+  }
+template <class T>
+void Launch<T>::flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (a == 0) k_flux_hlld<T, 0><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+    if (a == 1) k_flux_hlld<T, 1><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+    if (a == 2) k_flux_hlld<T, 2><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+  }
+template <class T>
+void Launch<T>::emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s) {
+    k_emf<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, E);
+  }
+template <class T>
+void Launch<T>::update_half(const Grid& g, const double* U, const T* F, const T* E, const double* dtp, T* W, T* Bh,
+                          unsigned* flags, cudaStream_t s) {
+    k_update_half<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp, W, Bh, flags);
+  }
+template <class T>
+void Launch<T>::update_full(const Grid& g, double* U, const T* F, const T* E, const double* dtp, cudaStream_t s) {
+    k_update_full<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp);
+  }
+template <class T>
+void Launch<T>::widen(const T* src, double* dst, long long n, cudaStream_t s) {
+    k_widen<T><<<1216, 256, 0, s>>>(src, dst, n);
+  }
+template <class T>
+void Launch<T>::narrow(const double* src, T* dst, long long n, cudaStream_t s) {
+    k_narrow<T><<<1216, 256, 0, s>>>(src, dst, n);
+  }
+
+}  // namespace mhd

@@ -1,0 +1,40 @@
+// mhd_launch.h -- host-side declarations of the kernel launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mhd {
+
+struct Grid {
+  int n[3];          // nx, ny, nz
+  long long N;       // nx * ny * nz
+  double d[3];       // dx, dy, dz
+  double gamma;
+  double rho_floor, p_floor;
+  double cfl;
+};
+
+// Launchers of the step kernels for compute type T (double: FP64 step,
+// float: FP32-bulk step); all asynchronous on stream s.
+template <class T> struct Launch {
+  static void prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
+                   unsigned long long* floors, cudaStream_t s);
+  static void flux_pcm(const Grid& g, const T* W, const double* U, T* F, cudaStream_t s);
+  static void recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s);
+  static void flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s);
+  static void emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s);
+  static void update_half(const Grid& g, const double* U, const T* F, const T* E, const double* dtp, T* W, T* Bh,
+                          unsigned* flags, cudaStream_t s);
+  static void update_full(const Grid& g, double* U, const T* F, const T* E, const double* dtp, cudaStream_t s);
+  static void widen(const T* src, double* dst, long long n, cudaStream_t s);
+  static void narrow(const double* src, T* dst, long long n, cudaStream_t s);
+};
+
+void launch_set_dt(double* dt_cur, double value, cudaStream_t s);
+void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
+                      unsigned* flags, cudaStream_t s);
+
+// max |div B| and field sums of a state into red[0..8] (red holds 9 + 9 nb doubles)
+void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s);
+
+}  // namespace mhd

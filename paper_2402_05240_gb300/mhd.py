@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libmhd.so (include/mhd_api.h).
+
+Every function here marshals arguments and calls the C ABI of the same name;
+all numerical work runs in the library's CUDA kernels.  Importing this module
+raises if the library has not been built: there is no CPU fallback.
+
+State tensors are torch float64 CUDA tensors of shape [8, nz, ny, nx]
+(fields rho, mx, my, mz, E, Bx, By, Bz; face fields on upper faces).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MHD_OK = 0
+MHD_ERR_ARG = -1
+MHD_ERR_CUDA = -2
+MHD_ERR_OOM = -3
+MHD_ERR_NONFINITE = -4
+MHD_ERR_DT = -5
+
+RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
+PRECISION = {"fp64": 0, "fp32_bulk": 1}
+
+
+class mhd_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("recon", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
+
+
+def _load_library():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmhd.so not built ({path}); run paper_2402_05240_gb300.build.build() "
+                           "or __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    sig = {
+        "mhd_workspace_bytes": (ip, [ctypes.POINTER(mhd_config), ctypes.POINTER(ctypes.c_size_t)]),
+        "mhd_init": (ip, [ctypes.POINTER(vp), ctypes.POINTER(mhd_config), vp]),
+        "mhd_destroy": (None, [vp]),
+        "mhd_dt": (ip, [vp, vp, dp]),
+        "mhd_step": (ip, [vp, vp, ctypes.c_double]),
+        "mhd_run": (ip, [vp, vp, ip, vp]),
+        "mhd_run_host": (ip, [vp, vp, ip, dp]),
+        "mhd_adjoint_step": (ip, [vp, vp, ctypes.c_double, vp, vp]),
+        "mhd_diagnostics": (ip, [vp, vp, dp, dp]),
+        "mhd_status": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "mhd_strerror": (ctypes.c_char_p, [ip]),
+        "mhd_stage_primitives": (ip, [vp, vp, vp]),
+        "mhd_stage_fluxes": (ip, [vp, vp, ip, vp]),
+        "mhd_stage_edges": (ip, [vp, vp, vp, vp]),
+        "mhd_stage_recon": (ip, [vp, vp, ip, ip, vp, vp]),
+        "mhd_profile_enable": (ip, [vp, ip]),
+        "mhd_profile_read": (ip, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
+        "mhd_stage_name": (ctypes.c_char_p, [ip]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load_library()
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {LIB.mhd_strerror(code).decode()} ({code})")
+
+
+def _check(code, where):
+    if code != MHD_OK:
+        raise MHDError(code, where)
+
+
+def _ptr(t: torch.Tensor):
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous(), "float64 contiguous CUDA tensor expected"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- C ABI, same names --------------------------------------------------
+def mhd_workspace_bytes(cfg: mhd_config) -> int:
+    b = ctypes.c_size_t(0)
+    _check(LIB.mhd_workspace_bytes(ctypes.byref(cfg), ctypes.byref(b)), "mhd_workspace_bytes")
+    return b.value
+
+
+def mhd_init(cfg: mhd_config, stream=None):
+    ctx = ctypes.c_void_p(0)
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(LIB.mhd_init(ctypes.byref(ctx), ctypes.byref(cfg), s), "mhd_init")
+    return ctx
+
+
+def mhd_destroy(ctx):
+    LIB.mhd_destroy(ctx)
+
+
+def mhd_dt(ctx, U: torch.Tensor) -> float:
+    v = ctypes.c_double(0)
+    _check(LIB.mhd_dt(ctx, _ptr(U), ctypes.byref(v)), "mhd_dt")
+    return v.value
+
+
+def mhd_step(ctx, U: torch.Tensor, dt: float):
+    _check(LIB.mhd_step(ctx, _ptr(U), float(dt)), "mhd_step")
+
+
+def mhd_run(ctx, U: torch.Tensor, nsteps: int, dt_log: torch.Tensor | None = None):
+    p = _ptr(dt_log) if dt_log is not None else ctypes.c_void_p(0)
+    _check(LIB.mhd_run(ctx, _ptr(U), int(nsteps), p), "mhd_run")
+
+
+def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:
+    assert U_host.dtype == torch.float64 and not U_host.is_cuda and U_host.is_contiguous()
+    t = ctypes.c_double(0)
+    _check(LIB.mhd_run_host(ctx, ctypes.c_void_p(U_host.data_ptr()), int(nsteps), ctypes.byref(t)), "mhd_run_host")
+    return t.value
+
+
+def mhd_adjoint_step(ctx, U_n: torch.Tensor, dt: float, gU_np1: torch.Tensor, gU_n: torch.Tensor):
+    _check(LIB.mhd_adjoint_step(ctx, _ptr(U_n), float(dt), _ptr(gU_np1), _ptr(gU_n)), "mhd_adjoint_step")
+
+
+def mhd_diagnostics(ctx, U: torch.Tensor):
+    m = ctypes.c_double(0)
+    tot = (ctypes.c_double * 8)()
+    _check(LIB.mhd_diagnostics(ctx, _ptr(U), ctypes.byref(m), tot), "mhd_diagnostics")
+    return m.value, list(tot)
+
+
+def mhd_status(ctx):
+    """Returns (status code, (rho floor triggers, pressure floor triggers))."""
+    cnt = (ctypes.c_longlong * 2)()
+    code = LIB.mhd_status(ctx, cnt)
+    return code, (cnt[0], cnt[1])
+
+
+def mhd_stage_primitives(ctx, U, W):
+    _check(LIB.mhd_stage_primitives(ctx, _ptr(U), _ptr(W)), "mhd_stage_primitives")
+
+
+def mhd_stage_fluxes(ctx, U, recon: int, F):
+    _check(LIB.mhd_stage_fluxes(ctx, _ptr(U), int(recon), _ptr(F)), "mhd_stage_fluxes")
+
+
+def mhd_stage_edges(ctx, U, F, E):
+    _check(LIB.mhd_stage_edges(ctx, _ptr(U), _ptr(F), _ptr(E)), "mhd_stage_edges")
+
+
+def mhd_stage_recon(ctx, U, axis: int, recon: int, WL, WR):
+    _check(LIB.mhd_stage_recon(ctx, _ptr(U), int(axis), int(recon), _ptr(WL), _ptr(WR)), "mhd_stage_recon")
+
+
+MHD_NUM_STAGES = 8
+
+
+def mhd_profile_enable(ctx, on: bool):
+    _check(LIB.mhd_profile_enable(ctx, 1 if on else 0), "mhd_profile_enable")
+
+
+def mhd_profile_read(ctx):
+    """{stage name: (device ms, launches)} since the last enable/read."""
+    ms = (ctypes.c_double * MHD_NUM_STAGES)()
+    n = (ctypes.c_longlong * MHD_NUM_STAGES)()
+    _check(LIB.mhd_profile_read(ctx, ms, n), "mhd_profile_read")
+    return {LIB.mhd_stage_name(i).decode(): (ms[i], n[i]) for i in range(MHD_NUM_STAGES)}
+
+
+# ---- convenience ------------------------------------------------------
+class Sim:
+    """Owns one library context for a grid and a configuration."""
+
+    def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, gamma=5.0 / 3.0, cfl=0.4, recon="plmc",
+                 precision="fp64", rho_floor=1e-20, p_floor=1e-20, stream=None):
+        self.shape = (nz, ny, nx)
+        self.cfg = mhd_config(nx, ny, nz, lx / nx, ly / ny, lz / nz, gamma, cfl,
+                              RECON[recon] if isinstance(recon, str) else recon,
+                              PRECISION[precision] if isinstance(precision, str) else precision,
+                              rho_floor, p_floor)
+        self.ctx = mhd_init(self.cfg, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            mhd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def N(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def dt(self, U):
+        return mhd_dt(self.ctx, U)
+
+    def step(self, U, dt):
+        mhd_step(self.ctx, U, dt)
+
+    def run(self, U, nsteps, dt_log=None):
+        mhd_run(self.ctx, U, nsteps, dt_log)
+
+    def status(self):
+        code, counts = mhd_status(self.ctx)
+        _check(code, "mhd_status")
+        return counts
+
+    def diagnostics(self, U):
+        return mhd_diagnostics(self.ctx, U)
+
+    def primitives(self, U):
+        W = torch.empty_like(U)
+        mhd_stage_primitives(self.ctx, U, W)
+        return W
+
+    def fluxes(self, U, recon=None):
+        r = self.cfg.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)
+        F = torch.empty((3, 7) + self.shape, dtype=torch.float64, device=U.device)
+        mhd_stage_fluxes(self.ctx, U, r, F)
+        return F
+
+    def edges(self, U, F):
+        E = torch.empty((3,) + self.shape, dtype=torch.float64, device=U.device)
+        mhd_stage_edges(self.ctx, U, F.contiguous(), E)
+        return E
+
+    def recon(self, U, axis, recon=None):
+        r = self.cfg.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)
+        WL = torch.empty((7,) + self.shape, dtype=torch.float64, device=U.device)
+        WR = torch.empty_like(WL)
+        mhd_stage_recon(self.ctx, U, axis, r, WL, WR)
+        return WL, WR

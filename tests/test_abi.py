@@ -1,0 +1,67 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol and
+validates configurations without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:int|void|const char\*)\s+\**(mhd_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_05240_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_step_api():
+    names = declared_functions()
+    for required in ("mhd_init", "mhd_step", "mhd_dt", "mhd_adjoint_step", "mhd_run", "mhd_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_config_validation_without_gpu():
+    from paper_2402_05240_gb300 import mhd
+    ok = mhd.mhd_config(32, 32, 32, 1 / 32, 1 / 32, 1 / 32, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20)
+    assert mhd.mhd_workspace_bytes(ok) > 32 ** 3 * 8 * 8
+    fp32 = mhd.mhd_config(32, 32, 32, 1 / 32, 1 / 32, 1 / 32, 5 / 3, 0.4, 1, 1, 1e-20, 1e-20)
+    assert mhd.mhd_workspace_bytes(fp32) < mhd.mhd_workspace_bytes(ok)
+    bad = [
+        mhd.mhd_config(0, 32, 32, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # empty
+        mhd.mhd_config(3, 32, 32, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # below minimum
+        mhd.mhd_config(8, 8, 8, 0, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # dx = 0
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 1.0, 0.4, 1, 0, 1e-20, 1e-20),  # gamma = 1
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.0, 1, 0, 1e-20, 1e-20),  # cfl = 0
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 7, 0, 1e-20, 1e-20),  # recon
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 5, 1e-20, 1e-20),  # precision
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 0.0, 1e-20),  # floor
+    ]
+    for cfg in bad:
+        with pytest.raises(mhd.MHDError) as e:
+            mhd.mhd_workspace_bytes(cfg)
+        assert e.value.code == mhd.MHD_ERR_ARG
+
+
+def test_null_arguments_rejected(lib):
+    lib.mhd_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]
+    lib.mhd_step.restype = ctypes.c_int
+    assert lib.mhd_step(None, None, 0.1) == -1
+    lib.mhd_strerror.restype = ctypes.c_char_p
+    assert lib.mhd_strerror(-4).startswith(b"non-finite")

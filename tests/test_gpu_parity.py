@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 step rel L1 <= 1e-12 per field after 10 steps (the stated
+target); per-stage FP64 outputs element-wise within 1e-12 relative to the
+field scale; FP32-bulk step rel L1 <= 1e-5 against the FP64 oracle.
+Sizes span several 32 x 4 thread tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2402_05240_gb300 import inputs as I  # noqa: E402
+from tests.helpers import rel_l1  # noqa: E402
+
+RAGGED = (37, 21, 19)
+
+
+@pytest.fixture(scope="module")
+def mhd():
+    from paper_2402_05240_gb300 import build
+    build.build()
+    from paper_2402_05240_gb300 import mhd as m
+    return m
+
+
+def turb(n, seed=3, kmax=4):
+    return I.turbulent_box(I.Box(*n), seed_v=seed, seed_b=seed + 1, kmax=kmax)
+
+
+def cuda(U):
+    return torch.from_numpy(np.ascontiguousarray(U)).cuda()
+
+
+def maxrel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ------------------------------------------------------------------ stages --
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32_bulk", 1e-6)])
+def test_primitives(mhd, precision, tol):
+    U = turb(RAGGED)
+    sim = mhd.Sim(*RAGGED, precision=precision)
+    W = sim.primitives(cuda(U)).cpu().numpy()
+    ref = O.Oracle(*RAGGED).primitives(U)
+    for f in range(8):
+        assert maxrel(W[f], ref[f]) < tol, f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_dt(mhd, precision):
+    U = turb(RAGGED)
+    sim = mhd.Sim(*RAGGED, cfl=0.3, precision=precision)
+    dt = sim.dt(cuda(U))
+    ref = O.Oracle(*RAGGED).dt(U, 0.3)
+    assert abs(dt - ref) <= (1e-14 if precision == "fp64" else 1e-6) * ref
+
+
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_recon_states(mhd, recon, axis):
+    U = turb(RAGGED)
+    sim = mhd.Sim(*RAGGED, recon=recon)
+    WL, WR = sim.recon(cuda(U), axis)
+    rL, rR = O.Oracle(*RAGGED).recon(U, axis, recon)
+    for q in range(7):
+        scale = np.max(np.abs(rL[q])) + 1e-300
+        assert np.max(np.abs(WL.cpu().numpy()[q] - rL[q])) < 1e-12 * max(scale, 1.0), (q, "L")
+        assert np.max(np.abs(WR.cpu().numpy()[q] - rR[q])) < 1e-12 * max(scale, 1.0), (q, "R")
+
+
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_fluxes(mhd, recon):
+    U = turb(RAGGED)
+    sim = mhd.Sim(*RAGGED, recon=recon)
+    F = sim.fluxes(cuda(U)).cpu().numpy()
+    ref = O.Oracle(*RAGGED, recon=recon).fluxes(U)
+    for a in range(3):
+        for q in range(7):
+            scale = max(np.max(np.abs(ref[a, q])), 1e-3)
+            assert np.max(np.abs(F[a, q] - ref[a, q])) < 1e-12 * scale, (a, q)
+
+
+def test_edges(mhd):
+    U = turb(RAGGED)
+    orc = O.Oracle(*RAGGED)
+    F = orc.fluxes(U, "plmc")
+    E = mhd.Sim(*RAGGED).edges(cuda(U), cuda(F)).cpu().numpy()
+    ref = orc.edges(U, F)
+    assert maxrel(E, ref) < 1e-13
+
+
+# -------------------------------------------------------------- full step --
+def run_gpu(mhd, U0, n, nsteps, cfl, **kw):
+    sim = mhd.Sim(*n, cfl=cfl, **kw)
+    U = cuda(U0)
+    dts = torch.zeros(nsteps, dtype=torch.float64, device="cuda")
+    sim.run(U, nsteps, dts)
+    torch.cuda.synchronize()
+    sim.status()
+    return U.cpu().numpy(), dts.cpu().numpy()
+
+
+def test_config0_linear_wave_fp64(mhd):
+    """32^3 fast wave, B = (1, sqrt2, 0.5), PLMC, CFL 0.4, 10 steps."""
+    n = (32, 32, 32)
+    U0, _ = I.linear_wave(I.Box(*n), amp=1e-6)
+    got, dts = run_gpu(mhd, U0, n, 10, 0.4, recon="plmc")
+    orc = O.Oracle(*n, recon="plmc")
+    assert abs(dts[0] - orc.dt(U0, 0.4)) <= 1e-14 * dts[0]
+    ref, _ = orc.run(U0, 10, dts=list(dts))
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-12), err
+    # the wave itself (perturbation) agrees too, not only the background
+    pert = np.sum(np.abs(got - ref)) / np.sum(np.abs(ref - I.uniform(I.Box(*n), 1.0, (0, 0, 0), 0.6,
+                                                                           (1.0, math.sqrt(2), 0.5))))
+    assert pert < 1e-8
+
+
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_turbulent_ragged_fp64(mhd, recon):
+    U0 = turb(RAGGED, seed=7)
+    got, dts = run_gpu(mhd, U0, RAGGED, 10, 0.3, recon=recon)
+    ref, _ = O.Oracle(*RAGGED, recon=recon).run(U0, 10, dts=list(dts))
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_turbulent_fp32_bulk(mhd, recon):
+    n = (40, 24, 20)
+    U0 = turb(n, seed=9)
+    got, dts = run_gpu(mhd, U0, n, 10, 0.3, recon=recon, precision="fp32_bulk")
+    ref, _ = O.Oracle(*n, recon=recon).run(U0, 10, dts=list(dts))
+    err = rel_l1(got, ref)
+    assert np.all(err <= 1e-5), err
+
+
+def test_fixed_dt_step_matches_run(mhd):
+    n = (16, 12, 8)
+    U0 = turb(n, seed=11)
+    sim = mhd.Sim(*n, cfl=0.3)
+    U = cuda(U0)
+    dt = sim.dt(U)
+    sim.step(U, dt)
+    ref = O.Oracle(*n).step(U0, dt)
+    assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_uniform_state_bit_identical(mhd, precision, recon):
+    n = (33, 9, 6)
+    U0 = I.uniform(I.Box(*n), 1.3, (0.4, -0.2, 0.3), 0.7, (0.6, -0.8, 0.2))
+    got, _ = run_gpu(mhd, U0, n, 10, 0.4, recon=recon, precision=precision)
+    assert np.array_equal(got, U0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_conservation_and_divb(mhd, precision):
+    n = (48, 32, 24)
+    U0 = turb(n, seed=13)
+    sim = mhd.Sim(*n, cfl=0.3, precision=precision)
+    U = cuda(U0)
+    d0, t0 = sim.diagnostics(U)
+    sim.run(U, 10)
+    d1, t1 = sim.diagnostics(U)
+    scale = np.array([np.sum(np.abs(U0[f])) for f in range(8)])
+    assert np.all(np.abs(np.array(t1) - np.array(t0)) <= 1e-13 * scale)
+    assert d1 * (1.0 / 24) / np.max(np.abs(U0[5:])) < 1e-13
+    od, ot = O.Oracle(*n).diagnostics(U0)
+    assert abs(d0 - od) <= 1e-15 * max(od, 1.0)
+    np.testing.assert_allclose(t0, ot, rtol=1e-12, atol=1e-12 * np.max(scale))
+
+
+# ---------------------------------------------------- full size, sampled --
+def _subbox_step(U, c, dt, recon, r=8):
+    """Oracle step on the periodic (2r+1)^3 neighbourhood of cell c; the centre
+    depends only on cells within the one-step stencil radius (< r), so the
+    wrap of the sub-box does not reach it."""
+    nz, ny, nx = U.shape[1:]
+    k, j, i = c
+    ks = [(k + d) % nz for d in range(-r, r + 1)]
+    js = [(j + d) % ny for d in range(-r, r + 1)]
+    is_ = [(i + d) % nx for d in range(-r, r + 1)]
+    sub = np.ascontiguousarray(U[:, ks][:, :, js][:, :, :, is_])
+    m = 2 * r + 1
+    orc = O.Oracle(m, m, m, dx=1.0 / nx, dy=1.0 / ny, dz=1.0 / nz, recon=recon)
+    return orc.step(sub, dt)[:, r, r, r]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_bulk", 1e-5)])
+def test_full_size_256_sampled(mhd, precision, tol):
+    """256^3 turbulent box (the benchmark workload): 2 GPU steps, then a third
+    step checked against the oracle at sampled cells, plus the invariants."""
+    n = (256, 256, 256)
+    U0 = I.turbulent_box(I.Box(*n), seed_v=1, seed_b=2)
+    sim = mhd.Sim(*n, cfl=0.3, recon="plmc", precision=precision)
+    U = cuda(U0)
+    del U0
+    sim.run(U, 2)
+    before = U.cpu().numpy()
+    dt = sim.dt(U)
+    sim.step(U, dt)
+    after = U.cpu().numpy()
+    rng = np.random.default_rng(0)
+    cells = [tuple(int(x) for x in rng.integers(0, 256, 3)) for _ in range(24)] + [(0, 0, 0), (255, 255, 255)]
+    for c in cells:
+        ref = _subbox_step(before, c, dt, "plmc")
+        got = after[:, c[0], c[1], c[2]]
+        scale = np.abs(ref) + np.array([1, 1, 1, 1, 1, 0.5, 0.5, 0.5])
+        assert np.all(np.abs(got - ref) <= tol * scale), (c, got - ref)
+    d, _ = sim.diagnostics(U)
+    assert d * (1.0 / 256) / np.max(np.abs(after[5:])) < 1e-12
+
+
+# ------------------------------------------------------------- error paths --
+def test_error_codes(mhd):
+    n = (8, 8, 8)
+    U0 = I.uniform(I.Box(*n), 1.0, (0, 0, 0), 1.0, (0.1, 0.2, 0.3))
+    sim = mhd.Sim(*n)
+    U = cuda(U0)
+    with pytest.raises(mhd.MHDError) as e:
+        sim.step(U, -1.0)
+    assert e.value.code == mhd.MHD_ERR_DT
+    with pytest.raises(mhd.MHDError) as e:
+        sim.step(U, float("nan"))
+    assert e.value.code == mhd.MHD_ERR_DT
+    bad = U0.copy()
+    bad[0, 3, 3, 3] = float("nan")
+    Ub = cuda(bad)
+    with pytest.raises(mhd.MHDError) as e:
+        sim.dt(Ub)
+    assert e.value.code == mhd.MHD_ERR_NONFINITE
+    bad = U0.copy()
+    bad[0, 1, 2, 3] = -1.0
+    Ub = cuda(bad)
+    sim.step(Ub, 1e-3)
+    code, _ = mhd.mhd_status(sim.ctx)
+    assert code == mhd.MHD_ERR_NONFINITE
+    # the context stays usable after an error
+    sim.step(U, 1e-3)
+    assert mhd.mhd_status(sim.ctx)[0] == mhd.MHD_OK
+
+
+def test_floors_trigger_and_count(mhd):
+    """A cell driven below the pressure floor is reset and counted (D-12)."""
+    n = (16, 8, 8)
+    box = I.Box(*n)
+    x, _, _ = box.centres()
+    vx = np.broadcast_to(np.where(x < 0.5, -3.0, 3.0), box.shape)  # strong rarefaction
+    U0 = I.assemble(box, 1.0, (vx, np.zeros(box.shape), np.zeros(box.shape)), 1e-3, (0.0, 0.0, 0.0))
+    pf = 5e-4
+    sim = mhd.Sim(*n, cfl=0.3, rho_floor=1e-3, p_floor=pf)
+    U = cuda(U0)
+    dts = torch.zeros(5, dtype=torch.float64, device="cuda")
+    sim.run(U, 5, dts)
+    counts = sim.status()
+    orc = O.Oracle(*n, rho_floor=1e-3, p_floor=pf)
+    ref, _ = orc.run(U0, 5, dts=list(dts.cpu().numpy()))
+    assert counts[1] > 0
+    assert counts[1] == orc.floor_counts[1] and counts[0] == orc.floor_counts[0]
+    assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-12)
