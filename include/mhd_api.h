@@ -41,6 +41,7 @@ extern "C" {
 #define MHD_ERR_OOM (-3)       /* workspace allocation failed                  */
 #define MHD_ERR_NONFINITE (-4) /* a kernel saw NaN/Inf or density <= 0         */
 #define MHD_ERR_DT (-5)        /* dt <= 0 or not finite                        */
+#define MHD_ERR_TOO_LARGE (-6) /* grid above the static scratch of mhd_diagnostics_static */
 
 #define MHD_RECON_PCM 0  /* piecewise constant (Sec. 2.2.2)                   */
 #define MHD_RECON_PLMC 1 /* piecewise linear, characteristic (Sec. 2.2.6)     */
@@ -104,6 +105,25 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const doubl
 /* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
  * |div B| from face differences, and the sums of the 8 fields.  Synchronous. */
 int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, double totals_host[8]);
+
+/* mhd_diagnostics without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc -- a host
+ * whose device memory is already owned by another allocator, or a step loop
+ * that must not pay the implicit synchronisation of cudaMalloc/cudaFree.
+ * It needs no context: cfg supplies nx, ny, nz (>= 1 each) and dx, dy, dz;
+ * U_dev is a state in the usual layout; the work runs on `stream` (a
+ * cudaStream_t, NULL = default stream) and the call synchronises it before
+ * writing the max |div B| and the 8 field sums to host memory.
+ * Scratch: a file-scope device array of 9.4 MB (grids up to 512^3 =
+ * 134,217,728 cells) that every GPU loading the library holds until the
+ * process exits.  Larger grids return MHD_ERR_TOO_LARGE.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams, other host threads
+ * on the same device) race and must be serialised by the caller. */
+int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev, void* stream, double* divb_max_host,
+                           double totals_host[8]);
 
 /* Synchronise and read the device flags raised since the last call;
  * counts_host[0..1] (may be NULL) receive the density / pressure floor

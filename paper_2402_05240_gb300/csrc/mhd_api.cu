@@ -417,6 +417,7 @@ const char* mhd_strerror(int code) {
     case MHD_ERR_OOM: return "out of device memory";
     case MHD_ERR_NONFINITE: return "non-finite value or non-positive density in the state";
     case MHD_ERR_DT: return "time step not positive or not finite";
+    case MHD_ERR_TOO_LARGE: return "grid larger than the static scratch of mhd_diagnostics_static (512^3 cells)";
     default: return "unknown status";
   }
 }

@@ -22,6 +22,7 @@ MHD_ERR_CUDA = -2
 MHD_ERR_OOM = -3
 MHD_ERR_NONFINITE = -4
 MHD_ERR_DT = -5
+MHD_ERR_TOO_LARGE = -6
 
 RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
 PRECISION = {"fp64": 0, "fp32_bulk": 1}
@@ -61,6 +62,7 @@ def _load_library():
         "mhd_profile_enable": (ip, [vp, ip]),
         "mhd_profile_read": (ip, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "mhd_stage_name": (ctypes.c_char_p, [ip]),
+        "mhd_diagnostics_static": (ip, [ctypes.POINTER(mhd_config), vp, vp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -136,6 +138,16 @@ def mhd_diagnostics(ctx, U: torch.Tensor):
     m = ctypes.c_double(0)
     tot = (ctypes.c_double * 8)()
     _check(LIB.mhd_diagnostics(ctx, _ptr(U), ctypes.byref(m), tot), "mhd_diagnostics")
+    return m.value, list(tot)
+
+
+def mhd_diagnostics_static(cfg: mhd_config, U: torch.Tensor, stream=None):
+    """mhd_diagnostics without a context or any device allocation (static
+    device scratch, grids up to 512^3); for callers that cannot allocate."""
+    m = ctypes.c_double(0)
+    tot = (ctypes.c_double * 8)()
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(LIB.mhd_diagnostics_static(ctypes.byref(cfg), _ptr(U), s, ctypes.byref(m), tot), "mhd_diagnostics_static")
     return m.value, list(tot)
 
 
