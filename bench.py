@@ -59,8 +59,18 @@ def load_peaks():
 
 
 # FP64 FMA rate of this GPU measured by an FMA-chain probe:
-# 601 G DFMA/s = 1.20 TFLOP/s.
+# 601 G DFMA/s = 1.20 TFLOP/s (about 2 DFMA per clock per SM at 2.07 GHz).
 FP64_PEAK_GFLOPS = 1202.6
+
+# Per-cell counters of one launch of each FP64 stage (PLMC), from the ncu
+# capture summarised in profiles/fp64_counters_turbulent128_plmc.md:
+# FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes (read + write).  They hold
+# for the kernels as profiled; a kernel changed since has no entry.
+FP64_COUNTERS = {
+    "prim": (225.0, 105.9), "flux_pcm": (1285.7, 231.3), "emf": (111.0, 139.6),
+    "update_half": (336.0, 283.3), "recon": (624.4, 150.4), "flux_hlld": (456.2, 162.3),
+    "update_full": (195.0, 260.3),
+}
 
 
 class ClockSampler:
@@ -161,28 +171,36 @@ def time_gpu(mhd, torch, U0, n, steps, warmup, recon, precision, barrier):
     return ms / steps, prof, launches, sim, U
 
 
-def roofline_of(prof, precision, n3, hbm_peak, peak_kind, traffic=None):
+def roofline_of(prof, precision, n3, hbm_peak, peak_kind):
+    """Roofline of the dominant stage (largest share of the timed region).
+
+    FP64: the stage is bound by the FP64 pipe; achieved = counted FP64 flops
+    per launch / live launch time against the measured FP64 FMA peak.
+    FP32-bulk: achieved = algorithmic bytes per launch / launch time against
+    the measured HBM copy bandwidth.
+    """
     T = 8 if precision == "fp64" else 4
     sb = stage_bytes(T)
     total = sum(v[0] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (ms, launches) = dom
-    per_launch_ms = ms / max(launches, 1)
-    achieved = sb[name] * n3 / (per_launch_ms * 1e-3) / 1e9
+    name, (ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_s = ms / max(launches, 1) * 1e-3
     shares = {k: round(v[0] / total, 4) for k, v in prof.items() if v[1]}
-    return {
-        "kernel": name,
-        "bound": "hbm",
-        "achieved": round(achieved, 1),
-        "peak": hbm_peak,
-        "unit": "GB/s",
-        "frac": round(achieved / hbm_peak, 4),
-        "peak_source": peak_kind,
-        "traffic": traffic,
-        "per_launch_ms": round(per_launch_ms, 4),
-        "stage_share": shares,
-        "bytes_per_cell_counted": sum(sb[k] * v[1] for k, v in prof.items()) / max(1, prof["update_full"][1]),
-    }
+    gbs = sb[name] * n3 / per_launch_s / 1e9
+    out = {"kernel": name, "per_launch_ms": round(per_launch_s * 1e3, 4), "stage_share": shares,
+           "bytes_per_cell_counted": sum(sb[k] * v[1] for k, v in prof.items()) / max(1, prof["update_full"][1]),
+           "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "frac": round(gbs / hbm_peak, 4),
+                   "peak_source": peak_kind}}
+    cnt = FP64_COUNTERS.get(name) if precision == "fp64" else None
+    if precision == "fp64" and cnt:
+        gf = cnt[0] * n3 / per_launch_s / 1e9
+        out.update({"bound": "alu", "achieved": round(gf, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": round(gf / FP64_PEAK_GFLOPS, 4), "peak_source": "measured (FP64 FMA probe)",
+                    "traffic": round(cnt[1] * n3), "flop_per_cell": cnt[0],
+                    "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
+    else:
+        out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(gbs / hbm_peak, 4), "peak_source": peak_kind, "traffic": None})
+    return out
 
 
 def cpu_baseline_sample(n_sample=128, steps=1):
@@ -289,13 +307,15 @@ def main():
     roof = roofline_of(prof64, "fp64", n3, hbm_peak, peak_kind)
 
     # end to end through the public host-buffer entry point (copies inside)
-    host = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True)
-    host.copy_(U0.cpu())
-    mhd.mhd_run_host(sim.ctx, host, 1)  # warm the host-state buffer
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        mhd.mhd_run_host(sim.ctx, host, 1)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = None
+    if args.e2e_steps > 0:
+        host = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True)
+        host.copy_(U0.cpu())
+        mhd.mhd_run_host(sim.ctx, host, 1)  # warm the host-state buffer
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            mhd.mhd_run_host(sim.ctx, host, 1)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     sim.close()
     del U, sim
 
@@ -316,8 +336,8 @@ def main():
         "config": {"workload": f"turbulent box {n}^3, {args.recon.upper()} + HLLD, FP64 step, CFL 0.3, device dt",
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (state 1.07 GB)"},
         "roofline": roof,
-        "alu_fp64": {"peak_gflops": FP64_PEAK_GFLOPS, "note": "FP64 FMA rate measured by a probe"},
-        "e2e": {"value": n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3, "d2h_bytes_per_step": 64 * n3},
+        "e2e": ({"value": world * n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3,
+                 "d2h_bytes_per_step": 64 * n3} if e2e_s else None),
         "gpu_launches": launches64,
         "clocks": clk,
         "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in prof64.items()},
