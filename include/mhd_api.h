@@ -102,6 +102,11 @@ int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const double* gU_np1_dev,
                      double* gU_n_dev);
 
+/* Bytes of device memory the first mhd_adjoint_step call allocates (once per
+ * context, freed by mhd_destroy): forward intermediates of one step plus
+ * cotangent buffers, 197 words of the compute type + 10 doubles per cell. */
+int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
+
 /* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
  * |div B| from face differences, and the sums of the 8 fields.  Synchronous. */
 int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, double totals_host[8]);
@@ -172,6 +177,23 @@ int mhd_stage_edges(mhd_ctx* ctx, const double* U_dev, const double* F_dev, doub
 /* WL_dev/WR_dev[7][N]: W_{L,p+1/2} and W_{R,p-1/2} of every cell along axis
  * (Step 6), solver frame, for recon = MHD_RECON_*. */
 int mhd_stage_recon(mhd_ctx* ctx, const double* U_dev, int axis, int recon, double* WL_dev, double* WR_dev);
+
+/* Vector-Jacobian product of the map U -> (W_L, W_R) of one axis (primitive
+ * recovery, Sec. 2.2.1, then the reconstruction of Step 6): given the
+ * cotangents gWL_dev, gWR_dev [7][N] (layouts of mhd_stage_recon), writes
+ * gU_dev [8][N].  Uses the adjoint workspace. */
+int mhd_stage_recon_vjp(mhd_ctx* ctx, const double* U_dev, int axis, int recon, const double* gWL_dev,
+                        const double* gWR_dev, double* gU_dev);
+
+/* HLLD flux and its vector-Jacobian product on n independent faces (Step 3;
+ * Miyoshi & Kusano 2005): wl_dev, wr_dev [n][7] solver-frame primitive states
+ * (rho, u, v, w, P, B_t1, B_t2), bn_dev [n] longitudinal fields, gf_dev [n][7]
+ * flux cotangents; writes gwl_dev, gwr_dev [n][7], gbn_dev [n] and the flux
+ * f_dev [n][7].  precision: MHD_FP64 or MHD_FP32_BULK (arithmetic in float).
+ * No context needed; asynchronous on stream. */
+int mhd_stage_hlld_vjp(int n, double gamma, int precision, const double* wl_dev, const double* wr_dev,
+                       const double* bn_dev, const double* gf_dev, double* gwl_dev, double* gwr_dev, double* gbn_dev,
+                       double* f_dev, void* stream);
 
 #ifdef __cplusplus
 }

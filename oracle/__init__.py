@@ -69,6 +69,8 @@ def _load():
             lib.oracle_step.argtypes = [P, dp, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_step_jvp.argtypes = [P, dp, dp, ctypes.c_double]
             lib.oracle_diagnostics.argtypes = [P, dp, dp, dp]
+            lib.oracle_hlld_jvp.argtypes = [ctypes.c_double, dp, dp, ctypes.c_double, dp, dp, ctypes.c_double, dp, dp]
+            lib.oracle_recon_jvp.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -173,6 +175,15 @@ class Oracle:
         self.lib.oracle_step_jvp(ctypes.byref(self.p), _ptr(V), _ptr(dV), dt)
         return V, dV
 
+    def recon_jvp(self, U, dU, axis, recon=None):
+        """(WL, WR, dWL, dWR) of U -> (W_L, W_R) along ``axis`` and its derivative along dU."""
+        U = self._chk(U)
+        dU = self._chk(dU)
+        r = self.p.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)
+        out = [np.empty((7,) + self.shape) for _ in range(4)]
+        self.lib.oracle_recon_jvp(ctypes.byref(self.p), _ptr(U), _ptr(dU), axis, r, *[_ptr(x) for x in out])
+        return tuple(out)
+
     def diagnostics(self, U):
         U = self._chk(U)
         m = ctypes.c_double(0)
@@ -201,6 +212,17 @@ def hlld_detail(gamma, wl, wr, bn):
     fl = np.zeros((2, 7))
     star = lib.oracle_hlld_detail(gamma, _ptr(wl), _ptr(wr), bn, _ptr(f), _ptr(sp), _ptr(st), _ptr(fl))
     return f, sp, st, fl, bool(star)
+
+
+def hlld_jvp(gamma, wl, wr, bn, dwl, dwr, dbn):
+    """(flux, J (dwl, dwr, dbn)) of the HLLD flux (forward-mode dual numbers)."""
+    lib = _load()
+    args = [np.ascontiguousarray(x, np.float64) for x in (wl, wr, dwl, dwr)]
+    f = np.zeros(7)
+    df = np.zeros(7)
+    lib.oracle_hlld_jvp(gamma, _ptr(args[0]), _ptr(args[1]), float(bn), _ptr(args[2]), _ptr(args[3]), float(dbn),
+                        _ptr(f), _ptr(df))
+    return f, df
 
 
 def eigen(gamma, w, bn):

@@ -924,6 +924,44 @@ void oracle_step_jvp(const Params* P, double* U, double* dU, double dt) {
   }
 }
 
+// Forward-mode derivative of the HLLD flux: f = HLLD(wl, wr, bn), df = J (dwl, dwr, dbn).
+void oracle_hlld_jvp(double gamma, const double* wl, const double* wr, double bn, const double* dwl,
+                     const double* dwr, double dbn, double* f, double* df) {
+  Dual a[7], b[7], out[7];
+  for (int q = 0; q < 7; ++q) {
+    a[q] = Dual(wl[q], dwl[q]);
+    b[q] = Dual(wr[q], dwr[q]);
+  }
+  hlld(gamma, a, b, Dual(bn, dbn), out);
+  for (int q = 0; q < 7; ++q) {
+    f[q] = out[q].v;
+    df[q] = out[q].d;
+  }
+}
+
+// Forward-mode derivative of U -> (W_L, W_R) along axis a (primitives then
+// reconstruction): WL, WR, dWL, dWR are [7][N].
+void oracle_recon_jvp(const Params* P, const double* U, const double* dU, int a, int recon, double* WL, double* WR,
+                      double* dWL, double* dWR) {
+  Grid g(*P);
+  const long N = g.N;
+  std::vector<Dual> X(8 * N);
+  for (long i = 0; i < 8 * N; ++i) X[i] = Dual(U[i], dU[i]);
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < N; ++c) {
+    int p[3];
+    g.coords(c, p);
+    Dual wl[7], wr[7];
+    reconstruct(*P, g, X.data(), p, a, recon, wl, wr);
+    for (int q = 0; q < 7; ++q) {
+      WL[q * N + c] = wl[q].v;
+      dWL[q * N + c] = wl[q].d;
+      WR[q * N + c] = wr[q].v;
+      dWR[q * N + c] = wr[q].d;
+    }
+  }
+}
+
 // max |div B| (face differences, per cell) and plain sums of the 8 fields.
 void oracle_diagnostics(const Params* P, const double* U, double* divb_max, double* totals) {
   Grid g(*P);

@@ -1,0 +1,546 @@
+// mhd_adjoint_kernels.cuh -- the reverse sweep of one VL+CT step (not in the
+// paper): gU^n = (dU^{n+1}/dU^n)^T gU^{n+1} at fixed dt.
+//
+// The forward intermediates are recomputed first (primitives W^n, predictor
+// fluxes F^n, half-step state, interface states and corrector fluxes F^{n+1/2},
+// edge fields).  The reverse kernels then run Step 9 back to Step 1.  Every
+// reverse kernel is written in gather form: one thread owns one cell and only
+// writes that cell's cotangents, reading the cotangents of its neighbours, so
+// the result is deterministic (no floating-point atomics).  Cotangents of the
+// state accumulate in double.
+#pragma once
+
+#include "mhd_adjoint.cuh"
+#include "mhd_kernels.cuh"
+
+namespace mhd {
+
+template <class T> struct AdjBufs {
+  // forward intermediates
+  T *Wn, *Fn, *Wh, *Bh, *WLa, *WRa, *Fh, *Eh;
+  double* Uh;  // [5][N] hydro half state
+  // cotangents
+  T *gF, *gE, *gW, *gWL, *gWR, *gS, *gBf, *gBcc, *gBccF;
+  double* g5;  // [5][N]
+};
+
+__device__ __forceinline__ double upw_lo(double m) { return m > 0.0 ? 1.0 : (m < 0.0 ? 0.0 : 0.5); }
+
+// ------------------------------------------------- R1: floors of Step 9 --
+// Recomputes the pre-floor U^{n+1} of the cell; writes the pre-floor
+// cotangent of the hydro fields into gU and the floor's B_cc cotangent.
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __restrict__ U, const T* __restrict__ F,
+                                                       const T* __restrict__ E, double dt,
+                                                       const double* __restrict__ gUp, double* __restrict__ gU,
+                                                       T* __restrict__ gBccF) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const long long N = g.N, c = cidx(g, i, j, k);
+  double u5[5];
+  hydro_update<T, true>(g, U, F, dt, i, j, k, u5);
+  const double bx = face_update<T, true, 0>(g, U, E, dt, i, j, k);
+  const double by = face_update<T, true, 1>(g, U, E, dt, i, j, k);
+  const double bz = face_update<T, true, 2>(g, U, E, dt, i, j, k);
+  const double bxm = face_update<T, true, 0>(g, U, E, dt, wrapi(i - 1, g.n[0]), j, k);
+  const double bym = face_update<T, true, 1>(g, U, E, dt, i, wrapi(j - 1, g.n[1]), k);
+  const double bzm = face_update<T, true, 2>(g, U, E, dt, i, j, wrapi(k - 1, g.n[2]));
+  const double b[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
+  double g5[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) g5[f] = gUp[f * N + c];
+  double gb[3] = {0.0, 0.0, 0.0};
+  const bool rfl = u5[0] < g.rho_floor;
+  const double r = rfl ? g.rho_floor : u5[0];
+  const double ke = 0.5 * (u5[1] * (u5[1] / r) + u5[2] * (u5[2] / r) + u5[3] * (u5[3] / r));
+  const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  const bool pfl = (g.gamma - 1.0) * (u5[4] - ke - me) < g.p_floor;
+  if (pfl) {  // E = p_floor/(gamma-1) + |m|^2/(2 r) + |B_cc|^2/2
+    const double gE = g5[4];
+    g5[4] = 0.0;
+    g5[1] += gE * u5[1] / r;
+    g5[2] += gE * u5[2] / r;
+    g5[3] += gE * u5[3] / r;
+    if (!rfl) g5[0] += -gE * ke / r;
+    gb[0] = gE * b[0];
+    gb[1] = gE * b[1];
+    gb[2] = gE * b[2];
+  }
+  if (rfl) g5[0] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) gU[f * N + c] = g5[f];
+  gBccF[c] = T(gb[0]);
+  gBccF[N + c] = T(gb[1]);
+  gBccF[2 * N + c] = T(gb[2]);
+}
+
+// ------------------------------------------ R2 / R7: conservative update --
+// U' = U - h div F, B' = B - h curl E.  Input: cotangents of the hydro U'
+// (g5, own and upper neighbours) and of the faces (gface(p) computed by
+// face_cot).  Output: gF hydro components, gE, and the identity part of gU.
+// cotangent of the new face B_a of cell p: gUp face + (1/2)(gBcc_a(p) + gBcc_a(p + e_a))
+template <class T, int A>
+__device__ __forceinline__ double face_cot(const Grid& g, const double* __restrict__ gUpF, const T* __restrict__ gBcc,
+                                           const T* __restrict__ gBfx, int i, int j, int k) {
+  const long long N = g.N, c = cidx(g, i, j, k);
+  double v = 0.5 * ((double)gBcc[A * N + c] + (double)gBcc[A * N + nb<A>(g, i, j, k, 1)]);
+  if (gUpF) v += gUpF[A * N + c];
+  if (gBfx) v += (double)gBfx[A * N + c];
+  return v;
+}
+
+// MODE 0 (Step 9): gface from gUp faces + floor gBcc; writes gU faces = gface.
+// MODE 1 (Step 5): gface from gBf (HLLD B_n) + gBcc (W^{n+1/2}); gU faces += gface.
+template <class T, int MODE>
+__global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const double* g5src,
+                                                       const double* __restrict__ gUpF, const T* __restrict__ gBcc,
+                                                       const T* __restrict__ gBfx, double* gU,
+                                                       T* __restrict__ gF, T* __restrict__ gE) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const long long N = g.N, c = cidx(g, i, j, k);
+  const long long cp[3] = {nb<0>(g, i, j, k, 1), nb<1>(g, i, j, k, 1), nb<2>(g, i, j, k, 1)};
+  // hydro: U'_f(p) has -h/d_a F_a(p) and +h/d_a F_a(p - e_a), so
+  // gF_a[comp](p) = -(h/d_a)(g_f(p) - g_f(p + e_a))
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double s = -h / g.d[a];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const double gv = g5src[f * N + c] - g5src[f * N + cp[a]];
+      gF[((long long)a * 7 + comp_of(f, a)) * N + c] = T(s * gv);
+    }
+  }
+  // faces of this cell and of the upper neighbours needed by the edge cotangents
+  const double gf0 = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, j, k);
+  const double gf1 = face_cot<T, 1>(g, gUpF, gBcc, gBfx, i, j, k);
+  const double gf2 = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, j, k);
+  // E_k(q) enters B_{k+1}(q) with -h/d_{k+2}, B_{k+1}(q + e_{k+2}) with +h/d_{k+2},
+  // B_{k+2}(q) with +h/d_{k+1}, B_{k+2}(q + e_{k+1}) with -h/d_{k+1}
+  // neighbours' face cotangents
+  const double f0_y = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
+  const double f0_z = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, j, wrapi(k + 1, g.n[2]));
+  const double f1_x = face_cot<T, 1>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
+  const double f1_z = face_cot<T, 1>(g, gUpF, gBcc, gBfx, i, j, wrapi(k + 1, g.n[2]));
+  const double f2_x = face_cot<T, 2>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
+  const double f2_y = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
+  // k = 0 (E_x): B_y (a=1) with e_z, B_z (a=2) with e_y
+  const double gEx = -(h / g.d[2]) * (gf1 - f1_z) + (h / g.d[1]) * (gf2 - f2_y);
+  // k = 1 (E_y): B_z with e_x, B_x with e_z
+  const double gEy = -(h / g.d[0]) * (gf2 - f2_x) + (h / g.d[2]) * (gf0 - f0_z);
+  // k = 2 (E_z): B_x with e_y, B_y with e_x
+  const double gEz = -(h / g.d[1]) * (gf0 - f0_y) + (h / g.d[0]) * (gf1 - f1_x);
+  gE[c] = T(gEx);
+  gE[N + c] = T(gEy);
+  gE[2 * N + c] = T(gEz);
+  if (MODE == 0) {
+    gU[5 * N + c] = gf0;
+    gU[6 * N + c] = gf1;
+    gU[7 * N + c] = gf2;
+  } else {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) gU[f * N + c] += g5src[f * N + c];
+    gU[5 * N + c] += gf0;
+    gU[6 * N + c] += gf1;
+    gU[7 * N + c] += gf2;
+  }
+}
+
+// ---------------------------------------------------- R3 / R8: edge EMF --
+// Gather-form reverse of Eq. emf-edge: writes gF[a][5], gF[a][6] and the
+// reference-field part of gW (v and B_cc components; rho, P zeroed).
+template <class T, int K>
+__device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
+                                             const T* __restrict__ gE, int i, int j, int k, T* __restrict__ gF,
+                                             double* gW8) {
+  constexpr int B = (K + 1) % 3, C = (K + 2) % 3;
+  const long long N = g.N;
+  int q[3] = {i, j, k};
+  auto at = [&](int db, int dc) {
+    int r[3] = {q[0], q[1], q[2]};
+    r[B] = wrapi(r[B] + db, g.n[B]);
+    r[C] = wrapi(r[C] + dc, g.n[C]);
+    return cidx(g, r[0], r[1], r[2]);
+  };
+  const long long c00 = at(0, 0), cb = at(-1, 0), cc = at(0, -1), cbc = at(-1, -1);
+  const long long cpb = at(1, 0), cpc = at(0, 1), cmcpb = at(1, -1), cmbpc = at(-1, 1);
+  const T* Fb = F + (long long)B * 7 * N;  // mass flux of b-faces: Fb[x]
+  const T* Fc = F + (long long)C * 7 * N;
+  const T* gEk = gE + (long long)K * N;
+  const double g00 = gEk[c00], gmb = gEk[cb], gmc = gEk[cc], gmbc = gEk[cbc];
+  // mass fluxes: mc(q), mc(q + e_b), mc(q - e_c), mc(q - e_c + e_b); mb(q), mb(q + e_c), mb(q - e_b), mb(q - e_b + e_c)
+  const double mc0 = Fc[c00], mc_pb = Fc[cpb], mc_mc = Fc[cc], mc_mcpb = Fc[cmcpb];
+  const double mb0 = Fb[c00], mb_pc = Fb[cpc], mb_mb = Fb[cb], mb_mbpc = Fb[cmbpc];
+  const double gbf = 0.25 * g00 * (1.0 + upw_lo(mc_pb) + upw_lo(mc0)) +
+                     0.25 * gmc * (1.0 + (1.0 - upw_lo(mc_mcpb)) + (1.0 - upw_lo(mc_mc)));
+  const double gcf = 0.25 * g00 * (1.0 + upw_lo(mb_pc) + upw_lo(mb0)) +
+                     0.25 * gmb * (1.0 + (1.0 - upw_lo(mb_mbpc)) + (1.0 - upw_lo(mb_mb)));
+  const double grf = -0.25 * (g00 * (upw_lo(mc0) + upw_lo(mb0)) + gmb * (upw_lo(mc0) + (1.0 - upw_lo(mb_mb))) +
+                              gmc * ((1.0 - upw_lo(mc_mc)) + upw_lo(mb0)) +
+                              gmbc * ((1.0 - upw_lo(mc_mc)) + (1.0 - upw_lo(mb_mb))));
+  // bf = -F_B[5], cf = +F_C[6]
+  gF[((long long)B * 7 + 5) * N + c00] = T(-gbf);
+  gF[((long long)C * 7 + 6) * N + c00] = T(gcf);
+  // ref_K = -(v_B B_C - v_C B_B)
+  const double vB = W[(1 + B) * N + c00], vC = W[(1 + C) * N + c00];
+  const double BB = W[(5 + B) * N + c00], BC = W[(5 + C) * N + c00];
+  gW8[1 + B] += -grf * BC;
+  gW8[5 + C] += -grf * vB;
+  gW8[1 + C] += grf * BB;
+  gW8[5 + B] += grf * vC;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_adj_emf(Grid g, const T* __restrict__ W, const T* __restrict__ F,
+                                                    const T* __restrict__ gE, T* __restrict__ gF, T* __restrict__ gW) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  double gw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  emf_cot_edge<T, 0>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
+  emf_cot_edge<T, 1>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
+  emf_cot_edge<T, 2>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) gW[f * N + c] = T(gw[f]);
+}
+
+// -------------------------------------------------- R4a / R9: HLLD reverse --
+// PCM (predictor): states from W of cells p and p + e_A, B_n from U's face.
+// Corrector: states from W_L, W_R buffers, B_n from the half-step faces.
+// Writes gWL(p) (left state of face p), gWR(p + e_A) (right state of the
+// face, owned by cell p + e_A) and gBf_A(p).
+template <class T, int A, bool PCM>
+__global__ void __launch_bounds__(BX* BY) k_adj_hlld(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
+                                                     const T* __restrict__ Wn, const double* __restrict__ U,
+                                                     const T* __restrict__ Bh, const T* __restrict__ gF,
+                                                     T* __restrict__ gWL, T* __restrict__ gWR, T* __restrict__ gBf) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k), cn = nb<A>(g, ci.i, ci.j, ci.k, 1);
+  T wl[7], wr[7], gf[7], gwl[7], gwr[7];
+  T bn;
+  if (PCM) {
+    load_dir<A>(Wn, N, c, wl);
+    load_dir<A>(Wn, N, cn, wr);
+    bn = T(U[(5 + A) * N + c]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      wl[q] = WL[q * N + c];
+      wr[q] = WR[q * N + cn];
+    }
+    bn = Bh[A * N + c];
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gf[q] = gF[((long long)A * 7 + q) * N + c];
+    gwl[q] = gwr[q] = T(0);
+  }
+  T gbn = T(0);
+  hlld_vjp<T>(T(g.gamma), wl, wr, bn, gf, gwl, gwr, gbn);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gWL[q * N + c] = gwl[q];
+    gWR[q * N + cn] = gwr[q];
+  }
+  gBf[A * N + c] = gbn;
+}
+
+// directional 7-vector cotangent -> W field cotangents (accumulate)
+template <int A, class T> __device__ __forceinline__ void add_dir(T* __restrict__ gW, long long N, long long q, const T* gw) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  gW[q] += gw[0];
+  gW[(1 + A) * N + q] += gw[1];
+  gW[(1 + B) * N + q] += gw[2];
+  gW[(1 + C) * N + q] += gw[3];
+  gW[4 * N + q] += gw[4];
+  gW[(5 + B) * N + q] += gw[5];
+  gW[(5 + C) * N + q] += gw[6];
+}
+
+// predictor: both face-state cotangents of cell p belong to cell p itself
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_pcm_gather(Grid g, const T* __restrict__ gWL, const T* __restrict__ gWR,
+                                                           T* __restrict__ gW) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T s[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) s[q] = gWL[q * N + c] + gWR[q * N + c];
+  add_dir<A>(gW, N, c, s);
+}
+
+// ------------------------------------------------- R4b/c: reconstruction --
+// Per cell: reverse of PLMC / PPMC for axis A; slots S[m][7] for the stencil
+// cells (PLMC m = 0..2 for p-1..p+1, PPMC m = 0..4 for p-2..p+2) and
+// S[NS*7] for the cotangent of the cell-centred B_A of cell p.
+template <class T, int RECON, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restrict__ W, const T* __restrict__ gWL,
+                                                      const T* __restrict__ gWR, T* __restrict__ S) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  constexpr int NS = RECON == 2 ? 5 : 3;
+  T gl[7], gr[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gl[q] = gWL[q * N + c];
+    gr[q] = gWR[q * N + c];
+  }
+  const T bn = W[(5 + A) * N + c];
+  T gbn = T(0);
+  T gw[NS][7];
+#pragma unroll
+  for (int m = 0; m < NS; ++m)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) gw[m][q] = T(0);
+  if (RECON == 0) {
+    // W_L = W_R = W_p, with the face floors
+    T w0[7];
+    load_dir<A>(W, N, c, w0);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      T a = gl[q], b = gr[q];
+      if (q == 0 && w0[0] < T(g.rho_floor)) a = b = T(0);
+      if (q == 4 && w0[4] < T(g.p_floor)) a = b = T(0);
+      gw[1][q] = a + b;
+    }
+  } else if (RECON == 1) {
+    T wm[7], w0[7], wp[7];
+    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
+    load_dir<A>(W, N, c, w0);
+    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
+    plmc_vjp<T>(T(g.gamma), T(g.rho_floor), T(g.p_floor), wm, w0, wp, bn, gl, gr, gw[0], gw[1], gw[2], gbn);
+  } else {
+    T w[5][7];
+#pragma unroll
+    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
+    ppmc_vjp<T>(T(g.gamma), T(g.rho_floor), T(g.p_floor), w, bn, gl, gr, (T(*)[7])gw, gbn);
+  }
+#pragma unroll
+  for (int m = 0; m < NS; ++m)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) S[((long long)m * 7 + q) * N + c] = gw[m][q];
+  S[(long long)NS * 7 * N + c] = gbn;
+}
+
+// cell p gathers slot m from cell p - (m - h) along A, h = NS/2
+template <class T, int RECON, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_recon_gather(Grid g, const T* __restrict__ S, T* __restrict__ gW) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  constexpr int NS = RECON == 2 ? 5 : 3;
+  constexpr int H = NS / 2;
+  T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    // the owner o has this cell at offset (m - H): o = p - (m - H)
+    const long long o = nb<A>(g, ci.i, ci.j, ci.k, H - m);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) acc[q] += S[((long long)m * 7 + q) * N + o];
+  }
+  add_dir<A>(gW, N, c, acc);
+  gW[(5 + A) * N + c] += S[(long long)NS * 7 * N + c];
+}
+
+// ------------------------------------------------ R5 / R10: primitives --
+// W = prim(hydro, B_cc): cotangent of the hydro fields (g5 out) and of B_cc
+// (gBcc out).  HALF: hydro from the stored half state; else from U^n.
+template <class T, bool HALF>
+__global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __restrict__ U, const double* __restrict__ Uh,
+                                                     const T* __restrict__ Bh, const T* __restrict__ gW,
+                                                     double* __restrict__ g5, T* __restrict__ gBcc) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const long long N = g.N, c = cidx(g, i, j, k);
+  double h5[5], b[3];
+  if (HALF) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) h5[f] = Uh[f * N + c];
+    b[0] = 0.5 * ((double)Bh[nb<0>(g, i, j, k, -1)] + (double)Bh[c]);
+    b[1] = 0.5 * ((double)Bh[N + nb<1>(g, i, j, k, -1)] + (double)Bh[N + c]);
+    b[2] = 0.5 * ((double)Bh[2 * N + nb<2>(g, i, j, k, -1)] + (double)Bh[2 * N + c]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 5; ++f) h5[f] = U[f * N + c];
+    b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
+    b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
+    b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
+  }
+  double gw8[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) gw8[f] = (double)gW[f * N + c];
+  double o5[5], gb[3] = {0.0, 0.0, 0.0};
+  prim_vjp(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) g5[f * N + c] = o5[f];
+  gBcc[c] = T(gb[0]);
+  gBcc[N + c] = T(gb[1]);
+  gBcc[2 * N + c] = T(gb[2]);
+}
+
+// R11: predictor faces: gU faces += gBf_a(p) + (1/2)(gBcc_a(p) + gBcc_a(p + e_a)); gU hydro += g5
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_adj_faces_n(Grid g, const double* __restrict__ g5, const T* __restrict__ gBcc,
+                                                        const T* __restrict__ gBf, double* __restrict__ gU) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const long long N = g.N, c = cidx(g, i, j, k);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) gU[f * N + c] += g5[f * N + c];
+  gU[5 * N + c] += face_cot<T, 0>(g, nullptr, gBcc, gBf, i, j, k);
+  gU[6 * N + c] += face_cot<T, 1>(g, nullptr, gBcc, gBf, i, j, k);
+  gU[7 * N + c] += face_cot<T, 2>(g, nullptr, gBcc, gBf, i, j, k);
+}
+
+// forward half update that also keeps the hydro half state (for R5)
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* __restrict__ U0, const T* __restrict__ F,
+                                                          const T* __restrict__ E, double dt, T* __restrict__ W,
+                                                          T* __restrict__ Bh, double* __restrict__ Uh) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const int i = ci.i, j = ci.j, k = ci.k;
+  const double h = 0.5 * dt;
+  const long long N = g.N, c = cidx(g, i, j, k);
+  constexpr bool X = sizeof(T) == 8;
+  double u5[5];
+  hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
+  const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
+  const double by = face_update<T, X, 1>(g, U0, E, h, i, j, k);
+  const double bz = face_update<T, X, 2>(g, U0, E, h, i, j, k);
+  const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
+  const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
+  const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
+  Bh[c] = T(bx);
+  Bh[N + c] = T(by);
+  Bh[2 * N + c] = T(bz);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) Uh[f * N + c] = u5[f];
+  const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
+  const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
+  T w8[8];
+  store_w<T>(g, W, c, p, w8);
+}
+
+// ---------------------------------------------- batch HLLD VJP (testing) --
+template <class T>
+__global__ void k_hlld_vjp_batch(int n, double gamma, const double* __restrict__ wl, const double* __restrict__ wr,
+                                 const double* __restrict__ bn, const double* __restrict__ gf, double* __restrict__ gwl,
+                                 double* __restrict__ gwr, double* __restrict__ gbn, double* __restrict__ f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  T a[7], b[7], g[7], ga[7], gb[7], ff[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    a[q] = T(wl[7 * t + q]);
+    b[q] = T(wr[7 * t + q]);
+    g[q] = T(gf[7 * t + q]);
+    ga[q] = gb[q] = T(0);
+  }
+  T gn = T(0);
+  hlld_vjp<T>(T(gamma), a, b, T(bn[t]), g, ga, gb, gn);
+  hlld<T>(T(gamma), a, b, T(bn[t]), ff);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gwl[7 * t + q] = ga[q];
+    gwr[7 * t + q] = gb[q];
+    f[7 * t + q] = ff[q];
+  }
+  gbn[t] = gn;
+}
+
+// --------------------------------------------------------------- launchers --
+
+template <class T>
+void AdjLaunch<T>::floors(const Grid& g, const double* U, const T* F, const T* E, double dt, const double* gUp, double* gU,
+                     T* gBccF, cudaStream_t s) {
+    k_adj_floors<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dt, gUp, gU, gBccF);
+  }
+template <class T>
+void AdjLaunch<T>::update(const Grid& g, int mode, double h, const double* g5src, const double* gUpF, const T* gBcc,
+                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s) {
+    if (mode == 0)
+      k_adj_update<T, 0><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE);
+    else
+      k_adj_update<T, 1><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE);
+  }
+template <class T>
+void AdjLaunch<T>::emf(const Grid& g, const T* W, const T* F, const T* gE, T* gF, T* gW, cudaStream_t s) {
+    k_adj_emf<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, gE, gF, gW);
+  }
+template <class T>
+void AdjLaunch<T>::hlld(const Grid& g, int a, bool pcm, const T* WL, const T* WR, const T* Wn, const double* U, const T* Bh,
+                   const T* gF, T* gWL, T* gWR, T* gBf, cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (pcm) {
+      if (a == 0) k_adj_hlld<T, 0, true><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+      if (a == 1) k_adj_hlld<T, 1, true><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+      if (a == 2) k_adj_hlld<T, 2, true><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+    } else {
+      if (a == 0) k_adj_hlld<T, 0, false><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+      if (a == 1) k_adj_hlld<T, 1, false><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+      if (a == 2) k_adj_hlld<T, 2, false><<<gr, bl, 0, s>>>(g, WL, WR, Wn, U, Bh, gF, gWL, gWR, gBf);
+    }
+  }
+template <class T>
+void AdjLaunch<T>::pcm_gather(const Grid& g, int a, const T* gWL, const T* gWR, T* gW, cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (a == 0) k_adj_pcm_gather<T, 0><<<gr, bl, 0, s>>>(g, gWL, gWR, gW);
+    if (a == 1) k_adj_pcm_gather<T, 1><<<gr, bl, 0, s>>>(g, gWL, gWR, gW);
+    if (a == 2) k_adj_pcm_gather<T, 2><<<gr, bl, 0, s>>>(g, gWL, gWR, gW);
+  }
+template <class T>
+template <int R>
+void AdjLaunch<T>::recon_r(const Grid& g, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW,
+                                       cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (a == 0) {
+      k_adj_recon<T, R, 0><<<gr, bl, 0, s>>>(g, W, gWL, gWR, S);
+      k_adj_recon_gather<T, R, 0><<<gr, bl, 0, s>>>(g, S, gW);
+    }
+    if (a == 1) {
+      k_adj_recon<T, R, 1><<<gr, bl, 0, s>>>(g, W, gWL, gWR, S);
+      k_adj_recon_gather<T, R, 1><<<gr, bl, 0, s>>>(g, S, gW);
+    }
+    if (a == 2) {
+      k_adj_recon<T, R, 2><<<gr, bl, 0, s>>>(g, W, gWL, gWR, S);
+      k_adj_recon_gather<T, R, 2><<<gr, bl, 0, s>>>(g, S, gW);
+    }
+  }
+template <class T>
+void AdjLaunch<T>::recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s) {
+    if (rc == 0) recon_r<0>(g, a, W, gWL, gWR, S, gW, s);
+    if (rc == 1) recon_r<1>(g, a, W, gWL, gWR, S, gW, s);
+    if (rc == 2) recon_r<2>(g, a, W, gWL, gWR, S, gW, s);
+  }
+template <class T>
+void AdjLaunch<T>::prim(const Grid& g, bool half, const double* U, const double* Uh, const T* Bh, const T* gW, double* g5,
+                   T* gBcc, cudaStream_t s) {
+    if (half)
+      k_adj_prim<T, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, Uh, Bh, gW, g5, gBcc);
+    else
+      k_adj_prim<T, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, Uh, Bh, gW, g5, gBcc);
+  }
+template <class T>
+void AdjLaunch<T>::faces_n(const Grid& g, const double* g5, const T* gBcc, const T* gBf, double* gU, cudaStream_t s) {
+    k_adj_faces_n<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, g5, gBcc, gBf, gU);
+  }
+template <class T>
+void AdjLaunch<T>::fwd_half_keep(const Grid& g, const double* U, const T* F, const T* E, double dt, T* W, T* Bh, double* Uh,
+                            cudaStream_t s) {
+    k_fwd_half_keep<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dt, W, Bh, Uh);
+  }
+template <class T>
+void AdjLaunch<T>::hlld_batch(int n, double gamma, const double* wl, const double* wr, const double* bn, const double* gf,
+                         double* gwl, double* gwr, double* gbn, double* f, cudaStream_t s) {
+    k_hlld_vjp_batch<T><<<(n + 127) / 128, 128, 0, s>>>(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f);
+  }
+
+}  // namespace mhd

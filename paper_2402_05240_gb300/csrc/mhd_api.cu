@@ -34,6 +34,8 @@ struct mhd_ctx {
   double* red;                  // diagnostics partials
   double* host_state;           // lazily allocated device copy for mhd_run_host
   size_t red_count;
+  void* adj_ws;                 // adjoint workspace, allocated by the first adjoint call
+  size_t adj_bytes;
   // optional per-stage CUDA-event timing (mhd_profile_enable)
   int prof_on;
   std::vector<ProfRec> prof;
@@ -177,6 +179,129 @@ template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
   return cuda_status();
 }
 
+// ---- adjoint ----------------------------------------------------------------
+// Adjoint workspace (compute type T): forward intermediates W^n[8], F^n[21],
+// W^{n+1/2}[8], B^{n+1/2}[3], W_L/W_R of the three axes [21+21], F^{n+1/2}[21],
+// E[3]; cotangents gF[21], gE[3], gW[8], gWL[7], gWR[7], recon slots[36],
+// gBf[3], gBcc[3], gBccF[3]; in double the half-step hydro state[5] and g5[5].
+size_t adj_bytes_of(const mhd_config& c) {
+  const size_t N = (size_t)c.nx * c.ny * c.nz;
+  const size_t ts = c.precision == MHD_FP32_BULK ? 4 : 8;
+  return up(197 * N * ts) + up(10 * N * sizeof(double)) + 4 * kAlign;
+}
+
+template <class T> struct AdjView {
+  T *Wn, *Fn, *Wh, *Bh, *WLa, *WRa, *Fh, *Eh, *gF, *gE, *gW, *gWL, *gWR, *gS, *gBf, *gBcc, *gBccF;
+  double *Uh, *g5;
+};
+
+template <class T> int adj_view(mhd_ctx* c, AdjView<T>& v) {
+  if (!c->adj_ws) {
+    const size_t b = adj_bytes_of(c->cfg);
+    cudaGetLastError();
+    if (cudaMalloc(&c->adj_ws, b) != cudaSuccess) {
+      cudaGetLastError();
+      c->adj_ws = nullptr;
+      return MHD_ERR_OOM;
+    }
+    c->adj_bytes = b;
+  }
+  const size_t N = (size_t)c->g.N;
+  T* p = static_cast<T*>(c->adj_ws);
+  auto take = [&](size_t n) {
+    T* q = p;
+    p += n * N;
+    return q;
+  };
+  v.Wn = take(8);
+  v.Fn = take(21);
+  v.Wh = take(8);
+  v.Bh = take(3);
+  v.WLa = take(21);
+  v.WRa = take(21);
+  v.Fh = take(21);
+  v.Eh = take(3);
+  v.gF = take(21);
+  v.gE = take(3);
+  v.gW = take(8);
+  v.gWL = take(7);
+  v.gWR = take(7);
+  v.gS = take(36);
+  v.gBf = take(3);
+  v.gBcc = take(3);
+  v.gBccF = take(3);
+  char* d = reinterpret_cast<char*>(c->adj_ws) + up(197 * N * sizeof(T));
+  v.Uh = reinterpret_cast<double*>(d);
+  v.g5 = v.Uh + 5 * N;
+  return MHD_OK;
+}
+
+template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, const double* gUp, double* gU) {
+  AdjView<T> b;
+  int st = adj_view<T>(c, b);
+  if (st != MHD_OK) return st;
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  const long long N = g.N;
+  double* U = const_cast<double*>(Un);  // read only: k_prim writes U only with floors on
+  const int rc = c->cfg.recon;
+  // forward recompute (Steps 1-8)
+  Launch<T>::prim(g, U, b.Wn, nullptr, c->flags, nullptr, s);
+  Launch<T>::flux_pcm(g, b.Wn, U, b.Fn, s);
+  Launch<T>::emf(g, b.Wn, b.Fn, b.Eh, s);
+  mhd::AdjLaunch<T>::fwd_half_keep(g, U, b.Fn, b.Eh, dt, b.Wh, b.Bh, b.Uh, s);
+  for (int a = 0; a < 3; ++a) {
+    Launch<T>::recon(g, rc, a, b.Wh, b.WLa + a * 7 * N, b.WRa + a * 7 * N, s);
+    Launch<T>::flux_hlld(g, a, b.WLa + a * 7 * N, b.WRa + a * 7 * N, b.Bh, b.Fh, s);
+  }
+  Launch<T>::emf(g, b.Wh, b.Fh, b.Eh, s);
+  // reverse: Step 9 (floors, full update)
+  mhd::AdjLaunch<T>::floors(g, U, b.Fh, b.Eh, dt, gUp, gU, b.gBccF, s);
+  mhd::AdjLaunch<T>::update(g, 0, dt, gU, gUp + 5 * N, b.gBccF, nullptr, gU, b.gF, b.gE, s);
+  // Step 8 (edge fields, half-step reference fields)
+  mhd::AdjLaunch<T>::emf(g, b.Wh, b.Fh, b.gE, b.gF, b.gW, s);
+  // Steps 7-6 per axis (HLLD, reconstruction)
+  for (int a = 0; a < 3; ++a) {
+    mhd::AdjLaunch<T>::hlld(g, a, false, b.WLa + a * 7 * N, b.WRa + a * 7 * N, nullptr, nullptr, b.Bh, b.gF, b.gWL,
+                            b.gWR, b.gBf, s);
+    mhd::AdjLaunch<T>::recon(g, rc, a, b.Wh, b.gWL, b.gWR, b.gS, b.gW, s);
+  }
+  // Step 5 (primitives of the half state, half update)
+  mhd::AdjLaunch<T>::prim(g, true, U, b.Uh, b.Bh, b.gW, b.g5, b.gBcc, s);
+  mhd::AdjLaunch<T>::update(g, 1, 0.5 * dt, b.g5, nullptr, b.gBcc, b.gBf, gU, b.gF, b.gE, s);
+  // Step 4 (edge fields, reference fields of W^n)
+  mhd::AdjLaunch<T>::emf(g, b.Wn, b.Fn, b.gE, b.gF, b.gW, s);
+  // Steps 3-2 (HLLD on PCM states)
+  for (int a = 0; a < 3; ++a) {
+    mhd::AdjLaunch<T>::hlld(g, a, true, nullptr, nullptr, b.Wn, U, nullptr, b.gF, b.gWL, b.gWR, b.gBf, s);
+    mhd::AdjLaunch<T>::pcm_gather(g, a, b.gWL, b.gWR, b.gW, s);
+  }
+  // Step 1 (primitives of U^n) and the face cotangents
+  mhd::AdjLaunch<T>::prim(g, false, U, nullptr, nullptr, b.gW, b.g5, b.gBcc, s);
+  mhd::AdjLaunch<T>::faces_n(g, b.g5, b.gBcc, b.gBf, gU, s);
+  return cuda_status();
+}
+
+template <class T>
+int stage_recon_vjp(mhd_ctx* c, const double* U, int axis, int recon, const double* gWL, const double* gWR, double* gU) {
+  AdjView<T> b;
+  int st = adj_view<T>(c, b);
+  if (st != MHD_OK) return st;
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  const long long N = g.N;
+  Launch<T>::prim(g, const_cast<double*>(U), b.Wn, nullptr, c->flags, nullptr, s);
+  Launch<T>::narrow(gWL, b.gWL, 7 * N, s);
+  Launch<T>::narrow(gWR, b.gWR, 7 * N, s);
+  cudaMemsetAsync(b.gW, 0, 8 * N * sizeof(T), s);
+  cudaMemsetAsync(b.gBf, 0, 3 * N * sizeof(T), s);
+  cudaMemsetAsync(gU, 0, 8 * N * sizeof(double), s);
+  mhd::AdjLaunch<T>::recon(g, recon, axis, b.Wn, b.gWL, b.gWR, b.gS, b.gW, s);
+  mhd::AdjLaunch<T>::prim(g, false, U, nullptr, nullptr, b.gW, b.g5, b.gBcc, s);
+  mhd::AdjLaunch<T>::faces_n(g, b.g5, b.gBcc, b.gBf, gU, s);
+  return cuda_status();
+}
+
 // ---- stage entry points ---------------------------------------------------
 template <class T> int stage_prims(mhd_ctx* c, const double* U, double* Wout) {
   Launch<T>::prim(c->g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, c->stream);
@@ -290,6 +415,7 @@ void mhd_destroy(mhd_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
   if (c->host_state) cudaFree(c->host_state);
+  if (c->adj_ws) cudaFree(c->adj_ws);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -385,9 +511,38 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
 }
 
 int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {
-  if (!c || !U_n || !gU_np1 || !gU_n) return MHD_ERR_ARG;
+  if (!c || !U_n || !gU_np1 || !gU_n || gU_np1 == gU_n) return MHD_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
-  return MHD_ERR_ARG;  // not built in this configuration
+  return c->cfg.precision == MHD_FP32_BULK ? adjoint_step<float>(c, U_n, dt, gU_np1, gU_n)
+                                            : adjoint_step<double>(c, U_n, dt, gU_np1, gU_n);
+}
+
+int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
+  int st = check_cfg(cfg);
+  if (st != MHD_OK) return st;
+  if (!bytes) return MHD_ERR_ARG;
+  *bytes = adj_bytes_of(*cfg);
+  return MHD_OK;
+}
+
+int mhd_stage_recon_vjp(mhd_ctx* c, const double* U, int axis, int recon, const double* gWL, const double* gWR,
+                        double* gU) {
+  if (!c || !U || !gWL || !gWR || !gU || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
+    return MHD_ERR_ARG;
+  return c->cfg.precision == MHD_FP32_BULK ? stage_recon_vjp<float>(c, U, axis, recon, gWL, gWR, gU)
+                                            : stage_recon_vjp<double>(c, U, axis, recon, gWL, gWR, gU);
+}
+
+int mhd_stage_hlld_vjp(int n, double gamma, int precision, const double* wl, const double* wr, const double* bn,
+                       const double* gf, double* gwl, double* gwr, double* gbn, double* f, void* stream) {
+  if (n < 0 || !wl || !wr || !bn || !gf || !gwl || !gwr || !gbn || !f || !(gamma > 1.0)) return MHD_ERR_ARG;
+  if (n == 0) return MHD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == MHD_FP32_BULK)
+    mhd::AdjLaunch<float>::hlld_batch(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f, s);
+  else
+    mhd::AdjLaunch<double>::hlld_batch(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f, s);
+  return cuda_status();
 }
 
 int mhd_status(mhd_ctx* c, long long counts[2]) {

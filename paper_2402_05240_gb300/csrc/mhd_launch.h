@@ -30,6 +30,28 @@ template <class T> struct Launch {
   static void narrow(const double* src, T* dst, long long n, cudaStream_t s);
 };
 
+// Launchers of the adjoint (reverse-sweep) kernels for compute type T.
+template <class T> struct AdjLaunch {
+  static void floors(const Grid& g, const double* U, const T* F, const T* E, double dt, const double* gUp, double* gU,
+                     T* gBccF, cudaStream_t s);
+  static void update(const Grid& g, int mode, double h, const double* g5src, const double* gUpF, const T* gBcc,
+                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s);
+  static void emf(const Grid& g, const T* W, const T* F, const T* gE, T* gF, T* gW, cudaStream_t s);
+  static void hlld(const Grid& g, int a, bool pcm, const T* WL, const T* WR, const T* Wn, const double* U, const T* Bh,
+                   const T* gF, T* gWL, T* gWR, T* gBf, cudaStream_t s);
+  static void pcm_gather(const Grid& g, int a, const T* gWL, const T* gWR, T* gW, cudaStream_t s);
+  template <int R>
+  static void recon_r(const Grid& g, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s);
+  static void recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s);
+  static void prim(const Grid& g, bool half, const double* U, const double* Uh, const T* Bh, const T* gW, double* g5,
+                   T* gBcc, cudaStream_t s);
+  static void faces_n(const Grid& g, const double* g5, const T* gBcc, const T* gBf, double* gU, cudaStream_t s);
+  static void fwd_half_keep(const Grid& g, const double* U, const T* F, const T* E, double dt, T* W, T* Bh, double* Uh,
+                            cudaStream_t s);
+  static void hlld_batch(int n, double gamma, const double* wl, const double* wr, const double* bn, const double* gf,
+                         double* gwl, double* gwr, double* gbn, double* f, cudaStream_t s);
+};
+
 void launch_set_dt(double* dt_cur, double value, cudaStream_t s);
 void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
                       unsigned* flags, cudaStream_t s);

@@ -63,6 +63,9 @@ def _load_library():
         "mhd_profile_read": (ip, [vp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "mhd_stage_name": (ctypes.c_char_p, [ip]),
         "mhd_diagnostics_static": (ip, [ctypes.POINTER(mhd_config), vp, vp, dp, dp]),
+        "mhd_adjoint_workspace_bytes": (ip, [ctypes.POINTER(mhd_config), ctypes.POINTER(ctypes.c_size_t)]),
+        "mhd_stage_recon_vjp": (ip, [vp, vp, ip, ip, vp, vp, vp]),
+        "mhd_stage_hlld_vjp": (ip, [ip, ctypes.c_double, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +177,24 @@ def mhd_stage_recon(ctx, U, axis: int, recon: int, WL, WR):
     _check(LIB.mhd_stage_recon(ctx, _ptr(U), int(axis), int(recon), _ptr(WL), _ptr(WR)), "mhd_stage_recon")
 
 
+def mhd_adjoint_workspace_bytes(cfg: mhd_config) -> int:
+    b = ctypes.c_size_t(0)
+    _check(LIB.mhd_adjoint_workspace_bytes(ctypes.byref(cfg), ctypes.byref(b)), "mhd_adjoint_workspace_bytes")
+    return b.value
+
+
+def mhd_stage_recon_vjp(ctx, U, axis: int, recon: int, gWL, gWR, gU):
+    _check(LIB.mhd_stage_recon_vjp(ctx, _ptr(U), int(axis), int(recon), _ptr(gWL), _ptr(gWR), _ptr(gU)),
+           "mhd_stage_recon_vjp")
+
+
+def mhd_stage_hlld_vjp(gamma, precision: int, wl, wr, bn, gf, gwl, gwr, gbn, f, stream=None):
+    s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    n = bn.numel()
+    _check(LIB.mhd_stage_hlld_vjp(int(n), float(gamma), int(precision), _ptr(wl), _ptr(wr), _ptr(bn), _ptr(gf),
+                                  _ptr(gwl), _ptr(gwr), _ptr(gbn), _ptr(f), s), "mhd_stage_hlld_vjp")
+
+
 MHD_NUM_STAGES = 8
 
 
@@ -250,6 +271,18 @@ class Sim:
         E = torch.empty((3,) + self.shape, dtype=torch.float64, device=U.device)
         mhd_stage_edges(self.ctx, U, F.contiguous(), E)
         return E
+
+    def adjoint_step(self, U_n, dt, gU_np1):
+        """gU_n = (dU^{n+1}/dU^n)^T gU_np1 for one step at fixed dt."""
+        gU = torch.empty_like(gU_np1)
+        mhd_adjoint_step(self.ctx, U_n, dt, gU_np1.contiguous(), gU)
+        return gU
+
+    def recon_vjp(self, U, axis, gWL, gWR, recon=None):
+        r = self.cfg.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)
+        gU = torch.empty_like(U)
+        mhd_stage_recon_vjp(self.ctx, U, axis, r, gWL.contiguous(), gWR.contiguous(), gU)
+        return gU
 
     def recon(self, U, axis, recon=None):
         r = self.cfg.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)
