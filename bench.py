@@ -171,6 +171,38 @@ def time_gpu(mhd, torch, U0, n, steps, warmup, recon, precision, barrier):
     return ms / steps, prof, launches, sim, U
 
 
+def time_adjoint(mhd, torch, U0, n, steps, warmup, recon, precision, barrier, fwd_ms):
+    """Times `steps` adjoint steps (VJP of one step at fixed dt, forward
+    recompute included) on the workload state; returns a variants entry."""
+    stream = torch.cuda.current_stream()
+    sim = mhd.Sim(n, n, n, cfl=0.3, recon=recon, precision=precision, stream=stream.cuda_stream)
+    U = U0.clone()
+    dt = sim.dt(U)
+    g = torch.ones_like(U)
+    gout = torch.empty_like(U)
+    for _ in range(warmup):
+        mhd.mhd_adjoint_step(sim.ctx, U, dt, g, gout)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(steps):
+        src, dst = (g, gout) if s % 2 == 0 else (gout, g)
+        mhd.mhd_adjoint_step(sim.ctx, U, dt, src, dst)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    ws = mhd.mhd_adjoint_workspace_bytes(sim.cfg)
+    code, _ = mhd.mhd_status(sim.ctx)
+    sim.close()
+    return {"value": n ** 3 / (ms * 1e-3), "ms_per_step": ms, "ratio_to_forward": ms / fwd_ms,
+            "dtype": "f64" if precision == "fp64" else "f32 (FP64 state)", "adjoint_workspace_gb": ws / 1e9,
+            "status": code}
+
+
 def roofline_of(prof, precision, n3, hbm_peak, peak_kind):
     """Roofline of the dominant stage (largest share of the timed region).
 
@@ -328,6 +360,10 @@ def main():
             "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind), "gpu_launches": launches32}
         sim32.close()
         del U32, sim32
+        adj_steps = max(2, args.steps // 2)
+        variants["adjoint_fp64"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64", barrier, ms64)
+        variants["adjoint_fp32_bulk"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp32_bulk",
+                                                     barrier, ms32)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
