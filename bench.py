@@ -67,9 +67,7 @@ FP64_PEAK_GFLOPS = 1202.6
 # FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes (read + write).  They hold
 # for the kernels as profiled; a kernel changed since has no entry.
 FP64_COUNTERS = {
-    "prim": (225.0, 105.9), "flux_pcm": (1285.7, 231.3), "emf": (111.0, 139.6),
-    "update_half": (336.0, 283.3), "recon": (624.4, 150.4), "flux_hlld": (456.2, 162.3),
-    "update_full": (195.0, 260.3),
+    "emf": (111.0, 139.6),
 }
 
 

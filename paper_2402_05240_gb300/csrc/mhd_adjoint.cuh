@@ -253,11 +253,11 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
     dR[q] = wp[q] - w0[q];
     dC[q] = T(0.5) * (wp[q] - wm[q]);
     const T pr = dL[q] * dR[q];
-    dG[q] = pr > T(0) ? T(2) * pr / (dL[q] + dR[q]) : T(0);
+    dG[q] = pr > T(0) ? T(2) * pr * trcp<T>(dL[q] + dR[q]) : T(0);
   }
   Eig<T> E;
   eig_build<T>(gamma, w0, bn, E);
-  const T ir = T(1) / E.rho;
+  const T ir = E.ir;
   T aL[7], aR[7], aC[7], aG[7], am[7], dW[7];
   eig_left<T>(E, dL, aL);
   eig_left<T>(E, dR, aR);
@@ -493,7 +493,7 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, const T (*w)[7], T bn,
                          T (*gw)[7], T& gbn) {
   Eig<T> E;
   eig_build<T>(gamma, w[2], bn, E);
-  const T ir = T(1) / E.rho;
+  const T ir = E.ir;
   T d[5][7], qs[5][7];
 #pragma unroll
   for (int m = 0; m < 5; ++m) {

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   const double r = rfl ? g.rho_floor : u5[0];
   const double ke = 0.5 * (u5[1] * (u5[1] / r) + u5[2] * (u5[2] / r) + u5[3] * (u5[3] / r));
   const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  const bool pfl = (g.gamma - 1.0) * (u5[4] - ke - me) < g.p_floor;
+  const bool pfl = g.gm1 * (u5[4] - ke - me) < g.p_floor;
   if (pfl) {  // E = p_floor/(gamma-1) + |m|^2/(2 r) + |B_cc|^2/2
     const double gE = g5[4];
     g5[4] = 0.0;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
   // gF_a[comp](p) = -(h/d_a)(g_f(p) - g_f(p + e_a))
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double s = -h / g.d[a];
+    const double s = -h * g.id[a];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const double gv = g5src[f * N + c] - g5src[f * N + cp[a]];
@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
   const double f2_x = face_cot<T, 2>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
   const double f2_y = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
   // k = 0 (E_x): B_y (a=1) with e_z, B_z (a=2) with e_y
-  const double gEx = -(h / g.d[2]) * (gf1 - f1_z) + (h / g.d[1]) * (gf2 - f2_y);
+  const double gEx = -(h * g.id[2]) * (gf1 - f1_z) + (h * g.id[1]) * (gf2 - f2_y);
   // k = 1 (E_y): B_z with e_x, B_x with e_z
-  const double gEy = -(h / g.d[0]) * (gf2 - f2_x) + (h / g.d[2]) * (gf0 - f0_z);
+  const double gEy = -(h * g.id[0]) * (gf2 - f2_x) + (h * g.id[2]) * (gf0 - f0_z);
   // k = 2 (E_z): B_x with e_y, B_y with e_x
-  const double gEz = -(h / g.d[1]) * (gf0 - f0_y) + (h / g.d[0]) * (gf1 - f1_x);
+  const double gEz = -(h * g.id[1]) * (gf0 - f0_y) + (h * g.id[0]) * (gf1 - f1_x);
   gE[c] = T(gEx);
   gE[N + c] = T(gEy);
   gE[2 * N + c] = T(gEz);

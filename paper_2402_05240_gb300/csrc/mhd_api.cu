@@ -156,8 +156,8 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
 template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
-  // arm the reduction word (bytes 0x7f: a huge positive double), then W^0 and dt^0
-  cudaMemsetAsync(c->dtbits, 0x7f, sizeof(unsigned long long), s);
+  // arm the reduction word (+0.0: the maximum of non-negative rates), then W^0 and dt^0
+  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);  // simulated time of this run
   Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
   for (int n = 0; n < nsteps; ++n) {
@@ -373,6 +373,9 @@ int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
   c->g.d[0] = cfg->dx;
   c->g.d[1] = cfg->dy;
   c->g.d[2] = cfg->dz;
+  for (int a = 0; a < 3; ++a) c->g.id[a] = 1.0 / c->g.d[a];
+  c->g.gm1 = cfg->gamma - 1.0;
+  c->g.igm1 = 1.0 / (cfg->gamma - 1.0);
   c->g.gamma = cfg->gamma;
   c->g.rho_floor = cfg->rho_floor;
   c->g.p_floor = cfg->p_floor;
@@ -470,7 +473,7 @@ int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {
 int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
   if (!c || !U || !dt_host) return MHD_ERR_ARG;
   cudaStream_t s = c->stream;
-  cudaMemsetAsync(c->dtbits, 0x7f, sizeof(unsigned long long), s);
+  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   double* Um = const_cast<double*>(U);  // k_prim writes U only when floors are requested
   if (c->cfg.precision == MHD_FP32_BULK)
     Launch<float>::prim(c->g, Um, as<float>(c->W), c->dtbits, c->flags, nullptr, s);

@@ -37,6 +37,15 @@ template <class T> __device__ __forceinline__ T tsqrt(T x);
 template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
 
+// correctly rounded reciprocal (cheaper than a general division) and the
+// library reciprocal square root
+template <class T> __device__ __forceinline__ T trcp(T x);
+template <> __device__ __forceinline__ double trcp<double>(double x) { return __drcp_rn(x); }
+template <> __device__ __forceinline__ float trcp<float>(float x) { return __frcp_rn(x); }
+template <class T> __device__ __forceinline__ T trsqrt(T x);
+template <> __device__ __forceinline__ double trsqrt<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float trsqrt<float>(float x) { return rsqrtf(x); }
+
 template <class T> struct Eps;
 template <> struct Eps<double> { static constexpr double hlld = 1e-8; };
 template <> struct Eps<float> { static constexpr float hlld = 1e-4f; };
@@ -54,7 +63,7 @@ struct PrimD {
 // (gamma P + B^2)^2 - 4 gamma P B_l^2 (over rho^2) as a sum of non-negative terms.
 template <class T>
 __device__ __forceinline__ T fast_speed(T gamma, T rho, T p, T bl, T bt1, T bt2) {
-  T ir = T(1) / rho;
+  T ir = trcp<T>(rho);
   T a2 = gamma * p * ir;
   T t2 = (bt1 * bt1 + bt2 * bt2) * ir;
   T b2 = bl * bl * ir + t2;
@@ -107,17 +116,17 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
   }
   const T dL = SL - wl[1], dR = SR - wr[1];
   const T rdL = wl[0] * dL, rdR = wr[0] * dR;
-  const T iden = T(1) / (rdR - rdL);
+  const T iden = trcp<T>(rdR - rdL);
   const T SM = (rdR * wr[1] - rdL * wl[1] - ptR + ptL) * iden;
   const T pts = (rdR * ptL - rdL * ptR + rdL * rdR * (wr[1] - wl[1])) * iden;
 
   // single-star states of one side: returns rho*, v*, w*, By*, Bz*, E*
   struct Star {
-    T r, v, w, by, bz, e, sq;
+    T r, v, w, by, bz, e, sq, rsq;
   };
   auto star = [&](const T* w, T e, T pt, T S, T d, T rd) {
     Star s;
-    const T iSM = T(1) / (S - SM);
+    const T iSM = trcp<T>(S - SM);
     s.r = rd * iSM;
     const T D = rd * (S - SM) - bn2;
     if (fabs(D) < Eps<T>::hlld * pts) {
@@ -126,7 +135,7 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
       s.by = w[5];
       s.bz = w[6];
     } else {
-      const T iD = T(1) / D;
+      const T iD = trcp<T>(D);
       const T t = bn * (SM - w[1]) * iD;
       s.v = w[2] - w[5] * t;
       s.w = w[3] - w[6] * t;
@@ -137,7 +146,8 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
     const T vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
     const T vbs = SM * bn + s.v * s.by + s.w * s.bz;
     s.e = (d * e - pt * w[1] + pts * SM + bn * (vb - vbs)) * iSM;
-    s.sq = tsqrt<T>(s.r);
+    s.rsq = trsqrt<T>(s.r);
+    s.sq = s.r * s.rsq;
     return s;
   };
   const Star sL = star(wl, eL, ptL, SL, dL, rdL);
@@ -150,9 +160,9 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
   if (dbl) {
     const T sg = bn > T(0) ? T(1) : T(-1);
     const T abn = fabs(bn);
-    SsL = SM - abn / sL.sq;
-    SsR = SM + abn / sR.sq;
-    const T inv = T(1) / (sL.sq + sR.sq);
+    SsL = SM - abn * sL.rsq;
+    SsR = SM + abn * sR.rsq;
+    const T inv = trcp<T>(sL.sq + sR.sq);
     vss = (sL.sq * sL.v + sR.sq * sR.v + (sR.by - sL.by) * sg) * inv;
     wss = (sL.sq * sL.w + sR.sq * sR.w + (sR.bz - sL.bz) * sg) * inv;
     byss = (sL.sq * sR.by + sR.sq * sL.by + sL.sq * sR.sq * (sR.v - sL.v) * sg) * inv;
@@ -188,47 +198,54 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
 // closed-form inverse of the right ones (rows scaled by 1/(2 a^2) for the
 // magnetosonic waves, 1/2 for the Alfven waves).
 template <class T> struct Eig {
-  T rho, sr, isr, a, a2, ia2, af, as, cf, cs, Qf, Qs, Af, As, b1, b2, sg;
+  T rho, ir, sr, isr, a, a2, ia2, af, as, cf, cs, Qf, Qs, Af, As, b1, b2, sg;
 };
 
+// Square roots and divisions are folded into five reciprocal square roots
+// and one square root: 1/sqrt(rho), 1/a, 1/c_f, 1/|B_t|, and
+// q = 1/sqrt(2 s (s + |D|)) with s = c_f^2 - c_s^2, D = a^2 - b^2, giving
+// c_s = a c_a / c_f and the alpha pair (s + |D|) q, 2 a |b_t| q.
 template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w, T bn, Eig<T>& E) {
   E.rho = w[0];
-  const T ir = T(1) / w[0];
-  E.a2 = gamma * w[4] * ir;
-  E.ia2 = T(1) / E.a2;
-  const T ca2 = bn * bn * ir;
+  E.isr = trsqrt<T>(w[0]);
+  E.sr = w[0] * E.isr;
+  E.ir = E.isr * E.isr;
+  E.a2 = gamma * w[4] * E.ir;
+  const T ra = trsqrt<T>(E.a2);
+  E.a = E.a2 * ra;
+  E.ia2 = ra * ra;
+  const T ca2 = bn * bn * E.ir;
   const T bt2r = w[5] * w[5] + w[6] * w[6];
-  const T bt2 = bt2r * ir;
+  const T bt2 = bt2r * E.ir;
   const T b2 = ca2 + bt2;
   const T D = E.a2 - b2;
   const T sd = tsqrt<T>(D * D + T(4) * E.a2 * bt2);
   const T cf2 = T(0.5) * (E.a2 + b2 + sd);
-  const T cs2 = E.a2 * ca2 / cf2;
-  E.cf = tsqrt<T>(cf2);
-  E.cs = tsqrt<T>(cs2);
+  const T rcf = trsqrt<T>(cf2);
+  E.cf = cf2 * rcf;
+  E.cs = E.a * fabs(bn) * E.isr * rcf;
+  const T ibt = bt2r > T(0) ? trsqrt<T>(bt2r) : T(0);
+  const T btn = bt2r * ibt * E.isr;  // |B_t| / sqrt(rho)
   if (sd == T(0)) {
     E.af = T(1);
     E.as = T(0);
   } else if (D >= T(0)) {
-    E.af = tsqrt<T>((sd + D) / (T(2) * sd));
-    E.as = tsqrt<T>(T(2) * E.a2 * bt2 / (sd * (sd + D)));
+    const T q = trsqrt<T>(T(2) * sd * (sd + D));
+    E.af = (sd + D) * q;
+    E.as = T(2) * E.a * btn * q;
   } else {
-    E.af = tsqrt<T>(T(2) * E.a2 * bt2 / (sd * (sd - D)));
-    E.as = tsqrt<T>((sd - D) / (T(2) * sd));
+    const T q = trsqrt<T>(T(2) * sd * (sd - D));
+    E.af = T(2) * E.a * btn * q;
+    E.as = (sd - D) * q;
   }
-  const T bt = tsqrt<T>(bt2r);
-  if (bt == T(0)) {
+  if (bt2r == T(0)) {
     E.b1 = T(0.70710678118654752440);
     E.b2 = T(0.70710678118654752440);
   } else {
-    const T ibt = T(1) / bt;
     E.b1 = w[5] * ibt;
     E.b2 = w[6] * ibt;
   }
   E.sg = bn >= T(0) ? T(1) : T(-1);
-  E.sr = tsqrt<T>(w[0]);
-  E.isr = T(1) / E.sr;
-  E.a = tsqrt<T>(E.a2);
   const T a = E.a;
   E.Qf = E.cf * E.af * E.sg;
   E.Qs = E.cs * E.as * E.sg;
@@ -239,7 +256,7 @@ template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w
 // characteristic amplitudes q = L dw
 template <class T> __device__ __forceinline__ void eig_left(const Eig<T>& E, const T* dw, T* q) {
   const T n = T(0.5) * E.ia2;
-  const T ir = T(1) / E.rho;
+  const T ir = E.ir;
   const T bv = E.b1 * dw[2] + E.b2 * dw[3];
   const T bb = (E.b1 * dw[5] + E.b2 * dw[6]) * E.isr;
   const T sa = E.a;
@@ -289,7 +306,7 @@ __device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T*
     dR[q] = wp[q] - w0[q];
     dC[q] = T(0.5) * (wp[q] - wm[q]);
     const T pr = dL[q] * dR[q];
-    dG[q] = pr > T(0) ? T(2) * pr / (dL[q] + dR[q]) : T(0);
+    dG[q] = pr > T(0) ? T(2) * pr * trcp<T>(dL[q] + dR[q]) : T(0);
   }
   Eig<T> E;
   eig_build<T>(gamma, w0, bn, E);

@@ -37,49 +37,57 @@ __device__ __forceinline__ CellIdx cell_of_thread(const Grid& g) {
 
 inline dim3 grid_of(const Grid& g) { return dim3((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, g.n[2]); }
 
-// positive doubles order like their bit patterns: min via integer atomicMin
-__device__ __forceinline__ void block_min_to(double v, unsigned long long* dst) {
-  __shared__ double red[BX * BY / 32];
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+// Positive doubles order like their bit patterns: the maximum inverse
+// crossing time goes through an integer atomicMax.  The block reduces in the
+// compute type and converts once.
+template <class T> __device__ __forceinline__ void block_max_to(T v, unsigned long long* dst) {
+  __shared__ T red[BX * BY / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int t = threadIdx.y * BX + threadIdx.x;
   if ((t & 31) == 0) red[t >> 5] = v;
   __syncthreads();
   if (t == 0) {
-    double m = red[0];
-    for (int w = 1; w < BX * BY / 32; ++w) m = fmin(m, red[w]);
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
-    if (bits < *(volatile unsigned long long*)dst) atomicMin(dst, bits);
+    T m = red[0];
+    for (int w = 1; w < BX * BY / 32; ++w) m = fmax(m, red[w]);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong((double)m);
+    if (bits > *(volatile unsigned long long*)dst) atomicMax(dst, bits);
   }
 }
 
-// crossing time min over l of d_l / (|v_l| + c_f,l) of one cell (Eq. dt)
-template <class T> __device__ __forceinline__ double cell_crossing(const Grid& g, const T* w8) {
-  double best = 1e300;
+// inverse crossing time max over l of (|v_l| + c_f,l) / d_l of one cell; the
+// step is dt = C_CFL / (max over cells) (Eq. dt)
+template <class T> __device__ __forceinline__ T cell_inv_crossing(const Grid& g, const T* w8) {
+  T best = T(0);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const T cf = fast_speed<T>(T(g.gamma), w8[0], w8[4], w8[5 + l], w8[5 + (l + 1) % 3], w8[5 + (l + 2) % 3]);
-    const T s = fabs(w8[1 + l]) + cf;
-    best = fmin(best, g.d[l] / (double)s);
+    best = fmax(best, (fabs(w8[1 + l]) + cf) * T(g.id[l]));
   }
   return best;
 }
 
-// primitives from a double state of one cell (same arithmetic as the double-precision recovery)
-__device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, double m1, double m2, double e,
-                                           const double* b) {
+// primitives from a double state of one cell: rho' = max(rho, floor),
+// v = m / rho', P' = max((gamma-1)(E - m.v/2 - |B_cc|^2/2), floor)
+__device__ __forceinline__ PrimD prim_core_ir(const Grid& g, double rho, double ir, double m0, double m1, double m2,
+                                              double e, const double* b) {
   PrimD w;
   w.b[0] = b[0];
   w.b[1] = b[1];
   w.b[2] = b[2];
-  w.rho = fmax(r, g.rho_floor);
-  const double ir = 1.0 / w.rho;
+  w.rho = rho;
   w.v[0] = m0 * ir;
   w.v[1] = m1 * ir;
   w.v[2] = m2 * ir;
   const double ke = 0.5 * (m0 * w.v[0] + m1 * w.v[1] + m2 * w.v[2]);
   const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  w.p = fmax((g.gamma - 1.0) * (e - ke - me), g.p_floor);
+  w.p = fmax(g.gm1 * (e - ke - me), g.p_floor);
   return w;
+}
+
+__device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, double m1, double m2, double e,
+                                           const double* b) {
+  const double rho = fmax(r, g.rho_floor);
+  return prim_core_ir(g, rho, __drcp_rn(rho), m0, m1, m2, e, b);
 }
 
 template <class T>
@@ -105,7 +113,7 @@ template <class T>
 __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
                                                  unsigned* flags, unsigned long long* floors) {
   const CellIdx ci = cell_of_thread(g);
-  double cross = 1e300;
+  T inv = T(0);
   if (ci.ok) {
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = cidx(g, i, j, k), N = g.N;
@@ -116,27 +124,28 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     double r = U[c], e = U[4 * N + c];
     const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
     if (!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) atomicOr(flags, 1u);
+    if (floors && r < g.rho_floor) {
+      r = g.rho_floor;
+      U[c] = r;
+      atomicAdd(&floors[0], 1ull);
+    }
+    const double rho = fmax(r, g.rho_floor);
+    const double ir = __drcp_rn(rho);
     if (floors) {
-      if (r < g.rho_floor) {
-        r = g.rho_floor;
-        U[c] = r;
-        atomicAdd(&floors[0], 1ull);
-      }
-      const double ir = 1.0 / r;
       const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
       const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-      if ((g.gamma - 1.0) * (e - ke - me) < g.p_floor) {
-        e = g.p_floor / (g.gamma - 1.0) + ke + me;
+      if (g.gm1 * (e - ke - me) < g.p_floor) {
+        e = g.p_floor * g.igm1 + ke + me;
         U[4 * N + c] = e;
         atomicAdd(&floors[1], 1ull);
       }
     }
-    const PrimD p = prim_core(g, r, m0, m1, m2, e, b);
+    const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
     T w8[8];
     store_w<T>(g, W, c, p, w8);
-    if (dtbits) cross = cell_crossing<T>(g, w8);
+    if (dtbits) inv = cell_inv_crossing<T>(g, w8);
   }
-  if (dtbits) block_min_to(cross, dtbits);
+  if (dtbits) block_max_to<T>(inv, dtbits);
 }
 
 // directional 7-vector (rho, v_n, v_t1, v_t2, P, B_t1, B_t2) of cell q
@@ -290,10 +299,10 @@ __device__ __forceinline__ double face_curl(const Grid& g, const T* __restrict__
   const T* EB = E + (long long)B * N;
   const T* EC = E + (long long)C * N;
   if (EXACT) {
-    return ((double)EC[c] - (double)EC[nb<B>(g, i, j, k, -1)]) / g.d[B] -
-           ((double)EB[c] - (double)EB[nb<C>(g, i, j, k, -1)]) / g.d[C];
+    return ((double)EC[c] - (double)EC[nb<B>(g, i, j, k, -1)]) * g.id[B] -
+           ((double)EB[c] - (double)EB[nb<C>(g, i, j, k, -1)]) * g.id[C];
   }
-  return (double)((EC[c] - EC[nb<B>(g, i, j, k, -1)]) / T(g.d[B]) - (EB[c] - EB[nb<C>(g, i, j, k, -1)]) / T(g.d[C]));
+  return (double)((EC[c] - EC[nb<B>(g, i, j, k, -1)]) * T(g.id[B]) - (EB[c] - EB[nb<C>(g, i, j, k, -1)]) * T(g.id[C]));
 }
 
 // solver-frame component of the global field f (0 rho, 1-3 m, 4 E) in the flux of axis a
@@ -312,6 +321,7 @@ __device__ __forceinline__ void hydro_update(const Grid& g, const double* __rest
                                              double h, int i, int j, int k, double* out5) {
   const long long N = g.N, c = cidx(g, i, j, k);
   const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
+  const double hd[3] = {h * g.id[0], h * g.id[1], h * g.id[2]};
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
     if (EXACT) {
@@ -319,7 +329,7 @@ __device__ __forceinline__ void hydro_update(const Grid& g, const double* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        acc -= (h / g.d[a]) * ((double)Fa[c] - (double)Fa[cm[a]]);
+        acc -= hd[a] * ((double)Fa[c] - (double)Fa[cm[a]]);
       }
       out5[f] = acc;
     } else {
@@ -327,7 +337,7 @@ __device__ __forceinline__ void hydro_update(const Grid& g, const double* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        inc -= T(h / g.d[a]) * (Fa[c] - Fa[cm[a]]);
+        inc -= T(hd[a]) * (Fa[c] - Fa[cm[a]]);
       }
       out5[f] = U0[f * N + c] + (double)inc;
     }
@@ -408,16 +418,16 @@ template <class T> __global__ void k_narrow(const double* __restrict__ src, T* _
 // --------------------------------------------------------- small kernels --
 __global__ void k_set_dt(double* dt_cur, double value) { dt_cur[0] = value; }
 
-// dt = cfl * min crossing; records it and re-arms the reduction word
+// dt = cfl / max inverse crossing time; records it and re-arms the reduction word
 __global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int s,
                             unsigned* flags) {
   const double m = __longlong_as_double((long long)dtbits[0]);
-  const double dt = cfl * m;
+  const double dt = cfl / m;
   if (!(dt > 0.0) || !isfinite(dt)) atomicOr(flags, 2u);
   dt_cur[0] = dt;
   dt_cur[1] += dt;  // simulated time of the current run
   if (dt_log) dt_log[s] = dt;
-  dtbits[0] = 0x7ff0000000000000ull;  // +inf
+  dtbits[0] = 0ull;  // +0.0
 }
 
 // ------------------------------------------------------------ diagnostics --
@@ -438,9 +448,9 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_partial(Grid g, const double* _
     const int k = (int)(c / ((long long)g.n[0] * g.n[1]));
 #pragma unroll
     for (int f = 0; f < 8; ++f) v[f] = U[f * N + c];
-    const double dv = (U[5 * N + c] - U[5 * N + nb<0>(g, i, j, k, -1)]) / g.d[0] +
-                      (U[6 * N + c] - U[6 * N + nb<1>(g, i, j, k, -1)]) / g.d[1] +
-                      (U[7 * N + c] - U[7 * N + nb<2>(g, i, j, k, -1)]) / g.d[2];
+    const double dv = (U[5 * N + c] - U[5 * N + nb<0>(g, i, j, k, -1)]) * g.id[0] +
+                      (U[6 * N + c] - U[6 * N + nb<1>(g, i, j, k, -1)]) * g.id[1] +
+                      (U[7 * N + c] - U[7 * N + nb<2>(g, i, j, k, -1)]) * g.id[2];
     v[8] = fabs(dv);
   }
 #pragma unroll

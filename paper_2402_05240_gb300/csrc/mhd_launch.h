@@ -9,7 +9,9 @@ struct Grid {
   int n[3];          // nx, ny, nz
   long long N;       // nx * ny * nz
   double d[3];       // dx, dy, dz
+  double id[3];      // 1/dx, 1/dy, 1/dz
   double gamma;
+  double gm1, igm1;  // gamma - 1 and 1/(gamma - 1)
   double rho_floor, p_floor;
   double cfl;
 };

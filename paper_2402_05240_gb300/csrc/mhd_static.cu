@@ -71,6 +71,9 @@ extern "C" int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev
   g.d[0] = cfg->dx;
   g.d[1] = cfg->dy;
   g.d[2] = cfg->dz;
+  for (int a = 0; a < 3; ++a) g.id[a] = 1.0 / g.d[a];
+  g.gm1 = cfg->gamma - 1.0;
+  g.igm1 = cfg->gamma > 1.0 ? 1.0 / (cfg->gamma - 1.0) : 0.0;
   g.gamma = cfg->gamma;
   g.rho_floor = cfg->rho_floor;
   g.p_floor = cfg->p_floor;
