@@ -282,6 +282,34 @@ def run_reference(args):
     return 0
 
 
+def run_workload(args, mhd, torch, rank):
+    """One of the extra measurements; prints one JSON line on rank 0."""
+    from paper_2402_05240_gb300 import workloads as Wk
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if args.workload == "precision512":
+        r = Wk.precision_compare(mhd, torch, n=args.n if args.n != 256 else 512, steps=args.steps,
+                                 warmup=args.warmup, recon="ppmc")
+        value, ms, dtype = r["fp64"]["value"], r["fp64"]["ms_per_step"], "f64"
+        wl = f"turbulent box {r['n']}^3, PPMC + HLLD, FP64 vs FP32-bulk, {r['steps']} steps"
+    elif args.workload == "adjoint_rollout":
+        r = Wk.adjoint_rollout(mhd, torch, n=args.n, steps=100, every=10)
+        value, ms, dtype = r["backward_cell_updates_per_s"], r["backward_s"] / r["steps"] * 1e3, "f32 (FP64 state)"
+        wl = f"blast beta=0.1 {r['n']}^3, PPMC + HLLD, FP32-bulk, 100-step adjoint rollout, checkpoints every 10"
+    else:
+        n = args.n if args.n != 256 else 459
+        r = Wk.slow_wave(mhd, torch, n=n, steps=args.steps, warmup=args.warmup)
+        value, ms, dtype = r["value"], r["ms_per_step"], "f64"
+        wl = f"slow magnetosonic wave {n}^3 (B = (1, 1.5, 0)), PLMC + HLLD, FP64"
+    clk = clocks.stop()
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                          "config": {"workload": wl}, "clocks": clk, "result": r}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,6 +322,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="turbulent",
+                    choices=["turbulent", "precision512", "adjoint_rollout", "slow_wave"],
+                    help="turbulent: the default step timing; the others are the extra measurements of "
+                         "paper_2402_05240_gb300.workloads (one JSON line each)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -318,6 +350,9 @@ def main():
     from paper_2402_05240_gb300 import build
     build.build()
     from paper_2402_05240_gb300 import mhd
+
+    if args.workload != "turbulent":
+        return run_workload(args, mhd, torch, rank)
 
     n = args.n
     n3 = n ** 3

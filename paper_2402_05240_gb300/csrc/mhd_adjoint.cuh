@@ -74,6 +74,11 @@ __device__ __forceinline__ void eig_build_dual(T gamma, Dl<T> rho, Dl<T> p, Dl<T
   if (bt.v == T(0)) {
     E.b1 = Dl<T>(T(0.70710678118654752440));
     E.b2 = Dl<T>(T(0.70710678118654752440));
+  } else if (bt2r.v < T(1e-12) * (bn.v * bn.v + gamma * p.v)) {
+    // |B_t| below 1e-6 sqrt(B_n^2 + gamma P): the direction B_t/|B_t| is held
+    // fixed (its exact derivative grows like 1/|B_t| at the degeneracy)
+    E.b1 = Dl<T>(by.v / bt.v);
+    E.b2 = Dl<T>(bz.v / bt.v);
   } else {
     E.b1 = by / bt;
     E.b2 = bz / bt;
@@ -324,10 +329,12 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
   for (int q = 0; q < 7; ++q) {
     const T pr = dL[q] * dR[q];
     if (pr > T(0)) {
+      // d dG/d dL = 2 (dR/s)^2, d dG/d dR = 2 (dL/s)^2 with s = dL + dR; the
+      // ratios are bounded by 1, so nothing under- or overflows when s is tiny
       const T s = dL[q] + dR[q];
-      const T is2 = T(1) / (s * s);
-      gdL[q] += gdG[q] * T(2) * dR[q] * dR[q] * is2;
-      gdR[q] += gdG[q] * T(2) * dL[q] * dL[q] * is2;
+      const T rR = dR[q] / s, rL = dL[q] / s;
+      gdL[q] += gdG[q] * T(2) * rR * rR;
+      gdR[q] += gdG[q] * T(2) * rL * rL;
     }
     gwp[q] += T(0.5) * gdC[q] + gdR[q];
     gwm[q] += -T(0.5) * gdC[q] - gdL[q];
@@ -404,8 +411,10 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
     g_qp += gdqp;
     if (s4 > 0) {  // r = C d2_x / d2f; s4 == 0 gives r = 1 (constant)
       const T num = s4 == 1 ? d2m1 : (s4 == 2 ? d20 : d2p1);
+      (void)num;
       const T gnum = gr * T(1.25) / d2f;
-      const T gd2f = -gr * T(1.25) * num / (d2f * d2f);
+      // d r / d d2f = -r / d2f, written without squaring d2f (tiny in quiet regions)
+      const T gd2f = -gr * r / d2f;
       if (s4 == 1) g2m1 += gnum;
       if (s4 == 2) g20 += gnum;
       if (s4 == 3) g2p1 += gnum;
