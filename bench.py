@@ -209,7 +209,7 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind):
     FP32-bulk: achieved = algorithmic bytes per launch / launch time against
     the measured HBM copy bandwidth.
     """
-    T = 8 if precision == "fp64" else 4
+    T = 4 if precision == "fp32_bulk" else 8
     sb = stage_bytes(T)
     total = sum(v[0] for v in prof.values())
     name, (ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
@@ -393,6 +393,15 @@ def main():
             "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind), "gpu_launches": launches32}
         sim32.close()
         del U32, sim32
+        msdf, profdf, launchesdf, simdf, Udf = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
+                                                        "fp64_df", barrier)
+        variants["fp64_df"] = {
+            "value": world * n3 / (msdf * 1e-3), "ms_per_step": msdf,
+            "dtype": "double-float (float pairs) on FP32 pipes, FP64 state",
+            "roofline": roofline_of(profdf, "fp64_df", n3, hbm_peak, peak_kind), "gpu_launches": launchesdf,
+            "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in profdf.items()}}
+        simdf.close()
+        del Udf, simdf
         adj_steps = max(2, args.steps // 2)
         variants["adjoint_fp64"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64", barrier, ms64)
         variants["adjoint_fp32_bulk"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp32_bulk",

@@ -50,6 +50,13 @@ extern "C" {
 #define MHD_FP64 0      /* all arithmetic in float64                          */
 #define MHD_FP32_BULK 1 /* reconstruction, Riemann solver and EMFs in float32;
                            state accumulation and pressure recovery in float64 */
+#define MHD_FP64_DF 2   /* reconstruction, Riemann solver, EMFs and the update
+                           increments in double-float (a float pair, ~2^-47
+                           relative error per operation, float exponent range)
+                           on the FP32 pipes; state, pressure recovery and
+                           accumulation in float64.  Differs from MHD_FP64 at
+                           the 1e-13 level.  The adjoint of this mode is the
+                           float64 adjoint. */
 
 typedef struct mhd_config {
   int nx, ny, nz;          /* cells per axis, each >= 4                       */
@@ -57,7 +64,7 @@ typedef struct mhd_config {
   double gamma;            /* adiabatic index, P = (gamma-1) eps (Sec. 2.1)   */
   double cfl;              /* Courant number C_CFL of Eq. dt (0 < cfl <= 0.5) */
   int recon;               /* MHD_RECON_* for Step 6                          */
-  int precision;           /* MHD_FP64 or MHD_FP32_BULK                       */
+  int precision;           /* MHD_FP64, MHD_FP32_BULK or MHD_FP64_DF          */
   double rho_floor;        /* density floor (use 1e-20 for "off")             */
   double p_floor;          /* pressure floor (use 1e-20 for "off")            */
 } mhd_config;
@@ -104,7 +111,8 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const doubl
 
 /* Bytes of device memory the first mhd_adjoint_step call allocates (once per
  * context, freed by mhd_destroy): forward intermediates of one step plus
- * cotangent buffers, 197 words of the compute type + 10 doubles per cell. */
+ * cotangent buffers, 197 words of the compute type (float64 for
+ * MHD_FP64_DF) + 10 doubles per cell. */
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
 /* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
@@ -160,7 +168,8 @@ const char* mhd_stage_name(int stage);
 
 /* ---- per-stage entry points (for stage-by-stage parity checks) ---------
  * All outputs are float64 device arrays in the oracle's layouts; in
- * MHD_FP32_BULK mode the float32 intermediates are widened on output. */
+ * MHD_FP32_BULK and MHD_FP64_DF modes the intermediates are widened on
+ * output. */
 
 /* W_dev[8][N]: rho, vx, vy, vz, P, Bcc_x, Bcc_y, Bcc_z (Sec. 2.2.1). */
 int mhd_stage_primitives(mhd_ctx* ctx, const double* U_dev, double* W_dev);

@@ -45,6 +45,20 @@ struct mhd_ctx {
 
 namespace {
 
+// compute type of each precision mode
+template <class T> struct Tag { using type = T; };
+template <class Fn> int with_type(int precision, Fn&& fn) {
+  if (precision == MHD_FP32_BULK) return fn(Tag<float>{});
+  if (precision == MHD_FP64_DF) return fn(Tag<mhd::df>{});
+  return fn(Tag<double>{});
+}
+// the adjoint of the double-float mode is the float64 adjoint
+template <class Fn> int with_adj_type(int precision, Fn&& fn) {
+  if (precision == MHD_FP32_BULK) return fn(Tag<float>{});
+  return fn(Tag<double>{});
+}
+#define MHD_T typename decltype(t)::type
+
 constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -96,7 +110,7 @@ int check_cfg(const mhd_config* c) {
   if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) return MHD_ERR_ARG;
   if (!(c->cfl > 0.0) || c->cfl > 1.0) return MHD_ERR_ARG;
   if (c->recon < MHD_RECON_PCM || c->recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
-  if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK) return MHD_ERR_ARG;
+  if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK && c->precision != MHD_FP64_DF) return MHD_ERR_ARG;
   if (!(c->rho_floor > 0) || !(c->p_floor > 0)) return MHD_ERR_ARG;
   return MHD_OK;
 }
@@ -460,14 +474,13 @@ const char* mhd_stage_name(int stage) {
 int mhd_step(mhd_ctx* c, double* U, double dt) {
   if (!c || !U) return MHD_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
-  return c->cfg.precision == MHD_FP32_BULK ? one_step<float>(c, U, dt) : one_step<double>(c, U, dt);
+  return with_type(c->cfg.precision, [&](auto t) { return one_step<MHD_T>(c, U, dt); });
 }
 
 int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {
   if (!c || !U || nsteps < 0) return MHD_ERR_ARG;
   if (nsteps == 0) return MHD_OK;
-  return c->cfg.precision == MHD_FP32_BULK ? run_steps<float>(c, U, nsteps, dt_dev)
-                                            : run_steps<double>(c, U, nsteps, dt_dev);
+  return with_type(c->cfg.precision, [&](auto t) { return run_steps<MHD_T>(c, U, nsteps, dt_dev); });
 }
 
 int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
@@ -475,10 +488,10 @@ int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
   cudaStream_t s = c->stream;
   cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   double* Um = const_cast<double*>(U);  // k_prim writes U only when floors are requested
-  if (c->cfg.precision == MHD_FP32_BULK)
-    Launch<float>::prim(c->g, Um, as<float>(c->W), c->dtbits, c->flags, nullptr, s);
-  else
-    Launch<double>::prim(c->g, Um, as<double>(c->W), c->dtbits, c->flags, nullptr, s);
+  with_type(c->cfg.precision, [&](auto t) {
+    Launch<MHD_T>::prim(c->g, Um, as<MHD_T>(c->W), c->dtbits, c->flags, nullptr, s);
+    return 0;
+  });
   mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, s);
   double v = 0;
   unsigned fl = 0;
@@ -516,8 +529,7 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
 int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {
   if (!c || !U_n || !gU_np1 || !gU_n || gU_np1 == gU_n) return MHD_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
-  return c->cfg.precision == MHD_FP32_BULK ? adjoint_step<float>(c, U_n, dt, gU_np1, gU_n)
-                                            : adjoint_step<double>(c, U_n, dt, gU_np1, gU_n);
+  return with_adj_type(c->cfg.precision, [&](auto t) { return adjoint_step<MHD_T>(c, U_n, dt, gU_np1, gU_n); });
 }
 
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes) {
@@ -532,8 +544,8 @@ int mhd_stage_recon_vjp(mhd_ctx* c, const double* U, int axis, int recon, const 
                         double* gU) {
   if (!c || !U || !gWL || !gWR || !gU || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
     return MHD_ERR_ARG;
-  return c->cfg.precision == MHD_FP32_BULK ? stage_recon_vjp<float>(c, U, axis, recon, gWL, gWR, gU)
-                                            : stage_recon_vjp<double>(c, U, axis, recon, gWL, gWR, gU);
+  return with_adj_type(c->cfg.precision,
+                       [&](auto t) { return stage_recon_vjp<MHD_T>(c, U, axis, recon, gWL, gWR, gU); });
 }
 
 int mhd_stage_hlld_vjp(int n, double gamma, int precision, const double* wl, const double* wr, const double* bn,
@@ -595,21 +607,21 @@ int mhd_diagnostics(mhd_ctx* c, const double* U, double* divb_max, double totals
 
 int mhd_stage_primitives(mhd_ctx* c, const double* U, double* W) {
   if (!c || !U || !W) return MHD_ERR_ARG;
-  return c->cfg.precision == MHD_FP32_BULK ? stage_prims<float>(c, U, W) : stage_prims<double>(c, U, W);
+  return with_type(c->cfg.precision, [&](auto t) { return stage_prims<MHD_T>(c, U, W); });
 }
 
 
 
 int mhd_stage_fluxes(mhd_ctx* c, const double* U, int recon, double* F) {
   if (!c || !U || !F || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
-  return c->cfg.precision == MHD_FP32_BULK ? stage_fluxes<float>(c, U, recon, F) : stage_fluxes<double>(c, U, recon, F);
+  return with_type(c->cfg.precision, [&](auto t) { return stage_fluxes<MHD_T>(c, U, recon, F); });
 }
 
 
 
 int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
   if (!c || !U || !F || !E) return MHD_ERR_ARG;
-  return c->cfg.precision == MHD_FP32_BULK ? stage_edges<float>(c, U, F, E) : stage_edges<double>(c, U, F, E);
+  return with_type(c->cfg.precision, [&](auto t) { return stage_edges<MHD_T>(c, U, F, E); });
 }
 
 
@@ -617,8 +629,7 @@ int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
 int mhd_stage_recon(mhd_ctx* c, const double* U, int axis, int recon, double* WL, double* WR) {
   if (!c || !U || !WL || !WR || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
     return MHD_ERR_ARG;
-  return c->cfg.precision == MHD_FP32_BULK ? stage_recon<float>(c, U, axis, recon, WL, WR)
-                                            : stage_recon<double>(c, U, axis, recon, WL, WR);
+  return with_type(c->cfg.precision, [&](auto t) { return stage_recon<MHD_T>(c, U, axis, recon, WL, WR); });
 }
 
 

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mhd_df.cuh"
 #include "mhd_launch.h"
 
 namespace mhd {
@@ -46,9 +47,21 @@ template <class T> __device__ __forceinline__ T trsqrt(T x);
 template <> __device__ __forceinline__ double trsqrt<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float trsqrt<float>(float x) { return rsqrtf(x); }
 
+template <> __device__ __forceinline__ df tsqrt<df>(df x) { return df_sqrt(x); }
+template <> __device__ __forceinline__ df trcp<df>(df x) { return df(1.0f, 0.0f) / x; }
+template <> __device__ __forceinline__ df trsqrt<df>(df x) { return df_rsqrt(x); }
+
+// Exact<T>: the full update widens each flux and edge value to double before
+// differencing (a difference of two floats is exact in double).  df values
+// already carry ~48 bits, so their differences and increments are formed in
+// df and added to the double state once.
+template <class T> struct Exact { static constexpr bool full = true; };
+template <> struct Exact<df> { static constexpr bool full = false; };
+
 template <class T> struct Eps;
 template <> struct Eps<double> { static constexpr double hlld = 1e-8; };
 template <> struct Eps<float> { static constexpr float hlld = 1e-4f; };
+template <> struct Eps<df> { static constexpr float hlld = 1e-8f; };
 
 // ------------------------------------------------- primitives (Sec. 2.2.1) --
 // Cell primitives: rho, v, P (pressure recovered in double) and B_cc, the mean

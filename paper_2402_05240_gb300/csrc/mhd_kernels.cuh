@@ -54,6 +54,11 @@ template <class T> __device__ __forceinline__ void block_max_to(T v, unsigned lo
   }
 }
 
+// double-float values reduce as doubles
+template <> __device__ __forceinline__ void block_max_to<df>(df v, unsigned long long* dst) {
+  block_max_to<double>((double)v, dst);
+}
+
 // inverse crossing time max over l of (|v_l| + c_f,l) / d_l of one cell; the
 // step is dt = C_CFL / (max over cells) (Eq. dt)
 template <class T> __device__ __forceinline__ T cell_inv_crossing(const Grid& g, const T* w8) {
@@ -362,7 +367,8 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   const int i = ci.i, j = ci.j, k = ci.k;
   const double h = 0.5 * dtp[0];
   const long long N = g.N, c = cidx(g, i, j, k);
-  constexpr bool X = sizeof(T) == 8;  // FP64: double differences; FP32-bulk half step: T increments
+  // FP64: double differences; FP32-bulk and df half step: increments in T
+  constexpr bool X = sizeof(T) == 8 && Exact<T>::full;
   double u5[5];
   hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
   const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
@@ -393,10 +399,11 @@ __global__ void __launch_bounds__(BX* BY) k_update_full(Grid g, double* U, const
   const double h = dtp[0];
   const long long N = g.N, c = cidx(g, i, j, k);
   double u5[5];
-  hydro_update<T, true>(g, U, F, h, i, j, k, u5);
-  const double bx = face_update<T, true, 0>(g, U, E, h, i, j, k);
-  const double by = face_update<T, true, 1>(g, U, E, h, i, j, k);
-  const double bz = face_update<T, true, 2>(g, U, E, h, i, j, k);
+  constexpr bool X = Exact<T>::full;
+  hydro_update<T, X>(g, U, F, h, i, j, k, u5);
+  const double bx = face_update<T, X, 0>(g, U, E, h, i, j, k);
+  const double by = face_update<T, X, 1>(g, U, E, h, i, j, k);
+  const double bz = face_update<T, X, 2>(g, U, E, h, i, j, k);
 #pragma unroll
   for (int f = 0; f < 5; ++f) U[f * N + c] = u5[f];
   U[5 * N + c] = bx;

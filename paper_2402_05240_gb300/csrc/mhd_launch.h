@@ -5,6 +5,8 @@
 
 namespace mhd {
 
+struct df;  // double-float number (mhd_df.cuh)
+
 struct Grid {
   int n[3];          // nx, ny, nz
   long long N;       // nx * ny * nz

@@ -25,7 +25,7 @@ MHD_ERR_DT = -5
 MHD_ERR_TOO_LARGE = -6
 
 RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
-PRECISION = {"fp64": 0, "fp32_bulk": 1}
+PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_df": 2}
 
 
 class mhd_config(ctypes.Structure):
