@@ -36,11 +36,11 @@ METRIC = "cell-updates/s on 1 GB300 (FP64 vs FP32-bulk step, adjoint step); % HB
 UNIT = "cell-updates/s"
 
 # Algorithmic HBM bytes per cell of one launch of each stage (reads + writes of
-# the arrays the stage must touch once; T = compute type size).  See the design doc.
+# the arrays the stage must touch once; T = compute type size).
 def stage_bytes(T: int) -> dict:
     return {
         "prim": 64 + 8 * T,                  # U in, W out
-        "flux_pcm": 8 * T + 24 + 21 * T,     # W, face B in; 3x7 fluxes out
+        "flux_pcm": 14 * T + 8,              # 7 W fields, face B in; 7 fluxes out (one axis)
         "emf": (6 + 9) * T + 3 * T,          # v, B_cc, 2 EMF + mass flux per axis; 3 edges out
         "update_half": 64 + 18 * T + 11 * T,  # U, 15 hydro fluxes + 3 edges in; W + 3 faces out
         "recon": 8 * T + 14 * T,             # W in; W_L, W_R out (one axis)
@@ -58,16 +58,36 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA rate of this GPU measured by an FMA-chain probe:
-# 601 G DFMA/s = 1.20 TFLOP/s (about 2 DFMA per clock per SM at 2.07 GHz).
-FP64_PEAK_GFLOPS = 1202.6
+# FP64 pipe rate of this GPU, measured by a dependent-DFMA-chain probe with
+# enough warps in flight: 601.3 G DFMA/s (1.91 per clock per SM at 2.07 GHz),
+# i.e. 1202.6 GFLOP/s.  DADD and DMUL occupy the pipe like a DFMA.
+FP64_PIPE_GINST = 601.3
+FP64_PEAK_GFLOPS = 2 * FP64_PIPE_GINST
+# Warp-instruction issue limit: 4 schedulers per SM, 152 SMs, 2.07 GHz.
+ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 
-# Per-cell counters of one launch of each FP64 stage (PLMC), from the ncu
-# capture summarised in profiles/fp64_counters_turbulent128_plmc.md:
-# FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes (read + write).  They hold
-# for the kernels as profiled; a kernel changed since has no entry.
-FP64_COUNTERS = {
-    "emf": (111.0, 139.6),
+# Per-cell counters of one launch of each stage (PLMC runs only), from an ncu capture of
+# one 128^3 turbulent-box step (per-kernel SASS op counters and DRAM bytes):
+# (FP64 pipe ops DFMA + DADD + DMUL, FP64 flop 2 DFMA + DADD + DMUL,
+#  warp instructions, DRAM bytes read + written).  They hold for the kernels
+# as profiled; a kernel changed since has no entry.
+COUNTERS = {
+    "fp64": {
+        "prim": (121.0, 171.0, 937 / 32, 105.5),
+        "emf": (96.0, 111.0, 940 / 32, 139.4),
+        "update_half": (90.0, 128.0, 797 / 32, 283.3),
+        "recon": (361.0, 481.1, 2475 / 32, 150.1),
+        "flux_hlld": (275.8, 421.9, 1756 / 32, 162.3),
+        "update_full": (50.0, 71.0, 491 / 32, 260.2),
+    },
+    "fp64_df": {
+        "prim": (37.0, 53.0, 1456 / 32, 105.1),
+        "emf": (0.0, 0.0, 1371 / 32, 139.9),
+        "update_half": (49.0, 66.0, 2144 / 32, 282.9),
+        "recon": (0.0, 0.0, 4194 / 32, 150.7),
+        "flux_hlld": (0.0, 0.0, 3090 / 32, 162.4),
+        "update_full": (19.0, 22.0, 1376 / 32, 260.2),
+    },
 }
 
 
@@ -201,13 +221,18 @@ def time_adjoint(mhd, torch, U0, n, steps, warmup, recon, precision, barrier, fw
             "status": code}
 
 
-def roofline_of(prof, precision, n3, hbm_peak, peak_kind):
+def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     """Roofline of the dominant stage (largest share of the timed region).
 
-    FP64: the stage is bound by the FP64 pipe; achieved = counted FP64 flops
-    per launch / live launch time against the measured FP64 FMA peak.
-    FP32-bulk: achieved = algorithmic bytes per launch / launch time against
-    the measured HBM copy bandwidth.
+    FP64: the stage is bound by the FP64 pipe; achieved = counted FP64 pipe
+    operations (DFMA + DADD + DMUL) per launch / live launch time, against the
+    measured FP64 pipe rate (the same ratio in flop terms is reported too).
+    Double-float: bound by instruction issue; achieved = counted warp
+    instructions per launch / launch time against the 4-per-clock-per-SM
+    issue limit.  FP32-bulk (and any stage without counters): algorithmic
+    bytes per launch / launch time against the measured HBM copy bandwidth.
+    `traffic` is the ncu DRAM bytes per cell of the profiled 128^3 launch
+    scaled to this launch's cells (null without counters).
     """
     T = 4 if precision == "fp32_bulk" else 8
     sb = stage_bytes(T)
@@ -220,12 +245,22 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind):
            "bytes_per_cell_counted": sum(sb[k] * v[1] for k, v in prof.items()) / max(1, prof["update_full"][1]),
            "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                    "peak_source": peak_kind}}
-    cnt = FP64_COUNTERS.get(name) if precision == "fp64" else None
-    if precision == "fp64" and cnt:
-        gf = cnt[0] * n3 / per_launch_s / 1e9
-        out.update({"bound": "alu", "achieved": round(gf, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": round(gf / FP64_PEAK_GFLOPS, 4), "peak_source": "measured (FP64 FMA probe)",
-                    "traffic": round(cnt[1] * n3), "flop_per_cell": cnt[0],
+    cnt = COUNTERS.get(precision, {}).get(name) if recon == "plmc" else None
+    if cnt and precision == "fp64":
+        gi = cnt[0] * n3 / per_launch_s / 1e9
+        gf = cnt[1] * n3 / per_launch_s / 1e9
+        out.update({"bound": "alu", "achieved": round(gi, 1), "peak": FP64_PIPE_GINST,
+                    "unit": "G FP64-pipe op/s (DFMA+DADD+DMUL)", "frac": round(gi / FP64_PIPE_GINST, 4),
+                    "peak_source": "measured (FP64 FMA-chain probe)", "traffic": round(cnt[3] * n3),
+                    "flop": {"achieved_gflops": round(gf, 1), "peak_gflops": FP64_PEAK_GFLOPS,
+                             "frac": round(gf / FP64_PEAK_GFLOPS, 4), "flop_per_cell": cnt[1]},
+                    "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
+    elif cnt and precision == "fp64_df":
+        gw = cnt[2] * n3 / per_launch_s / 1e9
+        out.update({"bound": "alu", "achieved": round(gw, 1), "peak": round(ISSUE_PEAK_GWARPINST, 1),
+                    "unit": "G warp-inst/s issued", "frac": round(gw / ISSUE_PEAK_GWARPINST, 4),
+                    "peak_source": "nominal (4 issue slots per clock per SM, 152 SMs, 2.07 GHz)",
+                    "traffic": round(cnt[3] * n3),
                     "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
     else:
         out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
@@ -291,16 +326,18 @@ def run_workload(args, mhd, torch, rank):
         r = Wk.precision_compare(mhd, torch, n=args.n if args.n != 256 else 512, steps=args.steps,
                                  warmup=args.warmup, recon="ppmc")
         value, ms, dtype = r["fp64"]["value"], r["fp64"]["ms_per_step"], "f64"
-        wl = f"turbulent box {r['n']}^3, PPMC + HLLD, FP64 vs FP32-bulk, {r['steps']} steps"
+        wl = f"turbulent box {r['n']}^3, PPMC + HLLD, FP64 vs FP32-bulk vs double-float, {r['steps']} steps"
     elif args.workload == "adjoint_rollout":
         r = Wk.adjoint_rollout(mhd, torch, n=args.n, steps=100, every=10)
         value, ms, dtype = r["backward_cell_updates_per_s"], r["backward_s"] / r["steps"] * 1e3, "f32 (FP64 state)"
         wl = f"blast beta=0.1 {r['n']}^3, PPMC + HLLD, FP32-bulk, 100-step adjoint rollout, checkpoints every 10"
     else:
         n = args.n if args.n != 256 else 459
-        r = Wk.slow_wave(mhd, torch, n=n, steps=args.steps, warmup=args.warmup)
-        value, ms, dtype = r["value"], r["ms_per_step"], "f64"
-        wl = f"slow magnetosonic wave {n}^3 (B = (1, 1.5, 0)), PLMC + HLLD, FP64"
+        r = Wk.slow_wave(mhd, torch, n=n, steps=args.steps, warmup=args.warmup, precision=args.precision)
+        value, ms = r["value"], r["ms_per_step"]
+        dtype = {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)", "fp64_df": "df64 (float pairs, FP64 state)"}[
+            args.precision]
+        wl = f"slow magnetosonic wave {n}^3 (B = (1, 1.5, 0)), PLMC + HLLD, {args.precision}"
     clk = clocks.stop()
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -320,6 +357,8 @@ def main():
     ap.add_argument("--recon", default="plmc", choices=["plmc", "ppmc"])
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp64_df"],
+                    help="precision of the headline timed run (default: the FP64 step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="turbulent",
@@ -361,15 +400,15 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms64, prof64, launches64, sim, U = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon, "fp64",
-                                                  barrier)
+    ms64, prof64, launches64, sim, U = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
+                                                  args.precision, barrier)
     clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([ms64], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms64 = float(t.item())
     value = world * n3 / (ms64 * 1e-3)
-    roof = roofline_of(prof64, "fp64", n3, hbm_peak, peak_kind)
+    roof = roofline_of(prof64, args.precision, n3, hbm_peak, peak_kind, args.recon)
 
     # end to end through the public host-buffer entry point (copies inside)
     e2e_s = None
@@ -390,7 +429,7 @@ def main():
                                                         "fp32_bulk", barrier)
         variants["fp32_bulk"] = {
             "value": world * n3 / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32 (FP64 state)",
-            "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind), "gpu_launches": launches32}
+            "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind, args.recon), "gpu_launches": launches32}
         sim32.close()
         del U32, sim32
         msdf, profdf, launchesdf, simdf, Udf = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
@@ -398,7 +437,7 @@ def main():
         variants["fp64_df"] = {
             "value": world * n3 / (msdf * 1e-3), "ms_per_step": msdf,
             "dtype": "double-float (float pairs) on FP32 pipes, FP64 state",
-            "roofline": roofline_of(profdf, "fp64_df", n3, hbm_peak, peak_kind), "gpu_launches": launchesdf,
+            "roofline": roofline_of(profdf, "fp64_df", n3, hbm_peak, peak_kind, args.recon), "gpu_launches": launchesdf,
             "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in profdf.items()}}
         simdf.close()
         del Udf, simdf
@@ -410,8 +449,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"turbulent box {n}^3, {args.recon.upper()} + HLLD, FP64 step, CFL 0.3, device dt",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)",
+                                       "fp64_df": "df64 (float pairs, FP64 state)"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"turbulent box {n}^3, {args.recon.upper()} + HLLD, "
+                               f"{ {'fp64': 'FP64', 'fp32_bulk': 'FP32-bulk', 'fp64_df': 'double-float'}[args.precision]} "
+                               "step, CFL 0.3, device dt",
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (state 1.07 GB)"},
         "roofline": roof,
         "e2e": ({"value": world * n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3,

@@ -96,6 +96,16 @@ int mhd_step(mhd_ctx* ctx, double* U_dev, double dt);
  * Asynchronous. */
 int mhd_run(mhd_ctx* ctx, double* U_dev, int nsteps, double* dt_dev);
 
+/* Advance U_dev in place from t = 0 to t = t_end (the end time of the paper's
+ * tests, Sec. 3): device-dt steps as in mhd_run, the last one shortened so
+ * that it lands on t_end exactly; at most max_steps steps.  Reads the time
+ * back after each step (synchronous).  *t_host (may be NULL) receives the
+ * time reached (t_end unless max_steps ran out), *steps_host (may be NULL)
+ * the steps taken.  Errors: MHD_ERR_ARG (t_end < 0 or not finite,
+ * max_steps < 0), MHD_ERR_NONFINITE / MHD_ERR_DT from the device flags, the
+ * state then holds the step that raised them. */
+int mhd_evolve(mhd_ctx* ctx, double* U_dev, double t_end, int max_steps, double* t_host, int* steps_host);
+
 /* As mhd_run on a HOST state: copies U_host to a device buffer owned by the
  * context, runs nsteps, copies the result back and synchronises.  *t_host
  * (may be NULL) receives the simulated time advanced. */

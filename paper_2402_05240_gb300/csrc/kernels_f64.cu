@@ -7,8 +7,8 @@ template struct Launch<double>;
 
 void launch_set_dt(double* dt_cur, double value, cudaStream_t s) { k_set_dt<<<1, 1, 0, s>>>(dt_cur, value); }
 void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
-                      unsigned* flags, cudaStream_t s) {
-  k_finish_dt<<<1, 1, 0, s>>>(cfl, dtbits, dt_cur, dt_log, step, flags);
+                      unsigned* flags, double t_end, cudaStream_t s) {
+  k_finish_dt<<<1, 1, 0, s>>>(cfl, dtbits, dt_cur, dt_log, step, flags, t_end);
 }
 void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s) {
   // partials live after the 9 final values

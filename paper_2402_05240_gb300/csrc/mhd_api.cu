@@ -154,7 +154,8 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
   T* W = as<T>(c->W);
   T* F = as<T>(c->F);
   T* E = as<T>(c->E);
-  prof(c, MHD_STAGE_FLUX_PCM, [&] { Launch<T>::flux_pcm(g, W, U, F, s); });  // Steps 2-3
+  for (int a = 0; a < 3; ++a)  // Steps 2-3
+    prof(c, MHD_STAGE_FLUX_PCM, [&] { Launch<T>::flux_pcm(g, a, W, U, F, s); });
   prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 4
   prof(c, MHD_STAGE_UPDATE_HALF,
        [&] { Launch<T>::update_half(g, U, F, E, c->scal, W, as<T>(c->Bh), c->flags, s); });  // Step 5
@@ -167,20 +168,53 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
   prof(c, MHD_STAGE_UPDATE_FULL, [&] { Launch<T>::update_full(g, U, F, E, c->scal, s); });  // Step 9
 }
 
-template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
+constexpr double kNoEnd = HUGE_VAL;
+
+// arm the reduction word (+0.0: the maximum of non-negative rates) and the
+// run's simulated time, then W^0 and the CFL maximum of U^0
+template <class T> void run_begin(mhd_ctx* c, double* U) {
+  cudaStream_t s = c->stream;
+  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);
+  Launch<T>::prim(c->g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+}
+
+// one device-dt step: dt (Step 1), Steps 2-9, then floors, W^{n+1} and the
+// next CFL maximum
+template <class T> void run_one(mhd_ctx* c, double* U, double* dt_log, int n, double t_end) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
-  // arm the reduction word (+0.0: the maximum of non-negative rates), then W^0 and dt^0
-  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);  // simulated time of this run
-  Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
-  for (int n = 0; n < nsteps; ++n) {
-    prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, s); });
-    step_body<T>(c, U, c->cfg.recon);
-    prof(c, MHD_STAGE_PRIM,
-         [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });  // floors, W^{n+1}, next dt
-  }
+  prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, t_end, s); });
+  step_body<T>(c, U, c->cfg.recon);
+  prof(c, MHD_STAGE_PRIM, [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });
+}
+
+template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
+  run_begin<T>(c, U);
+  for (int n = 0; n < nsteps; ++n) run_one<T>(c, U, dt_log, n, kNoEnd);
   return cuda_status();
+}
+
+// steps until the simulated time reaches t_end (the last step shortened);
+// reads the time back after every step
+template <class T> int evolve_to(mhd_ctx* c, double* U, double t_end, int max_steps, double* t_out, int* n_out) {
+  cudaStream_t s = c->stream;
+  run_begin<T>(c, U);
+  double t = 0.0;
+  int n = 0;
+  while (n < max_steps && t < t_end) {
+    run_one<T>(c, U, nullptr, n, t_end);
+    ++n;
+    unsigned fl = 0;
+    if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (fl & 1u) return MHD_ERR_NONFINITE;
+    if (fl & 2u) return MHD_ERR_DT;
+  }
+  if (t_out) *t_out = t;
+  if (n_out) *n_out = n;
+  return MHD_OK;
 }
 
 template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
@@ -261,7 +295,7 @@ template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, con
   const int rc = c->cfg.recon;
   // forward recompute (Steps 1-8)
   Launch<T>::prim(g, U, b.Wn, nullptr, c->flags, nullptr, s);
-  Launch<T>::flux_pcm(g, b.Wn, U, b.Fn, s);
+  for (int a = 0; a < 3; ++a) Launch<T>::flux_pcm(g, a, b.Wn, U, b.Fn, s);
   Launch<T>::emf(g, b.Wn, b.Fn, b.Eh, s);
   mhd::AdjLaunch<T>::fwd_half_keep(g, U, b.Fn, b.Eh, dt, b.Wh, b.Bh, b.Uh, s);
   for (int a = 0; a < 3; ++a) {
@@ -328,7 +362,7 @@ template <class T> int stage_fluxes(mhd_ctx* c, const double* U, int recon, doub
   cudaStream_t s = c->stream;
   Launch<T>::prim(g, const_cast<double*>(U), as<T>(c->W), nullptr, c->flags, nullptr, s);
   if (recon == MHD_RECON_PCM) {
-    Launch<T>::flux_pcm(g, as<T>(c->W), U, as<T>(c->F), s);
+    for (int a = 0; a < 3; ++a) Launch<T>::flux_pcm(g, a, as<T>(c->W), U, as<T>(c->F), s);
   } else {
     Launch<T>::narrow(U + 5 * g.N, as<T>(c->Bh), 3 * g.N, s);
     for (int a = 0; a < 3; ++a) {
@@ -483,6 +517,12 @@ int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {
   return with_type(c->cfg.precision, [&](auto t) { return run_steps<MHD_T>(c, U, nsteps, dt_dev); });
 }
 
+int mhd_evolve(mhd_ctx* c, double* U, double t_end, int max_steps, double* t_host, int* steps_host) {
+  if (!c || !U || max_steps < 0 || !(t_end >= 0.0) || !std::isfinite(t_end)) return MHD_ERR_ARG;
+  return with_type(c->cfg.precision,
+                   [&](auto t) { return evolve_to<MHD_T>(c, U, t_end, max_steps, t_host, steps_host); });
+}
+
 int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
   if (!c || !U || !dt_host) return MHD_ERR_ARG;
   cudaStream_t s = c->stream;
@@ -492,7 +532,7 @@ int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
     Launch<MHD_T>::prim(c->g, Um, as<MHD_T>(c->W), c->dtbits, c->flags, nullptr, s);
     return 0;
   });
-  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, s);
+  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
   double v = 0;
   unsigned fl = 0;
   if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;

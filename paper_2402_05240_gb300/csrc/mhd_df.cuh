@@ -54,28 +54,31 @@ struct __align__(8) df {
   __device__ __forceinline__ explicit operator double() const { return f2d_bits(hi) + f2d_bits(lo); }
 };
 
-// double -> df.  For 2^-80 <= |x| < 2^128: hi = x with its significand cut to
+// double -> df, integer and FP32 instructions only (no branch: a cold path
+// with conversion instructions would be if-converted and still occupy the
+// FP64 pipe).  For 2^-80 <= |x| < 2^128: hi = x with its significand cut to
 // 24 bits (exact), lo = the remaining 29 bits rounded to 23 bits, via the
-// 2^23 magic-number conversion, times 2^(e-46).  |lo| < ulp(hi) and
-// |x - (hi + lo)| <= 2^-47 |x|.  Zero maps to zero; tiny, huge and
-// non-finite values take the conversion instructions.
+// 2^23 magic-number conversion, times 2^(e-46); |lo| < ulp(hi) and
+// |x - (hi + lo)| <= 2^-47 |x|.  For 2^-126 <= |x| < 2^-80, lo = 0 (absolute
+// error below 2^-103); smaller |x| gives a signed zero, |x| >= 2^128 an
+// infinity and NaN a NaN.
 __device__ __forceinline__ df df_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
   const unsigned eb = (hw >> 20) & 0x7ffu;  // biased exponent
-  if (eb == 0u) return df(__uint_as_float(hw & 0x80000000u), 0.0f);  // zero (subnormals flush)
-  if (eb < 943u || eb > 1150u) {
-    const float h = (float)x;
-    return df(h, (float)(x - (double)h));
-  }
   const unsigned s = hw & 0x80000000u;
-  const float hi = __uint_as_float(s | ((eb - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const unsigned sig = ((hw & 0xfffffu) << 3) | (lw >> 29);  // top 23 stored significand bits
+  unsigned hb = s | ((eb - 896u) << 23) | sig;
+  hb = eb < 897u ? s : hb;
+  const unsigned big = s | 0x7f800000u | ((eb == 0x7ffu && ((hw & 0xfffffu) | lw)) ? 0x400000u : 0u);
+  hb = eb > 1150u ? big : hb;
   const unsigned r = lw & 0x1fffffffu;  // remainder: r * 2^(E-52), E = eb - 1023
   // (r + 32) >> 6 <= 2^23: ORed into the significand of 2^23 it gives 2^23 + q
   // exactly (q = 2^23 carries into the exponent, giving 2^24 = 2^23 + q too)
   const float q = __uint_as_float(0x4b000000u | ((r + 32u) >> 6)) - 8388608.0f;
-  const float sc = __uint_as_float((eb - 942u) << 23);  // 2^(E-46)
-  return df(hi, __uint_as_float(__float_as_uint(q * sc) ^ s));
+  const bool has_lo = eb >= 943u && eb <= 1150u;
+  const float sc = __uint_as_float(has_lo ? (eb - 942u) << 23 : 0u);  // 2^(E-46), or 0
+  return df(__uint_as_float(hb), __uint_as_float(__float_as_uint(q * sc) ^ s));
 }
 
 __device__ __forceinline__ df::df(double x) : df(df_from_double(x)) {}

@@ -2,7 +2,7 @@
 //
 // Schedule of one step (Caddy & Schneider, arXiv:2402.05240, Sec. 2.2):
 //   k_prim          Step 1: primitives W^n (+ CFL dt min-reduction)
-//   k_flux_pcm      Steps 2-3: PCM states + HLLD on x, y, z faces
+//   k_flux_pcm<A>   Steps 2-3: PCM states + HLLD on the faces of axis A
 //   k_emf           Step 4: edge electric fields (reference fields of W^n)
 //   k_update_half   Step 5: U^{n+1/2}, B^{n+1/2}; emits W^{n+1/2} and the
 //                   half-step face fields (the hydro U^{n+1/2} is never stored)
@@ -178,14 +178,15 @@ __device__ __forceinline__ void pcm_face(const Grid& g, const T* __restrict__ W,
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
 
-template <class T>
+// one axis per launch: a thread solving three Riemann problems in sequence
+// holds too many registers for the occupancy the double-float arithmetic
+// needs to hide its latencies
+template <class T, int A>
 __global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, const T* __restrict__ W, const double* __restrict__ U,
                                                      T* __restrict__ F) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
-  pcm_face<T, 0>(g, W, U, F, ci.i, ci.j, ci.k);
-  pcm_face<T, 1>(g, W, U, F, ci.i, ci.j, ci.k);
-  pcm_face<T, 2>(g, W, U, F, ci.i, ci.j, ci.k);
+  pcm_face<T, A>(g, W, U, F, ci.i, ci.j, ci.k);
 }
 
 // ------------------------------------------------------------------ Step 6 --
@@ -194,8 +195,15 @@ template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* 
   w[4] = fmax(w[4], T(g.p_floor));
 }
 
+// blocks of 128 threads per SM requested from the register allocator (4:
+// at most 128 registers per thread, 3: at most 168).  The double and
+// double-float PPMC and the double PLMC kernels fit 128 registers without
+// spilling; the double-float PLMC kernel would spill there.
+template <class T, int RECON> struct ReconMinBlocks { static constexpr int v = 4; };
+template <> struct ReconMinBlocks<df, 1> { static constexpr int v = 3; };
+
 template <class T, int RECON, int A>
-__global__ void __launch_bounds__(BX* BY) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
+__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
                                                   T* __restrict__ WR) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
@@ -426,13 +434,21 @@ template <class T> __global__ void k_narrow(const double* __restrict__ src, T* _
 __global__ void k_set_dt(double* dt_cur, double value) { dt_cur[0] = value; }
 
 // dt = cfl / max inverse crossing time; records it and re-arms the reduction word
+// dt = C_CFL / max rate (Eq. dt), shortened to t_end - t when it would step
+// past t_end (t_end = +inf: no end time); the shortened step lands on t_end.
 __global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int s,
-                            unsigned* flags) {
+                            unsigned* flags, double t_end) {
   const double m = __longlong_as_double((long long)dtbits[0]);
-  const double dt = cfl / m;
+  double dt = cfl / m;
   if (!(dt > 0.0) || !isfinite(dt)) atomicOr(flags, 2u);
+  const double t = dt_cur[1];  // simulated time of the current run
+  if (dt >= t_end - t) {
+    dt = t_end - t;
+    dt_cur[1] = t_end;
+  } else {
+    dt_cur[1] = t + dt;
+  }
   dt_cur[0] = dt;
-  dt_cur[1] += dt;  // simulated time of the current run
   if (dt_log) dt_log[s] = dt;
   dtbits[0] = 0ull;  // +0.0
 }
@@ -508,8 +524,11 @@ void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits,
     k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors);
   }
 template <class T>
-void Launch<T>::flux_pcm(const Grid& g, const T* W, const double* U, T* F, cudaStream_t s) {
-    k_flux_pcm<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, U, F);
+void Launch<T>::flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (a == 0) k_flux_pcm<T, 0><<<gr, bl, 0, s>>>(g, W, U, F);
+    if (a == 1) k_flux_pcm<T, 1><<<gr, bl, 0, s>>>(g, W, U, F);
+    if (a == 2) k_flux_pcm<T, 2><<<gr, bl, 0, s>>>(g, W, U, F);
   }
 template <class T>
 void Launch<T>::recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s) {

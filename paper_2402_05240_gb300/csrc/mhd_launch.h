@@ -23,7 +23,7 @@ struct Grid {
 template <class T> struct Launch {
   static void prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
                    unsigned long long* floors, cudaStream_t s);
-  static void flux_pcm(const Grid& g, const T* W, const double* U, T* F, cudaStream_t s);
+  static void flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s);  // axis a
   static void recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s);
   static void flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s);
   static void emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s);
@@ -57,8 +57,9 @@ template <class T> struct AdjLaunch {
 };
 
 void launch_set_dt(double* dt_cur, double value, cudaStream_t s);
+// dt of the next step from the reduction word; t_end = +inf for no end time
 void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
-                      unsigned* flags, cudaStream_t s);
+                      unsigned* flags, double t_end, cudaStream_t s);
 
 // max |div B| and field sums of a state into red[0..8] (red holds 9 + 9 nb doubles)
 void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s);

@@ -51,6 +51,7 @@ def _load_library():
         "mhd_step": (ip, [vp, vp, ctypes.c_double]),
         "mhd_run": (ip, [vp, vp, ip, vp]),
         "mhd_run_host": (ip, [vp, vp, ip, dp]),
+        "mhd_evolve": (ip, [vp, vp, ctypes.c_double, ip, dp, ctypes.POINTER(ip)]),
         "mhd_adjoint_step": (ip, [vp, vp, ctypes.c_double, vp, vp]),
         "mhd_diagnostics": (ip, [vp, vp, dp, dp]),
         "mhd_status": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -124,6 +125,14 @@ def mhd_step(ctx, U: torch.Tensor, dt: float):
 def mhd_run(ctx, U: torch.Tensor, nsteps: int, dt_log: torch.Tensor | None = None):
     p = _ptr(dt_log) if dt_log is not None else ctypes.c_void_p(0)
     _check(LIB.mhd_run(ctx, _ptr(U), int(nsteps), p), "mhd_run")
+
+
+def mhd_evolve(ctx, U: torch.Tensor, t_end: float, max_steps: int = 1 << 30):
+    """Advance U in place to t_end; returns (time reached, steps taken)."""
+    t = ctypes.c_double(0)
+    n = ctypes.c_int(0)
+    _check(LIB.mhd_evolve(ctx, _ptr(U), float(t_end), int(max_steps), ctypes.byref(t), ctypes.byref(n)), "mhd_evolve")
+    return t.value, n.value
 
 
 def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:
@@ -247,6 +256,9 @@ class Sim:
 
     def run(self, U, nsteps, dt_log=None):
         mhd_run(self.ctx, U, nsteps, dt_log)
+
+    def evolve(self, U, t_end, max_steps=1 << 30):
+        return mhd_evolve(self.ctx, U, t_end, max_steps)
 
     def status(self):
         code, counts = mhd_status(self.ctx)

@@ -1,15 +1,15 @@
 """Benchmark workloads beyond the default step timing (used by bench.py).
 
-* precision_compare: the 512^3 PPMC turbulent box, FP64 and FP32-bulk steps
-  timed on the same state, and the FP32-bulk state after n steps compared
-  with the FP64 state per field (relative L1 and max error), both runs using
-  the FP64 run's dt sequence.
+* precision_compare: the 512^3 PPMC turbulent box, FP64, FP32-bulk and
+  double-float steps timed on the same state, and the FP32-bulk and
+  double-float states after n steps compared with the FP64 state per field
+  (relative L1 and max error), all runs on the FP64 run's dt sequence.
 * adjoint_rollout: the strongly magnetised blast at 256^3, FP32-bulk PPMC,
   a 100-step rollout differentiated through torch.autograd with checkpoints
   every 10 steps; reports forward and backward time, their ratio, the peak
   device memory and the floor triggers.
 * slow_wave: the paper's single-GPU throughput problem (slow magnetosonic
-  wave, B = (1, 1.5, 0), FP64, PLMC) at a given size.
+  wave, B = (1, 1.5, 0), PLMC) at a given size and precision.
 
 Everything runs through the library's C ABI; torch supplies device memory.
 """
@@ -70,23 +70,25 @@ def precision_compare(mhd, torch, n=512, steps=10, warmup=2, recon="ppmc"):
     sim.status()
     sim.close()
     torch.cuda.empty_cache()
-    # FP32-bulk: timing run (device dt), then the comparison run on the FP64 dts
-    sim = mhd.Sim(n, n, n, cfl=0.3, recon=recon, precision="fp32_bulk", stream=stream)
-    W = U0.clone()
-    sim.run(W, warmup)
-    ms32 = _timed_run(mhd, torch, sim, W, steps)
-    W.copy_(U0)
-    for dt in dts.cpu().numpy().tolist():
-        sim.step(W, dt)
-    torch.cuda.synchronize()
-    sim.status()
-    sim.close()
     n3 = n ** 3
     res["fp64"] = {"value": n3 / (ms64 * 1e-3), "ms_per_step": ms64}
-    res["fp32_bulk"] = {"value": n3 / (ms32 * 1e-3), "ms_per_step": ms32}
-    res["speedup_fp32_bulk"] = ms64 / ms32
-    res["fp32_bulk_vs_fp64_after_steps"] = field_errors(torch, W, U64)
-    del W, U64, U0
+    # the other modes: a timing run (device dt), then the comparison run on the FP64 dts
+    for prec in ("fp32_bulk", "fp64_df"):
+        sim = mhd.Sim(n, n, n, cfl=0.3, recon=recon, precision=prec, stream=stream)
+        W = U0.clone()
+        sim.run(W, warmup)
+        ms = _timed_run(mhd, torch, sim, W, steps)
+        W.copy_(U0)
+        for dt in dts.cpu().numpy().tolist():
+            sim.step(W, dt)
+        torch.cuda.synchronize()
+        sim.status()
+        sim.close()
+        res[prec] = {"value": n3 / (ms * 1e-3), "ms_per_step": ms, "speedup_over_fp64": ms64 / ms,
+                     "vs_fp64_after_steps": field_errors(torch, W, U64)}
+        del W
+        torch.cuda.empty_cache()
+    del U64, U0
     torch.cuda.empty_cache()
     return res
 
@@ -134,15 +136,15 @@ def adjoint_rollout(mhd, torch, n=256, steps=100, every=10, recon="ppmc", precis
     return res
 
 
-def slow_wave(mhd, torch, n=459, steps=20, warmup=2):
+def slow_wave(mhd, torch, n=459, steps=20, warmup=2, precision="fp64"):
     box = inputs.Box(n, n, n)
     U0, _ = inputs.linear_wave(box, amp=1e-6, b=(1.0, 1.5, 0.0), wave="slow+")
     U = torch.from_numpy(U0).cuda()
     del U0
-    sim = mhd.Sim(n, n, n, cfl=0.3, recon="plmc", precision="fp64",
+    sim = mhd.Sim(n, n, n, cfl=0.3, recon="plmc", precision=precision,
                   stream=torch.cuda.current_stream().cuda_stream)
     sim.run(U, warmup)
     ms = _timed_run(mhd, torch, sim, U, steps)
     sim.status()
     sim.close()
-    return {"n": n, "steps": steps, "value": n ** 3 / (ms * 1e-3), "ms_per_step": ms}
+    return {"n": n, "steps": steps, "precision": precision, "value": n ** 3 / (ms * 1e-3), "ms_per_step": ms}
