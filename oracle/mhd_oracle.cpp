@@ -534,7 +534,7 @@ void plmc(const Params& P, const Grid& g, const S* U, const int* p, int a, S* wl
 
 // --------------------------------------------------------------- O10. PPMC --
 // Felker & Stone (2018) PPM in the characteristic variables of cell i:
-// (1) project W_{i-2..i+2} with L(W_i); (2) fourth-order interface values
+// (1) project W_{i-2..i+2} - W_i with L(W_i); (2) fourth-order interface values
 // q_{i-1/2} = 7/12 (q_{i-1}+q_i) - 1/12 (q_{i-2}+q_{i+1}); (3) Colella & Sekora
 // (2008) interface limiter with C = 1.25; (4) McCorquodale & Colella (2011)
 // cell limiter; (5) back-projection of the deviations with R(W_i).  D-11.
@@ -593,8 +593,16 @@ void ppmc(const Params& P, const Grid& g, const S* U, const int* p, int a, S* wl
   for (int s = -2; s <= 2; ++s) dir_state(P, g, U, p, a, s, w[s + 2], s == 0 ? &bn : &tmp);
   Eigen<S> E;
   eigensystem(P.gamma, w[2], bn, E);
+  // characteristic variables relative to cell i: q_s = L (W_s - W_i), so
+  // q_i = 0 and the limiter's sign tests see the differences of the data
+  // (projecting W_s itself and subtracting would round away differences
+  // below ~1e-16 of the O(1) projected values)
   S q[5][7];
-  for (int s = 0; s < 5; ++s) matvec7(E.L, w[s], q[s]);
+  for (int s = 0; s < 5; ++s) {
+    S dw[7];
+    for (int c = 0; c < 7; ++c) dw[c] = w[s][c] - w[2][c];
+    matvec7(E.L, dw, q[s]);
+  }
   S dm[7], dp[7];
   for (int c = 0; c < 7; ++c) {
     S col[5] = {q[0][c], q[1][c], q[2][c], q[3][c], q[4][c]};
