@@ -268,6 +268,104 @@ def shock_tube(box: Box, left, right, bn, gamma=GAMMA_DEFAULT, axis=0):
 
 
 # ---------------------------------------------------------------------------
+# The paper's periodic system problems (Sec. 3.1).  Face fields are discrete
+# curls of vector potentials on cell edges, so their discrete divergence is
+# zero to round-off; a uniform field is added face by face.
+# ---------------------------------------------------------------------------
+
+def edge_positions(box: Box, origin=(0.0, 0.0, 0.0)):
+    """Coordinates of the edges that carry A_x (i, j+1/2, k+1/2), A_y
+    (i+1/2, j, k+1/2) and A_z (i+1/2, j+1/2, k), as (x, y, z) triples of arrays
+    broadcastable to (nz, ny, nx)."""
+    x, y, z = box.centres()
+    x, y, z = x + origin[0], y + origin[1], z + origin[2]
+    xf, yf, zf = x + 0.5 * box.dx, y + 0.5 * box.dy, z + 0.5 * box.dz
+    return (x, yf, zf), (xf, y, zf), (xf, yf, z)
+
+
+def faces_from_potential(box: Box, ax, ay, az):
+    """Face fields (Bx, By, Bz) on the upper faces from edge potentials (each
+    broadcast to the grid, layout [k, j, i], positions of edge_positions)."""
+    ax, ay, az = (np.broadcast_to(np.asarray(a, np.float64), box.shape) for a in (ax, ay, az))
+    dx, dy, dz = box.dx, box.dy, box.dz
+    bx = (az - np.roll(az, 1, axis=1)) / dy - (ay - np.roll(ay, 1, axis=0)) / dz
+    by = (ax - np.roll(ax, 1, axis=0)) / dz - (az - np.roll(az, 1, axis=2)) / dx
+    bz = (ay - np.roll(ay, 1, axis=2)) / dx - (ax - np.roll(ax, 1, axis=1)) / dy
+    return bx, by, bz
+
+
+# wave-frame basis of the circularly polarised Alfven wave: e1 = (1, 2, 2)/3
+# (sin a = 2/3, sin b = 2/sqrt5), the normal for which one wavelength fits the
+# 3 x 1.5 x 1.5 box along every axis
+_CPAW_E1 = np.array([1.0, 2.0, 2.0]) / 3.0
+_CPAW_E2 = np.array([-2.0, 1.0, 0.0]) / math.sqrt(5.0)
+_CPAW_E3 = np.cross(_CPAW_E1, _CPAW_E2)
+
+
+def cpaw(n: int, amp=0.1, v_par=0.0, gamma=GAMMA_DEFAULT):
+    """Circularly polarised Alfven wave (Sec. 3.1.2) on 3 x 1.5 x 1.5 with
+    2n x n x n cells: rho = 1, P = 0.1, B_par = 1, and in the wave frame
+    v_perp = B_perp = amp (sin 2 pi x1, cos 2 pi x1), x1 = e1 . r, lambda = 1.
+    v_par = 0 travels at v_A = 1 (period 1); v_par = -1 stands.
+    Returns (box, U)."""
+    box = Box(2 * n, n, n, 3.0, 1.5, 1.5)
+    k = 2.0 * math.pi
+    x, y, z = box.centres()
+    x1 = _CPAW_E1[0] * x + _CPAW_E1[1] * y + _CPAW_E1[2] * z
+    s, c = np.sin(k * x1), np.cos(k * x1)
+    vel = [v_par * _CPAW_E1[d] + amp * (s * _CPAW_E2[d] + c * _CPAW_E3[d]) for d in range(3)]
+    pots = []
+    for d, (ex, ey, ez) in enumerate(edge_positions(box)):
+        q = _CPAW_E1[0] * ex + _CPAW_E1[1] * ey + _CPAW_E1[2] * ez
+        # dA = (amp/k)(sin(k x1) e2 + cos(k x1) e3): curl gives amp (sin e2 + cos e3)
+        pots.append((amp / k) * (np.sin(k * q) * _CPAW_E2[d] + np.cos(k * q) * _CPAW_E3[d]))
+    bx, by, bz = faces_from_potential(box, *pots)
+    bface = (bx + _CPAW_E1[0], by + _CPAW_E1[1], bz + _CPAW_E1[2])
+    return box, assemble(box, 1.0, vel, 0.1, bface, gamma)
+
+
+def field_loop(n: int, amp=1e-3, radius=0.3, vel=(1.0, 1.0, 2.0), centre=(0.0, 0.0, 0.0), b0=(0.0, 0.0, 0.0),
+               gamma=GAMMA_DEFAULT):
+    """Advecting field loop (Sec. 3.1.3) on [-1/2, 1/2]^2 x [-1, 1] with
+    n x n x 2n cells: rho = 1, P = 1, v = (1, 1, 2), A_x = 0,
+    A_y = A_z = amp (R - r) inside r < R = 0.3 (r: distance from ``centre``,
+    the domain centre in the paper), plus a uniform field ``b0`` (zero in the
+    paper).  One period is t = 1.  Returns (box, U)."""
+    box = Box(n, n, 2 * n, 1.0, 1.0, 2.0)
+    origin = (-0.5 - centre[0], -0.5 - centre[1], -1.0 - centre[2])
+    (_, _, _), (yx, yy, yz), (zx, zy, zz) = edge_positions(box, origin)
+
+    def pot(px, py, pz):
+        r = np.sqrt(px * px + py * py + pz * pz)
+        return np.where(r < radius, amp * (radius - r), 0.0)
+
+    bx, by, bz = faces_from_potential(box, 0.0, pot(yx, yy, yz), pot(zx, zy, zz))
+    return box, assemble(box, 1.0, vel, 1.0, (bx + b0[0], by + b0[1], bz + b0[2]), gamma)
+
+
+def orszag_tang(n: int, nz: int = 4, gamma=GAMMA_DEFAULT):
+    """Orszag-Tang vortex (Sec. 3.1.6) on the unit box with n x n x nz cells
+    (uniform along z): rho = 25/(36 pi), P = 5/(12 pi), v = (sin 2 pi y,
+    -sin 2 pi x, 0), A_z = (B0 / 4 pi)(cos 4 pi x + 2 cos 2 pi y) with
+    B0 = 1/sqrt(4 pi).  Returns (box, U)."""
+    box = Box(n, n, nz)
+    x, y, _ = box.centres()
+    b0 = 1.0 / math.sqrt(4.0 * math.pi)
+    (_, _, _), (_, _, _), (zx, zy, _) = edge_positions(box)
+    az = (b0 / (4.0 * math.pi)) * (np.cos(4.0 * math.pi * zx) + 2.0 * np.cos(2.0 * math.pi * zy))
+    bface = faces_from_potential(box, 0.0, 0.0, az)
+    vel = (np.sin(2.0 * math.pi * y), -np.sin(2.0 * math.pi * x), 0.0)
+    return box, assemble(box, 25.0 / (36.0 * math.pi), vel, 5.0 / (12.0 * math.pi), bface, gamma)
+
+
+def l1_error_norm(U, U0):
+    """The paper's error measure (Sec. 3.1.1): the L2 norm over the conserved
+    variables of their mean absolute differences."""
+    d = np.abs(np.asarray(U) - np.asarray(U0)).reshape(U.shape[0], -1).mean(axis=1)
+    return float(np.sqrt(np.sum(d * d)))
+
+
+# ---------------------------------------------------------------------------
 # Axis relabelling (for symmetry checks)
 # ---------------------------------------------------------------------------
 
@@ -282,7 +380,7 @@ def cycle_axes(U):
     def perm(a):
         return np.ascontiguousarray(np.transpose(a, (1, 2, 0)))
 
-    V = np.empty_like(U)
+    V = np.empty((U.shape[0],) + perm(U[0]).shape, dtype=U.dtype)
     V[0] = perm(U[0])
     V[1] = perm(U[3])  # new mx = old mz
     V[2] = perm(U[1])  # new my = old mx
