@@ -341,7 +341,8 @@ void hlld(double gamma, const S* wl, const S* wr, const S& bn, S* flux, HlldDeta
 // normalisation of Stone et al. (2008, App. A); columns ordered by
 // lambda = u-cf, u-ca, u-cs, u, u+cs, u+ca, u+cf.  D-10 conventions:
 // beta = (1,1)/sqrt2 when B_t = 0; alpha_f = 1, alpha_s = 0 when cf2 = cs2;
-// S = sgn(B_n) with sgn(0) = +1.  L = R^-1 by Gaussian elimination.
+// S = sgn(B_n) with sgn(0) = +1.  L = R^-1 by Gaussian elimination, with the
+// elimination's round-off in exactly-zero entries removed.
 template <class S> struct Eigen {
   S lam[7];
   S R[7][7];  // R[row][col]
@@ -451,6 +452,17 @@ template <class S> void eigensystem(double gamma, const S* w, const S& bn, Eigen
   // entropy wave (column 3)
   E.R[0][3] = S(1.0);
   invert7(E.R, E.L);
+  // Entries of R^-1 that are exactly zero (the v_n entries of the slow and
+  // entropy rows when B_n = 0, the beta_2 entries when B_t2 = 0, ...) come out
+  // of the elimination as O(eps) noise.  The limiters branch on the signs of
+  // L dW, so such noise would decide ties that are exact in exact arithmetic:
+  // entries below 32 eps of their row's largest entry are set to zero.
+  for (int i = 0; i < 7; ++i) {
+    double m = 0.0;
+    for (int j = 0; j < 7; ++j) m = std::max(m, std::fabs(val(E.L[i][j])));
+    for (int j = 0; j < 7; ++j)
+      if (std::fabs(val(E.L[i][j])) < 32.0 * 2.220446049250313e-16 * m) E.L[i][j] = S(0.0);
+  }
 }
 
 template <class S> void matvec7(const S M[7][7], const S* x, S* y) {
@@ -801,13 +813,16 @@ template <class S> void step(const Params& P, S* U, double dt, long long* counts
 }
 
 // ----------------------------------------------------------------- O2. dt --
-double cfl_dt(const Params& P, const double* U, double cfl) {
+// Eq. dt over the cells of the box [lo, hi) (the whole grid when lo is null)
+double cfl_dt(const Params& P, const double* U, double cfl, const int* lo = nullptr, const int* hi = nullptr) {
   Grid g(P);
   double best = std::numeric_limits<double>::infinity();
 #pragma omp parallel for reduction(min : best) schedule(static)
   for (long c = 0; c < g.N; ++c) {
     int p[3];
     g.coords(c, p);
+    if (lo && (p[0] < lo[0] || p[0] >= hi[0] || p[1] < lo[1] || p[1] >= hi[1] || p[2] < lo[2] || p[2] >= hi[2]))
+      continue;
     Prim<double> w = primitive(P, g, U, p);
     for (int l = 0; l < 3; ++l) {
       int b = (l + 1) % 3, cc = (l + 2) % 3;
@@ -836,6 +851,10 @@ void oracle_primitives(const Params* P, const double* U, double* W) {
 }
 
 double oracle_dt(const Params* P, const double* U, double cfl) { return cfl_dt(*P, U, cfl); }
+
+double oracle_dt_box(const Params* P, const double* U, double cfl, const int* lo, const int* hi) {
+  return cfl_dt(*P, U, cfl, lo, hi);
+}
 
 double oracle_fast_speed(double gamma, double rho, double p, double bl, double bt1, double bt2) {
   return fast_speed(gamma, rho, p, bl, bt1, bt2);
