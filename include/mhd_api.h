@@ -58,6 +58,19 @@ extern "C" {
                            the 1e-13 level.  The adjoint of this mode is the
                            float64 adjoint. */
 
+/* Boundary condition of each axis (mhd_config.bc).  Periodic: wrap-around
+ * indexing inside the kernels, no ghost cells.  Outflow (zero gradient, the
+ * paper's Riemann problems, Sec. 3.1.4): the library embeds the grid in a
+ * padded grid with MHD_GHOST cells on both sides of each outflow axis, fills
+ * every ghost cell (all 8 fields, face fields included) from the nearest
+ * interior cell before each step, and runs the step on the padded grid; the
+ * ghost depth exceeds the step's dependency radius (5 cells for PPMC), so
+ * the interior result is that of ghost cells filled once per step.  The CFL
+ * dt and the floor counters cover interior cells only. */
+#define MHD_BC_PERIODIC 0
+#define MHD_BC_OUTFLOW 1
+#define MHD_GHOST 8
+
 typedef struct mhd_config {
   int nx, ny, nz;          /* cells per axis, each >= 4                       */
   double dx, dy, dz;       /* cell widths (> 0)                               */
@@ -67,6 +80,7 @@ typedef struct mhd_config {
   int precision;           /* MHD_FP64, MHD_FP32_BULK or MHD_FP64_DF          */
   double rho_floor;        /* density floor (use 1e-20 for "off")             */
   double p_floor;          /* pressure floor (use 1e-20 for "off")            */
+  int bc[3];               /* MHD_BC_* per axis x, y, z                       */
 } mhd_config;
 
 typedef struct mhd_ctx mhd_ctx; /* opaque; owns the workspace */
@@ -115,7 +129,7 @@ int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
  * gU_n = (dU^{n+1}/dU^n)^T gU_np1.  U_n_dev: the state the forward step
  * started from (read only); gU_np1_dev: cotangent of U^{n+1}; gU_n_dev:
  * output, same layout as U.  Recomputes the forward intermediates in the
- * workspace.  Asynchronous. */
+ * workspace.  Asynchronous.  Periodic grids only (MHD_ERR_ARG otherwise). */
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const double* gU_np1_dev,
                      double* gU_n_dev);
 
@@ -126,7 +140,9 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const doubl
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
 /* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
- * |div B| from face differences, and the sums of the 8 fields.  Synchronous. */
+ * |div B| from face differences, and the sums of the 8 fields.  On an
+ * outflow axis the lower face of the first cell is its ghost copy (equal to
+ * the cell's upper face).  Synchronous. */
 int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, double totals_host[8]);
 
 /* mhd_diagnostics without any device allocation.  The paper has no
@@ -179,7 +195,7 @@ const char* mhd_stage_name(int stage);
 /* ---- per-stage entry points (for stage-by-stage parity checks) ---------
  * All outputs are float64 device arrays in the oracle's layouts; in
  * MHD_FP32_BULK and MHD_FP64_DF modes the intermediates are widened on
- * output. */
+ * output.  Periodic grids only (MHD_ERR_ARG otherwise). */
 
 /* W_dev[8][N]: rho, vx, vy, vz, P, Bcc_x, Bcc_y, Bcc_z (Sec. 2.2.1). */
 int mhd_stage_primitives(mhd_ctx* ctx, const double* U_dev, double* W_dev);

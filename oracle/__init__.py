@@ -55,6 +55,9 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lib.oracle_dt.restype = ctypes.c_double
             lib.oracle_dt.argtypes = [P, dp, ctypes.c_double]
+            ip3 = ctypes.POINTER(ctypes.c_int)
+            lib.oracle_dt_box.restype = ctypes.c_double
+            lib.oracle_dt_box.argtypes = [P, dp, ctypes.c_double, ip3, ip3]
             lib.oracle_fast_speed.restype = ctypes.c_double
             lib.oracle_fast_speed.argtypes = [ctypes.c_double] * 6
             lib.oracle_hlld.argtypes = [ctypes.c_double, dp, dp, ctypes.c_double, dp]
@@ -73,6 +76,56 @@ def _load():
             lib.oracle_recon_jvp.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
             _lib = lib
     return _lib
+
+
+GHOST = 10  # ghost depth of the outflow oracle: more than one step's dependency radius (5 cells)
+
+
+class OutflowOracle:
+    """The step on a grid with outflow (zero-gradient) boundaries on some axes
+    (Sec. 3.1.4: the Riemann problems): U^n is padded with GHOST ghost cells
+    on both sides of each outflow axis, every ghost cell a copy of the nearest
+    interior cell (all 8 fields, face fields included), the periodic oracle
+    step runs on the padded grid and the interior is kept -- ghost cells
+    filled once per step.  dt is Eq. dt over the interior cells of the padded
+    state.  ``bc``: per axis x, y, z, "periodic" or "outflow"."""
+
+    def __init__(self, nx, ny, nz, bc, gamma=5.0 / 3.0, recon="plmc", rho_floor=1e-20, p_floor=1e-20,
+                 lx=1.0, ly=1.0, lz=1.0):
+        self.shape = (nz, ny, nx)
+        self.g = [GHOST if b == "outflow" else 0 for b in bc]  # x, y, z
+        gx, gy, gz = self.g
+        self.inner = Oracle(nx + 2 * gx, ny + 2 * gy, nz + 2 * gz, dx=lx / nx, dy=ly / ny, dz=lz / nz,
+                            gamma=gamma, recon=recon, rho_floor=rho_floor, p_floor=p_floor)
+        self.lo = (ctypes.c_int * 3)(gx, gy, gz)
+        self.hi = (ctypes.c_int * 3)(gx + nx, gy + ny, gz + nz)
+
+    def pad(self, U):
+        gx, gy, gz = self.g
+        U = np.ascontiguousarray(U, np.float64)
+        assert U.shape == (8,) + self.shape
+        return np.ascontiguousarray(np.pad(U, ((0, 0), (gz, gz), (gy, gy), (gx, gx)), mode="edge"))
+
+    def unpad(self, V):
+        gx, gy, gz = self.g
+        nz, ny, nx = self.shape
+        return np.ascontiguousarray(V[:, gz:gz + nz, gy:gy + ny, gx:gx + nx])
+
+    def dt(self, U, cfl):
+        P = self.pad(U)
+        return self.inner.lib.oracle_dt_box(ctypes.byref(self.inner.p), _ptr(P), cfl, self.lo, self.hi)
+
+    def step(self, U, dt):
+        return self.unpad(self.inner.step(self.pad(U), dt))
+
+    def run(self, U, nsteps, cfl=None, dts=None):
+        V = np.ascontiguousarray(U, np.float64).copy()
+        used = []
+        for s in range(nsteps):
+            dt = dts[s] if dts is not None else self.dt(V, cfl)
+            V = self.step(V, dt)
+            used.append(dt)
+        return V, used
 
 
 def _ptr(a: np.ndarray):

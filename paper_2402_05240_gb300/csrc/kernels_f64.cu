@@ -10,6 +10,19 @@ void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, do
                       unsigned* flags, double t_end, cudaStream_t s) {
   k_finish_dt<<<1, 1, 0, s>>>(cfl, dtbits, dt_cur, dt_log, step, flags, t_end);
 }
+static int copy_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+void launch_pad(const Grid& gp, const Grid& gi, const double* U, double* Up, cudaStream_t s) {
+  k_pad_copy<<<copy_blocks(8 * gi.N), 256, 0, s>>>(gp, gi, Up, const_cast<double*>(U), 0);
+}
+void launch_unpad(const Grid& gp, const Grid& gi, const double* Up, double* U, cudaStream_t s) {
+  k_pad_copy<<<copy_blocks(8 * gi.N), 256, 0, s>>>(gp, gi, const_cast<double*>(Up), U, 1);
+}
+void launch_fill_ghosts(const Grid& gp, double* Up, cudaStream_t s) {
+  k_fill_ghosts<<<copy_blocks(gp.N), 256, 0, s>>>(gp, Up);
+}
 void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s) {
   // partials live after the 9 final values
   k_diag_partial<<<nb, DIAG_T, 0, s>>>(g, U, red + 9, nb);

@@ -20,7 +20,9 @@ struct ProfRec {
 
 struct mhd_ctx {
   mhd_config cfg;
-  Grid g;
+  Grid g;               // grid of the step kernels (padded along outflow axes)
+  Grid gi;              // the caller's grid
+  double* Up;           // padded state (outflow boundaries), else nullptr
   cudaStream_t stream;
   size_t ts;            // bytes of the compute type
   void* ws;             // one workspace allocation
@@ -63,8 +65,22 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t W, F, E, WL, WR, Bh, scal, dtbits, floors, flags, red, total;
+  size_t W, F, E, WL, WR, Bh, scal, dtbits, floors, flags, red, Up, total;
 };
+
+bool padded(const mhd_config& c) {
+  return c.bc[0] == MHD_BC_OUTFLOW || c.bc[1] == MHD_BC_OUTFLOW || c.bc[2] == MHD_BC_OUTFLOW;
+}
+
+// cells per axis of the step kernels' grid: MHD_GHOST more on each side of
+// an outflow axis
+void padded_dims(const mhd_config& c, int n[3], int lo[3]) {
+  const int ni[3] = {c.nx, c.ny, c.nz};
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = c.bc[a] == MHD_BC_OUTFLOW ? MHD_GHOST : 0;
+    n[a] = ni[a] + 2 * lo[a];
+  }
+}
 
 size_t red_blocks(long long N) {
   long long b = (N + 1023) / 1024;
@@ -72,7 +88,10 @@ size_t red_blocks(long long N) {
 }
 
 Layout layout_of(const mhd_config& c) {
-  const size_t N = (size_t)c.nx * c.ny * c.nz;
+  int np[3], lo[3];
+  padded_dims(c, np, lo);
+  const size_t N = (size_t)np[0] * np[1] * np[2];
+  const size_t Ni = (size_t)c.nx * c.ny * c.nz;
   const size_t ts = c.precision == MHD_FP32_BULK ? 4 : 8;
   Layout L;
   size_t off = 0;
@@ -97,7 +116,9 @@ Layout layout_of(const mhd_config& c) {
   L.flags = off;
   off += up(sizeof(unsigned));
   L.red = off;
-  off += up((9 + 9 * red_blocks((long long)N)) * sizeof(double));
+  off += up((9 + 9 * red_blocks((long long)Ni)) * sizeof(double));
+  L.Up = off;
+  if (padded(c)) off += up(8 * N * sizeof(double));
   L.total = off;
   return L;
 }
@@ -112,6 +133,11 @@ int check_cfg(const mhd_config* c) {
   if (c->recon < MHD_RECON_PCM || c->recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
   if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK && c->precision != MHD_FP64_DF) return MHD_ERR_ARG;
   if (!(c->rho_floor > 0) || !(c->p_floor > 0)) return MHD_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (c->bc[a] != MHD_BC_PERIODIC && c->bc[a] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
+  int np[3], lo[3];
+  padded_dims(*c, np, lo);
+  if ((long long)np[0] * np[1] > (1ll << 31) || np[2] > 65535) return MHD_ERR_ARG;
   return MHD_OK;
 }
 
@@ -170,6 +196,22 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
 
 constexpr double kNoEnd = HUGE_VAL;
 
+// Outflow boundaries: the step kernels work on the padded copy Up of the
+// caller's state, whose ghost cells are refilled from the interior after
+// every step (before the primitives, floors and CFL maximum of the next).
+double* enter(mhd_ctx* c, const double* U) {
+  if (!c->Up) return const_cast<double*>(U);
+  mhd::launch_pad(c->g, c->gi, U, c->Up, c->stream);
+  mhd::launch_fill_ghosts(c->g, c->Up, c->stream);
+  return c->Up;
+}
+void leave(mhd_ctx* c, double* U) {
+  if (c->Up) mhd::launch_unpad(c->g, c->gi, c->Up, U, c->stream);
+}
+void refill(mhd_ctx* c, double* S) {
+  if (c->Up) mhd::launch_fill_ghosts(c->g, S, c->stream);
+}
+
 // arm the reduction word (+0.0: the maximum of non-negative rates) and the
 // run's simulated time, then W^0 and the CFL maximum of U^0
 template <class T> void run_begin(mhd_ctx* c, double* U) {
@@ -186,12 +228,15 @@ template <class T> void run_one(mhd_ctx* c, double* U, double* dt_log, int n, do
   cudaStream_t s = c->stream;
   prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, t_end, s); });
   step_body<T>(c, U, c->cfg.recon);
+  refill(c, U);
   prof(c, MHD_STAGE_PRIM, [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });
 }
 
 template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
-  run_begin<T>(c, U);
-  for (int n = 0; n < nsteps; ++n) run_one<T>(c, U, dt_log, n, kNoEnd);
+  double* S = enter(c, U);
+  run_begin<T>(c, S);
+  for (int n = 0; n < nsteps; ++n) run_one<T>(c, S, dt_log, n, kNoEnd);
+  leave(c, U);
   return cuda_status();
 }
 
@@ -199,31 +244,38 @@ template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_l
 // reads the time back after every step
 template <class T> int evolve_to(mhd_ctx* c, double* U, double t_end, int max_steps, double* t_out, int* n_out) {
   cudaStream_t s = c->stream;
-  run_begin<T>(c, U);
+  double* S = enter(c, U);
+  run_begin<T>(c, S);
   double t = 0.0;
-  int n = 0;
-  while (n < max_steps && t < t_end) {
-    run_one<T>(c, U, nullptr, n, t_end);
+  int n = 0, st = MHD_OK;
+  while (st == MHD_OK && n < max_steps && t < t_end) {
+    run_one<T>(c, S, nullptr, n, t_end);
     ++n;
     unsigned fl = 0;
-    if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
-    if (cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
-    if (fl & 1u) return MHD_ERR_NONFINITE;
-    if (fl & 2u) return MHD_ERR_DT;
+    if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return MHD_ERR_CUDA;
+    if (fl & 1u) st = MHD_ERR_NONFINITE;
+    else if (fl & 2u) st = MHD_ERR_DT;
   }
+  leave(c, U);
   if (t_out) *t_out = t;
   if (n_out) *n_out = n;
-  return MHD_OK;
+  if (st != MHD_OK) return st;
+  return cuda_status();
 }
 
 template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
   mhd::launch_set_dt(c->scal, dt, s);
-  Launch<T>::prim(g, U, as<T>(c->W), nullptr, c->flags, nullptr, s);
-  step_body<T>(c, U, c->cfg.recon);
-  Launch<T>::prim(g, U, as<T>(c->W), nullptr, c->flags, c->floors, s);
+  double* S = enter(c, U);
+  Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, nullptr, s);
+  step_body<T>(c, S, c->cfg.recon);
+  refill(c, S);
+  Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, c->floors, s);
+  leave(c, U);
   return cuda_status();
 }
 
@@ -414,10 +466,15 @@ int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
   mhd_ctx* c = new (std::nothrow) mhd_ctx();
   if (!c) return MHD_ERR_OOM;
   c->cfg = *cfg;
-  c->g.n[0] = cfg->nx;
-  c->g.n[1] = cfg->ny;
-  c->g.n[2] = cfg->nz;
-  c->g.N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  int np[3], lo[3];
+  padded_dims(*cfg, np, lo);
+  for (int a = 0; a < 3; ++a) {
+    c->g.n[a] = np[a];
+    c->g.lo[a] = lo[a];
+    c->g.hi[a] = np[a] - lo[a];
+    c->g.bc[a] = MHD_BC_PERIODIC;  // the padded grid itself wraps
+  }
+  c->g.N = (long long)np[0] * np[1] * np[2];
   c->g.d[0] = cfg->dx;
   c->g.d[1] = cfg->dy;
   c->g.d[2] = cfg->dz;
@@ -428,6 +485,16 @@ int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
   c->g.rho_floor = cfg->rho_floor;
   c->g.p_floor = cfg->p_floor;
   c->g.cfl = cfg->cfl;
+  c->gi = c->g;
+  c->gi.n[0] = cfg->nx;
+  c->gi.n[1] = cfg->ny;
+  c->gi.n[2] = cfg->nz;
+  c->gi.N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  for (int a = 0; a < 3; ++a) {
+    c->gi.lo[a] = 0;
+    c->gi.hi[a] = c->gi.n[a];
+    c->gi.bc[a] = cfg->bc[a];
+  }
   c->stream = static_cast<cudaStream_t>(stream);
   c->ts = cfg->precision == MHD_FP32_BULK ? 4 : 8;
   const Layout L = layout_of(*cfg);
@@ -450,7 +517,8 @@ int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
   c->floors = reinterpret_cast<unsigned long long*>(b + L.floors);
   c->flags = reinterpret_cast<unsigned*>(b + L.flags);
   c->red = reinterpret_cast<double*>(b + L.red);
-  c->red_count = red_blocks(c->g.N);
+  c->red_count = red_blocks(c->gi.N);
+  c->Up = padded(*cfg) ? reinterpret_cast<double*>(b + L.Up) : nullptr;
   cudaMemsetAsync(c->ws, 0, L.total, c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
     cudaFree(c->ws);
@@ -527,7 +595,7 @@ int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
   if (!c || !U || !dt_host) return MHD_ERR_ARG;
   cudaStream_t s = c->stream;
   cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
-  double* Um = const_cast<double*>(U);  // k_prim writes U only when floors are requested
+  double* Um = enter(c, U);  // k_prim writes its state only when floors are requested
   with_type(c->cfg.precision, [&](auto t) {
     Launch<MHD_T>::prim(c->g, Um, as<MHD_T>(c->W), c->dtbits, c->flags, nullptr, s);
     return 0;
@@ -546,7 +614,7 @@ int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
 
 int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
   if (!c || !U_host || nsteps < 0) return MHD_ERR_ARG;
-  const size_t bytes = 8 * (size_t)c->g.N * sizeof(double);
+  const size_t bytes = 8 * (size_t)c->gi.N * sizeof(double);
   if (!c->host_state) {
     if (cudaMalloc(&c->host_state, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -568,6 +636,7 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
 
 int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {
   if (!c || !U_n || !gU_np1 || !gU_n || gU_np1 == gU_n) return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
   return with_adj_type(c->cfg.precision, [&](auto t) { return adjoint_step<MHD_T>(c, U_n, dt, gU_np1, gU_n); });
 }
@@ -584,6 +653,7 @@ int mhd_stage_recon_vjp(mhd_ctx* c, const double* U, int axis, int recon, const 
                         double* gU) {
   if (!c || !U || !gWL || !gWR || !gU || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
     return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_adj_type(c->cfg.precision,
                        [&](auto t) { return stage_recon_vjp<MHD_T>(c, U, axis, recon, gWL, gWR, gU); });
 }
@@ -635,7 +705,7 @@ const char* mhd_strerror(int code) {
 int mhd_diagnostics(mhd_ctx* c, const double* U, double* divb_max, double totals[8]) {
   if (!c || !U || !divb_max || !totals) return MHD_ERR_ARG;
   cudaStream_t s = c->stream;
-  mhd::launch_diagnostics(c->g, U, c->red, (int)c->red_count, s);
+  mhd::launch_diagnostics(c->gi, U, c->red, (int)c->red_count, s);
   double out[9];
   if (cudaMemcpyAsync(out, c->red, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
@@ -647,6 +717,7 @@ int mhd_diagnostics(mhd_ctx* c, const double* U, double* divb_max, double totals
 
 int mhd_stage_primitives(mhd_ctx* c, const double* U, double* W) {
   if (!c || !U || !W) return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_prims<MHD_T>(c, U, W); });
 }
 
@@ -654,6 +725,7 @@ int mhd_stage_primitives(mhd_ctx* c, const double* U, double* W) {
 
 int mhd_stage_fluxes(mhd_ctx* c, const double* U, int recon, double* F) {
   if (!c || !U || !F || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_fluxes<MHD_T>(c, U, recon, F); });
 }
 
@@ -661,6 +733,7 @@ int mhd_stage_fluxes(mhd_ctx* c, const double* U, int recon, double* F) {
 
 int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
   if (!c || !U || !F || !E) return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_edges<MHD_T>(c, U, F, E); });
 }
 
@@ -669,6 +742,7 @@ int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
 int mhd_stage_recon(mhd_ctx* c, const double* U, int axis, int recon, double* WL, double* WR) {
   if (!c || !U || !WL || !WR || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
     return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_recon<MHD_T>(c, U, axis, recon, WL, WR); });
 }
 

@@ -37,6 +37,11 @@ __device__ __forceinline__ CellIdx cell_of_thread(const Grid& g) {
 
 inline dim3 grid_of(const Grid& g) { return dim3((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, g.n[2]); }
 
+// inside the interior box of a padded grid (always true without padding)
+__device__ __forceinline__ bool interior(const Grid& g, int i, int j, int k) {
+  return i >= g.lo[0] && i < g.hi[0] && j >= g.lo[1] && j < g.hi[1] && k >= g.lo[2] && k < g.hi[2];
+}
+
 // Positive doubles order like their bit patterns: the maximum inverse
 // crossing time goes through an integer atomicMax.  The block reduces in the
 // compute type and converts once.
@@ -113,7 +118,9 @@ __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long l
 // Primitives W of a state, and optionally (floors != nullptr) the end-of-step
 // floors of the conserved state (D-12): rho < rho_floor is raised; if the
 // recovered P < p_floor, E is reset so that P = p_floor.  Only the cell's own
-// rho and E are written, so this is race-free in place.
+// rho and E are written, so this is race-free in place.  The CFL maximum and
+// the floor counters take interior cells only (ghost cells of a padded grid
+// are copies).
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
                                                  unsigned* flags, unsigned long long* floors) {
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
   if (ci.ok) {
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = cidx(g, i, j, k), N = g.N;
+    const bool in = interior(g, i, j, k);
     double b[3];
     b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
     b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
@@ -132,7 +140,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     if (floors && r < g.rho_floor) {
       r = g.rho_floor;
       U[c] = r;
-      atomicAdd(&floors[0], 1ull);
+      if (in) atomicAdd(&floors[0], 1ull);
     }
     const double rho = fmax(r, g.rho_floor);
     const double ir = __drcp_rn(rho);
@@ -142,13 +150,13 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
       if (g.gm1 * (e - ke - me) < g.p_floor) {
         e = g.p_floor * g.igm1 + ke + me;
         U[4 * N + c] = e;
-        atomicAdd(&floors[1], 1ull);
+        if (in) atomicAdd(&floors[1], 1ull);
       }
     }
     const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
     T w8[8];
     store_w<T>(g, W, c, p, w8);
-    if (dtbits) inv = cell_inv_crossing<T>(g, w8);
+    if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
   }
   if (dtbits) block_max_to<T>(inv, dtbits);
 }
@@ -389,7 +397,8 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   Bh[N + c] = T(by);
   Bh[2 * N + c] = T(bz);
   const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
-  if (!(u5[0] > 0.0) || !isfinite(u5[4])) atomicOr(flags, 1u);
+  // (the outer ghost layers of a padded grid see the wrap and carry no check)
+  if ((!(u5[0] > 0.0) || !isfinite(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);
   const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
   T w8[8];
   store_w<T>(g, W, c, p, w8);
@@ -453,6 +462,40 @@ __global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_c
   dtbits[0] = 0ull;  // +0.0
 }
 
+// ------------------------------------------------- outflow ghost cells --
+// Up (grid gp) holds the caller's grid in its interior box [lo, hi); Ui is
+// the caller's state (grid gi).  dir = 0: Ui -> Up; dir = 1: Up -> Ui.
+__global__ void k_pad_copy(Grid gp, Grid gi, double* Up, double* Ui, int dir) {
+  const long long Ni = gi.N;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 8 * Ni;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(q / Ni);
+    const long long c = q - f * Ni;
+    const int i = (int)(c % gi.n[0]), j = (int)((c / gi.n[0]) % gi.n[1]);
+    const int k = (int)(c / ((long long)gi.n[0] * gi.n[1]));
+    const long long cp = f * gp.N + cidx(gp, i + gp.lo[0], j + gp.lo[1], k + gp.lo[2]);
+    if (dir == 0) Up[cp] = Ui[q];
+    else Ui[q] = Up[cp];
+  }
+}
+
+// every cell of Up outside the interior box takes all 8 fields (face fields
+// included) of the nearest interior cell: zero-gradient (outflow) ghosts
+__global__ void k_fill_ghosts(Grid gp, double* Up) {
+  const long long N = gp.N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % gp.n[0]), j = (int)((c / gp.n[0]) % gp.n[1]);
+    const int k = (int)(c / ((long long)gp.n[0] * gp.n[1]));
+    if (interior(gp, i, j, k)) continue;
+    const int si = min(max(i, gp.lo[0]), gp.hi[0] - 1);
+    const int sj = min(max(j, gp.lo[1]), gp.hi[1] - 1);
+    const int sk = min(max(k, gp.lo[2]), gp.hi[2] - 1);
+    const long long s = cidx(gp, si, sj, sk);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Up[f * N + c] = Up[f * N + s];
+  }
+}
+
 // ------------------------------------------------------------ diagnostics --
 // Per-block partial sums of the 8 fields and max |div B| over 1024 cells, then
 // one block combines the partials in a fixed order: deterministic results.
@@ -471,9 +514,13 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_partial(Grid g, const double* _
     const int k = (int)(c / ((long long)g.n[0] * g.n[1]));
 #pragma unroll
     for (int f = 0; f < 8; ++f) v[f] = U[f * N + c];
-    const double dv = (U[5 * N + c] - U[5 * N + nb<0>(g, i, j, k, -1)]) * g.id[0] +
-                      (U[6 * N + c] - U[6 * N + nb<1>(g, i, j, k, -1)]) * g.id[1] +
-                      (U[7 * N + c] - U[7 * N + nb<2>(g, i, j, k, -1)]) * g.id[2];
+    // lower faces; on an outflow axis the first cell's lower face is its ghost
+    // copy, equal to the cell's own upper face
+    const long long lx = (g.bc[0] && i == 0) ? c : nb<0>(g, i, j, k, -1);
+    const long long ly = (g.bc[1] && j == 0) ? c : nb<1>(g, i, j, k, -1);
+    const long long lz = (g.bc[2] && k == 0) ? c : nb<2>(g, i, j, k, -1);
+    const double dv = (U[5 * N + c] - U[5 * N + lx]) * g.id[0] + (U[6 * N + c] - U[6 * N + ly]) * g.id[1] +
+                      (U[7 * N + c] - U[7 * N + lz]) * g.id[2];
     v[8] = fabs(dv);
   }
 #pragma unroll

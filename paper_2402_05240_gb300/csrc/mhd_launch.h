@@ -16,6 +16,10 @@ struct Grid {
   double gm1, igm1;  // gamma - 1 and 1/(gamma - 1)
   double rho_floor, p_floor;
   double cfl;
+  // interior box [lo, hi) of a padded grid (outflow boundaries): the CFL
+  // reduction and the floor counters cover it only; lo = 0, hi = n otherwise
+  int lo[3], hi[3];
+  int bc[3];         // boundary condition per axis of the caller's grid (0 periodic, 1 outflow)
 };
 
 // Launchers of the step kernels for compute type T (double: FP64 step,
@@ -63,5 +67,12 @@ void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, do
 
 // max |div B| and field sums of a state into red[0..8] (red holds 9 + 9 nb doubles)
 void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s);
+
+// outflow boundaries: copy the caller's state U (grid gi) into the interior
+// box of the padded state Up (grid gp), copy it back, and fill every ghost
+// cell of Up (outside gp's interior box) from the nearest interior cell
+void launch_pad(const Grid& gp, const Grid& gi, const double* U, double* Up, cudaStream_t s);
+void launch_unpad(const Grid& gp, const Grid& gi, const double* Up, double* U, cudaStream_t s);
+void launch_fill_ghosts(const Grid& gp, double* Up, cudaStream_t s);
 
 }  // namespace mhd

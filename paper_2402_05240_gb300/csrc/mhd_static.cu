@@ -58,6 +58,8 @@ extern "C" int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev
   if (!cfg || !U_dev || !divb_max_host || !totals_host) return MHD_ERR_ARG;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return MHD_ERR_ARG;
   if (!(cfg->dx > 0) || !(cfg->dy > 0) || !(cfg->dz > 0)) return MHD_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (cfg->bc[a] != MHD_BC_PERIODIC && cfg->bc[a] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
   if (N > kMaxCells || cfg->nz > 65535) return MHD_ERR_TOO_LARGE;
   double* scratch = nullptr;
@@ -78,6 +80,11 @@ extern "C" int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev
   g.rho_floor = cfg->rho_floor;
   g.p_floor = cfg->p_floor;
   g.cfl = cfg->cfl;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = 0;
+    g.hi[a] = g.n[a];
+    g.bc[a] = cfg->bc[a];
+  }
   const int nblk = (int)((N + kCellsPerBlock - 1) / kCellsPerBlock);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Every partial the final pass reads is written by the partial pass of this

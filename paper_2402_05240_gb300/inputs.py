@@ -358,6 +358,55 @@ def orszag_tang(n: int, nz: int = 4, gamma=GAMMA_DEFAULT):
     return box, assemble(box, 25.0 / (36.0 * math.pi), vel, 5.0 / (12.0 * math.pi), bface, gamma)
 
 
+# The paper's Riemann problems (Sec. 3.1.4, table of initial conditions):
+# gamma, t_max, B_x, and the left / right states (rho, P, vx, vy, vz, By, Bz).
+_S4PI = math.sqrt(4.0 * math.pi)
+RIEMANN = {
+    "brio_wu": (2.0, 0.1, 0.75, (1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0), (0.125, 0.1, 0.0, 0.0, 0.0, -1.0, 0.0)),
+    "dai_woodward": (5.0 / 3.0, 0.2, 2.0 / _S4PI,
+                     (1.08, 0.95, 1.2, 0.01, 0.5, 3.6 / _S4PI, 2.0 / _S4PI),
+                     (1.0, 1.0, 0.0, 0.0, 0.0, 4.0 / _S4PI, 2.0 / _S4PI)),
+    "ryu_jones_1a": (5.0 / 3.0, 0.08, 5.0 / _S4PI, (1.0, 20.0, 10.0, 0.0, 0.0, 5.0 / _S4PI, 0.0),
+                     (1.0, 1.0, -10.0, 0.0, 0.0, 5.0 / _S4PI, 0.0)),
+    "ryu_jones_4d": (5.0 / 3.0, 0.16, 0.7, (1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0), (0.3, 0.2, 0.0, 0.0, 1.0, 1.0, 0.0)),
+    "einfeldt": (1.4, 0.16, 0.0, (1.0, 0.45, -2.0, 0.0, 0.0, 0.5, 0.0), (1.0, 0.45, 2.0, 0.0, 0.0, 0.5, 0.0)),
+}
+
+
+def riemann(name: str, n=512, ntrans=16, mirror=False, skew=0.0):
+    """One of the paper's Riemann problems along x on the unit box with
+    n x ntrans x ntrans cells, the states split at x = 1/2 (run with outflow
+    boundaries along x).  ``mirror``: the same problem reflected, x -> 1 - x
+    with v_x -> -v_x and B_x -> -B_x (left and right swapped).  ``skew``
+    scales the right state's rho and P by (1 + skew) (0 in the paper).
+    Returns (box, U, gamma, t_max)."""
+    gamma, t_max, bx, left, right = RIEMANN[name]
+    right = (right[0] * (1.0 + skew), right[1] * (1.0 + skew)) + tuple(right[2:])
+    box = Box(n, ntrans, ntrans)
+    x, _, _ = box.centres()
+    if mirror:
+        left, right = right, left
+    lmask = np.broadcast_to(x < 0.5, box.shape)
+    f = [np.where(lmask, a, b) for a, b in zip(left, right)]
+    rho, p, vx, vy, vz, by, bz = f
+    sx = -1.0 if mirror else 1.0
+    U = assemble(box, rho, (sx * vx, vy, vz), p, (np.full(box.shape, sx * bx), by, bz), gamma)
+    return box, U, gamma, t_max
+
+
+def blast_paper(nx=200, ny=300, nz=200, centre=(0.5, 0.75, 0.5), gamma=GAMMA_DEFAULT):
+    """MHD blast wave in a strongly magnetised medium (Sec. 3.1.5) on
+    1 x 1.5 x 1: rho = 1, P = 0.1 (beta = 0.2), B = (1, 1, 0)/sqrt2, v = 0,
+    P = 10 inside the sphere r < 0.1 about ``centre`` (the domain centre in
+    the paper; cell centres decide).  Returns (box, U)."""
+    box = Box(nx, ny, nz, 1.0, 1.5, 1.0)
+    x, y, z = box.centres()
+    r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
+    pres = np.where(r2 < 0.01, 10.0, 0.1)
+    b = 1.0 / math.sqrt(2.0)
+    return box, assemble(box, 1.0, (0.0, 0.0, 0.0), pres, (b, b, 0.0), gamma)
+
+
 def l1_error_norm(U, U0):
     """The paper's error measure (Sec. 3.1.1): the L2 norm over the conserved
     variables of their mean absolute differences."""

@@ -26,6 +26,7 @@ MHD_ERR_TOO_LARGE = -6
 
 RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
 PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_df": 2}
+BC = {"periodic": 0, "outflow": 1}
 
 
 class mhd_config(ctypes.Structure):
@@ -33,7 +34,8 @@ class mhd_config(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("recon", ctypes.c_int), ("precision", ctypes.c_int),
-                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
+                ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double),
+                ("bc", ctypes.c_int * 3)]
 
 
 def _load_library():
@@ -224,12 +226,13 @@ class Sim:
     """Owns one library context for a grid and a configuration."""
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, gamma=5.0 / 3.0, cfl=0.4, recon="plmc",
-                 precision="fp64", rho_floor=1e-20, p_floor=1e-20, stream=None):
+                 precision="fp64", rho_floor=1e-20, p_floor=1e-20, stream=None, bc=("periodic",) * 3):
         self.shape = (nz, ny, nx)
+        bcs = (ctypes.c_int * 3)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
         self.cfg = mhd_config(nx, ny, nz, lx / nx, ly / ny, lz / nz, gamma, cfl,
                               RECON[recon] if isinstance(recon, str) else recon,
                               PRECISION[precision] if isinstance(precision, str) else precision,
-                              rho_floor, p_floor)
+                              rho_floor, p_floor, bcs)
         self.ctx = mhd_init(self.cfg, stream)
 
     def close(self):

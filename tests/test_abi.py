@@ -52,11 +52,17 @@ def test_config_validation_without_gpu():
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 7, 0, 1e-20, 1e-20),  # recon
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 5, 1e-20, 1e-20),  # precision
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 0.0, 1e-20),  # floor
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(0, 2, 0)),  # bc
     ]
     for cfg in bad:
         with pytest.raises(mhd.MHDError) as e:
             mhd.mhd_workspace_bytes(cfg)
         assert e.value.code == mhd.MHD_ERR_ARG
+    # an outflow axis pads the grid by MHD_GHOST cells per side and adds the padded state
+    out = mhd.mhd_config(32, 32, 32, 1 / 32, 1 / 32, 1 / 32, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20,
+                         (ctypes.c_int * 3)(1, 0, 0))
+    ratio = mhd.mhd_workspace_bytes(out) / mhd.mhd_workspace_bytes(ok)
+    assert 48 / 32 < ratio < 48 / 32 * (1 + 8 * 8 / (49 * 8)) + 0.01
 
 
 def test_null_arguments_rejected(lib):
