@@ -69,6 +69,9 @@ extern "C" {
  * dt and the floor counters cover interior cells only. */
 #define MHD_BC_PERIODIC 0
 #define MHD_BC_OUTFLOW 1
+#define MHD_BC_HALO 2 /* subdomain of a decomposed periodic grid: MHD_GHOST halo
+                         cells per side, filled by mhd_step_sub (only entry
+                         point that accepts it) */
 #define MHD_GHOST 8
 
 typedef struct mhd_config {
@@ -109,6 +112,26 @@ int mhd_step(mhd_ctx* ctx, double* U_dev, double dt);
  * place.  dt_dev (device, may be NULL) receives the nsteps dt values used.
  * Asynchronous. */
 int mhd_run(mhd_ctx* ctx, double* U_dev, int nsteps, double* dt_dev);
+
+/* One step (Steps 2-10 at the given dt) of a subdomain of a periodic global
+ * grid: domain decomposition (Step 10 exchanges the halo cells of each
+ * rank's subdomain; Sec. 3.2 runs one subdomain per GPU).  ctx:
+ * created with cfg.nx, ny, nz = the subdomain's cells and bc = MHD_BC_HALO
+ * on every decomposed axis (MHD_BC_PERIODIC on axes it spans whole).
+ * Ug_dev: a state [8][gn[2]][gn[1]][gn[0]] holding the subdomain at offset
+ * off[3] and at least MHD_GHOST cells of halo around it along the decomposed
+ * axes (a whole periodic global grid, wrapped, or the subdomain's own
+ * halo-extended block at offset MHD_GHOST); read only.  Ug_out_dev (must not
+ * alias Ug_dev): receives the subdomain's new interior at the same offset;
+ * other cells are untouched.  The interior equals that of one mhd_step on
+ * the whole global grid bit for bit.  Asynchronous.  Errors: MHD_ERR_ARG
+ * (no MHD_BC_HALO axis, sizes, offsets, aliasing), MHD_ERR_DT. */
+int mhd_step_sub(mhd_ctx* ctx, const double* Ug_dev, const int gn[3], const int off[3], double dt, double* Ug_out_dev);
+
+/* Step 1 (Eq. dt) over the interior cells of a subdomain, with Ug_dev, gn
+ * and off as in mhd_step_sub (the halo supplies the lower faces of the first
+ * cells).  Synchronous; the global dt is the minimum over the subdomains. */
+int mhd_dt_sub(mhd_ctx* ctx, const double* Ug_dev, const int gn[3], const int off[3], double* dt_host);
 
 /* Advance U_dev in place from t = 0 to t = t_end (the end time of the paper's
  * tests, Sec. 3): device-dt steps as in mhd_run, the last one shortened so

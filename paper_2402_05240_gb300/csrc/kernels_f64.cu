@@ -20,6 +20,15 @@ void launch_pad(const Grid& gp, const Grid& gi, const double* U, double* Up, cud
 void launch_unpad(const Grid& gp, const Grid& gi, const double* Up, double* U, cudaStream_t s) {
   k_pad_copy<<<copy_blocks(8 * gi.N), 256, 0, s>>>(gp, gi, const_cast<double*>(Up), U, 1);
 }
+void launch_gather_sub(const Grid& gp, const Grid& gg, const int off[3], const double* Ug, double* Up,
+                       cudaStream_t s) {
+  k_gather_sub<<<copy_blocks(gp.N), 256, 0, s>>>(gp, gg, off[0], off[1], off[2], Ug, Up);
+}
+void launch_scatter_sub(const Grid& gp, const Grid& gg, const int off[3], const double* Up, double* Ug,
+                        cudaStream_t s) {
+  const long long M = (long long)(gp.hi[0] - gp.lo[0]) * (gp.hi[1] - gp.lo[1]) * (gp.hi[2] - gp.lo[2]);
+  k_scatter_sub<<<copy_blocks(8 * M), 256, 0, s>>>(gp, gg, off[0], off[1], off[2], Up, Ug);
+}
 void launch_fill_ghosts(const Grid& gp, double* Up, cudaStream_t s) {
   k_fill_ghosts<<<copy_blocks(gp.N), 256, 0, s>>>(gp, Up);
 }

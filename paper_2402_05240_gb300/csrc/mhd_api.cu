@@ -69,7 +69,10 @@ struct Layout {
 };
 
 bool padded(const mhd_config& c) {
-  return c.bc[0] == MHD_BC_OUTFLOW || c.bc[1] == MHD_BC_OUTFLOW || c.bc[2] == MHD_BC_OUTFLOW;
+  return c.bc[0] != MHD_BC_PERIODIC || c.bc[1] != MHD_BC_PERIODIC || c.bc[2] != MHD_BC_PERIODIC;
+}
+bool has_halo(const mhd_config& c) {
+  return c.bc[0] == MHD_BC_HALO || c.bc[1] == MHD_BC_HALO || c.bc[2] == MHD_BC_HALO;
 }
 
 // cells per axis of the step kernels' grid: MHD_GHOST more on each side of
@@ -77,7 +80,7 @@ bool padded(const mhd_config& c) {
 void padded_dims(const mhd_config& c, int n[3], int lo[3]) {
   const int ni[3] = {c.nx, c.ny, c.nz};
   for (int a = 0; a < 3; ++a) {
-    lo[a] = c.bc[a] == MHD_BC_OUTFLOW ? MHD_GHOST : 0;
+    lo[a] = c.bc[a] != MHD_BC_PERIODIC ? MHD_GHOST : 0;
     n[a] = ni[a] + 2 * lo[a];
   }
 }
@@ -134,7 +137,9 @@ int check_cfg(const mhd_config* c) {
   if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK && c->precision != MHD_FP64_DF) return MHD_ERR_ARG;
   if (!(c->rho_floor > 0) || !(c->p_floor > 0)) return MHD_ERR_ARG;
   for (int a = 0; a < 3; ++a)
-    if (c->bc[a] != MHD_BC_PERIODIC && c->bc[a] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
+    if (c->bc[a] != MHD_BC_PERIODIC && c->bc[a] != MHD_BC_OUTFLOW && c->bc[a] != MHD_BC_HALO) return MHD_ERR_ARG;
+  if (has_halo(*c) && (c->bc[0] == MHD_BC_OUTFLOW || c->bc[1] == MHD_BC_OUTFLOW || c->bc[2] == MHD_BC_OUTFLOW))
+    return MHD_ERR_ARG;  // subdomains of periodic global grids only
   int np[3], lo[3];
   padded_dims(*c, np, lo);
   if ((long long)np[0] * np[1] > (1ll << 31) || np[2] > 65535) return MHD_ERR_ARG;
@@ -277,6 +282,49 @@ template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
   Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, c->floors, s);
   leave(c, U);
   return cuda_status();
+}
+
+template <class T> int step_sub(mhd_ctx* c, const double* Ug, const int gn[3], const int off[3], double dt,
+                                double* Ug_out) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  Grid gg = c->gi;
+  for (int a = 0; a < 3; ++a) gg.n[a] = gn[a];
+  gg.N = (long long)gn[0] * gn[1] * gn[2];
+  mhd::launch_set_dt(c->scal, dt, s);
+  mhd::launch_gather_sub(g, gg, off, Ug, c->Up, s);
+  Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, nullptr, s);
+  step_body<T>(c, c->Up, c->cfg.recon);
+  Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, c->floors, s);
+  mhd::launch_scatter_sub(g, gg, off, c->Up, Ug_out, s);
+  return cuda_status();
+}
+
+template <class T> int dt_sub(mhd_ctx* c, const double* Ug, const int gn[3], const int off[3], double* dt_host) {
+  cudaStream_t s = c->stream;
+  Grid gg = c->gi;
+  for (int a = 0; a < 3; ++a) gg.n[a] = gn[a];
+  gg.N = (long long)gn[0] * gn[1] * gn[2];
+  mhd::launch_gather_sub(c->g, gg, off, Ug, c->Up, s);
+  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
+  Launch<T>::prim(c->g, c->Up, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
+  double v = 0;
+  if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  *dt_host = v;
+  if (!(v > 0.0) || !std::isfinite(v)) return MHD_ERR_DT;
+  return MHD_OK;
+}
+
+// sizes and offset of a subdomain inside the state handed to mhd_step_sub / mhd_dt_sub
+int check_sub(mhd_ctx* c, const int gn[3], const int off[3]) {
+  for (int a = 0; a < 3; ++a) {
+    if (gn[a] < c->gi.n[a] || off[a] < 0 || off[a] + c->gi.n[a] > gn[a]) return MHD_ERR_ARG;
+    if (c->cfg.bc[a] == MHD_BC_PERIODIC && gn[a] != c->gi.n[a]) return MHD_ERR_ARG;
+  }
+  if ((long long)gn[0] * gn[1] > (1ll << 31) || gn[2] > 65535) return MHD_ERR_ARG;
+  return MHD_OK;
 }
 
 // ---- adjoint ----------------------------------------------------------------
@@ -575,24 +623,43 @@ const char* mhd_stage_name(int stage) {
 
 int mhd_step(mhd_ctx* c, double* U, double dt) {
   if (!c || !U) return MHD_ERR_ARG;
+  if (has_halo(c->cfg)) return MHD_ERR_ARG;  // subdomains step through mhd_step_sub
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
   return with_type(c->cfg.precision, [&](auto t) { return one_step<MHD_T>(c, U, dt); });
 }
 
 int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {
   if (!c || !U || nsteps < 0) return MHD_ERR_ARG;
+  if (has_halo(c->cfg)) return MHD_ERR_ARG;  // subdomains step through mhd_step_sub
   if (nsteps == 0) return MHD_OK;
   return with_type(c->cfg.precision, [&](auto t) { return run_steps<MHD_T>(c, U, nsteps, dt_dev); });
 }
 
+int mhd_step_sub(mhd_ctx* c, const double* Ug, const int gn[3], const int off[3], double dt, double* Ug_out) {
+  if (!c || !Ug || !gn || !off || !Ug_out || Ug == Ug_out || !has_halo(c->cfg)) return MHD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
+  const int st = check_sub(c, gn, off);
+  if (st != MHD_OK) return st;
+  return with_type(c->cfg.precision, [&](auto t) { return step_sub<MHD_T>(c, Ug, gn, off, dt, Ug_out); });
+}
+
+int mhd_dt_sub(mhd_ctx* c, const double* Ug, const int gn[3], const int off[3], double* dt_host) {
+  if (!c || !Ug || !gn || !off || !dt_host || !has_halo(c->cfg)) return MHD_ERR_ARG;
+  const int st = check_sub(c, gn, off);
+  if (st != MHD_OK) return st;
+  return with_type(c->cfg.precision, [&](auto t) { return dt_sub<MHD_T>(c, Ug, gn, off, dt_host); });
+}
+
 int mhd_evolve(mhd_ctx* c, double* U, double t_end, int max_steps, double* t_host, int* steps_host) {
   if (!c || !U || max_steps < 0 || !(t_end >= 0.0) || !std::isfinite(t_end)) return MHD_ERR_ARG;
+  if (has_halo(c->cfg)) return MHD_ERR_ARG;
   return with_type(c->cfg.precision,
                    [&](auto t) { return evolve_to<MHD_T>(c, U, t_end, max_steps, t_host, steps_host); });
 }
 
 int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
   if (!c || !U || !dt_host) return MHD_ERR_ARG;
+  if (has_halo(c->cfg)) return MHD_ERR_ARG;  // subdomains step through mhd_step_sub
   cudaStream_t s = c->stream;
   cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   double* Um = enter(c, U);  // k_prim writes its state only when floors are requested

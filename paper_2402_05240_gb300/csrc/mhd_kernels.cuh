@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
     double r = U[c], e = U[4 * N + c];
     const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
-    if (!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) atomicOr(flags, 1u);
+    if ((!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) && in) atomicOr(flags, 1u);
     if (floors && r < g.rho_floor) {
       r = g.rho_floor;
       U[c] = r;
@@ -476,6 +476,40 @@ __global__ void k_pad_copy(Grid gp, Grid gi, double* Up, double* Ui, int dir) {
     const long long cp = f * gp.N + cidx(gp, i + gp.lo[0], j + gp.lo[1], k + gp.lo[2]);
     if (dir == 0) Up[cp] = Ui[q];
     else Ui[q] = Up[cp];
+  }
+}
+
+// Subdomain of a periodic global grid (gg): every cell of the padded
+// subdomain state Up (grid gp, interior box [lo, hi)) takes the global cell
+// at offset off + (p - lo), wrapped periodically: interior and halo in one
+// gather.
+__global__ void k_gather_sub(Grid gp, Grid gg, int o0, int o1, int o2, const double* __restrict__ Ug,
+                             double* __restrict__ Up) {
+  const long long N = gp.N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % gp.n[0]), j = (int)((c / gp.n[0]) % gp.n[1]);
+    const int k = (int)(c / ((long long)gp.n[0] * gp.n[1]));
+    int gi = (o0 + i - gp.lo[0]) % gg.n[0], gj = (o1 + j - gp.lo[1]) % gg.n[1], gk = (o2 + k - gp.lo[2]) % gg.n[2];
+    gi += gi < 0 ? gg.n[0] : 0;
+    gj += gj < 0 ? gg.n[1] : 0;
+    gk += gk < 0 ? gg.n[2] : 0;
+    const long long s = cidx(gg, gi, gj, gk);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Up[f * N + c] = Ug[f * gg.N + s];
+  }
+}
+
+// the interior box of Up into the global state at offset off (no wrap: the
+// subdomain lies inside the global grid)
+__global__ void k_scatter_sub(Grid gp, Grid gg, int o0, int o1, int o2, const double* __restrict__ Up,
+                              double* __restrict__ Ug) {
+  const int ni = gp.hi[0] - gp.lo[0], nj = gp.hi[1] - gp.lo[1], nk = gp.hi[2] - gp.lo[2];
+  const long long M = (long long)ni * nj * nk;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 8 * M; q += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(q / M);
+    const long long c = q - f * M;
+    const int i = (int)(c % ni), j = (int)((c / ni) % nj), k = (int)(c / ((long long)ni * nj));
+    Ug[f * gg.N + cidx(gg, o0 + i, o1 + j, o2 + k)] = Up[f * gp.N + cidx(gp, gp.lo[0] + i, gp.lo[1] + j, gp.lo[2] + k)];
   }
 }
 

@@ -74,5 +74,11 @@ void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cud
 void launch_pad(const Grid& gp, const Grid& gi, const double* U, double* Up, cudaStream_t s);
 void launch_unpad(const Grid& gp, const Grid& gi, const double* Up, double* U, cudaStream_t s);
 void launch_fill_ghosts(const Grid& gp, double* Up, cudaStream_t s);
+// subdomains: gather the padded subdomain state (interior + halo, periodic
+// wrap of the global grid gg) at global offset off; scatter its interior back
+void launch_gather_sub(const Grid& gp, const Grid& gg, const int off[3], const double* Ug, double* Up,
+                       cudaStream_t s);
+void launch_scatter_sub(const Grid& gp, const Grid& gg, const int off[3], const double* Up, double* Ug,
+                        cudaStream_t s);
 
 }  // namespace mhd

@@ -59,7 +59,7 @@ extern "C" int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return MHD_ERR_ARG;
   if (!(cfg->dx > 0) || !(cfg->dy > 0) || !(cfg->dz > 0)) return MHD_ERR_ARG;
   for (int a = 0; a < 3; ++a)
-    if (cfg->bc[a] != MHD_BC_PERIODIC && cfg->bc[a] != MHD_BC_OUTFLOW) return MHD_ERR_ARG;
+    if (cfg->bc[a] != MHD_BC_PERIODIC && cfg->bc[a] != MHD_BC_OUTFLOW && cfg->bc[a] != MHD_BC_HALO) return MHD_ERR_ARG;
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
   if (N > kMaxCells || cfg->nz > 65535) return MHD_ERR_TOO_LARGE;
   double* scratch = nullptr;

@@ -26,7 +26,7 @@ MHD_ERR_TOO_LARGE = -6
 
 RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
 PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_df": 2}
-BC = {"periodic": 0, "outflow": 1}
+BC = {"periodic": 0, "outflow": 1, "halo": 2}
 
 
 class mhd_config(ctypes.Structure):
@@ -54,6 +54,8 @@ def _load_library():
         "mhd_run": (ip, [vp, vp, ip, vp]),
         "mhd_run_host": (ip, [vp, vp, ip, dp]),
         "mhd_evolve": (ip, [vp, vp, ctypes.c_double, ip, dp, ctypes.POINTER(ip)]),
+        "mhd_step_sub": (ip, [vp, vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.c_double, vp]),
+        "mhd_dt_sub": (ip, [vp, vp, ctypes.POINTER(ip), ctypes.POINTER(ip), dp]),
         "mhd_adjoint_step": (ip, [vp, vp, ctypes.c_double, vp, vp]),
         "mhd_diagnostics": (ip, [vp, vp, dp, dp]),
         "mhd_status": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -135,6 +137,22 @@ def mhd_evolve(ctx, U: torch.Tensor, t_end: float, max_steps: int = 1 << 30):
     n = ctypes.c_int(0)
     _check(LIB.mhd_evolve(ctx, _ptr(U), float(t_end), int(max_steps), ctypes.byref(t), ctypes.byref(n)), "mhd_evolve")
     return t.value, n.value
+
+
+def mhd_step_sub(ctx, Ug: torch.Tensor, offset, dt: float, Ug_out: torch.Tensor):
+    """One step of a subdomain: Ug is [8, gnz, gny, gnx] holding it at
+    offset (ox, oy, oz) with its halo; its new interior goes to Ug_out."""
+    gn = (ctypes.c_int * 3)(Ug.shape[3], Ug.shape[2], Ug.shape[1])
+    off = (ctypes.c_int * 3)(*[int(o) for o in offset])
+    _check(LIB.mhd_step_sub(ctx, _ptr(Ug), gn, off, float(dt), _ptr(Ug_out)), "mhd_step_sub")
+
+
+def mhd_dt_sub(ctx, Ug: torch.Tensor, offset) -> float:
+    gn = (ctypes.c_int * 3)(Ug.shape[3], Ug.shape[2], Ug.shape[1])
+    off = (ctypes.c_int * 3)(*[int(o) for o in offset])
+    v = ctypes.c_double(0)
+    _check(LIB.mhd_dt_sub(ctx, _ptr(Ug), gn, off, ctypes.byref(v)), "mhd_dt_sub")
+    return v.value
 
 
 def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:

@@ -52,7 +52,8 @@ def test_config_validation_without_gpu():
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 7, 0, 1e-20, 1e-20),  # recon
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 5, 1e-20, 1e-20),  # precision
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 0.0, 1e-20),  # floor
-        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(0, 2, 0)),  # bc
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(0, 3, 0)),  # bc
+        mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(1, 2, 0)),  # outflow+halo
     ]
     for cfg in bad:
         with pytest.raises(mhd.MHDError) as e:
