@@ -73,20 +73,22 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # as profiled; a kernel changed since has no entry.
 COUNTERS = {
     "fp64": {
-        "prim": (121.0, 171.0, 937 / 32, 105.5),
-        "emf": (96.0, 111.0, 940 / 32, 139.4),
-        "update_half": (90.0, 128.0, 797 / 32, 283.3),
-        "recon": (361.0, 481.1, 2475 / 32, 150.1),
-        "flux_hlld": (275.8, 421.9, 1756 / 32, 162.3),
-        "update_full": (50.0, 71.0, 491 / 32, 260.2),
+        "prim": (121.0, 171.0, 954 / 32, 105.1),
+        "flux_pcm": (276.9, 423.3, 1766 / 32, 100.9),
+        "emf": (96.0, 111.0, 1028 / 32, 139.8),
+        "update_half": (88.0, 126.0, 826 / 32, 282.8),
+        "recon": (355.0, 475.1, 2453 / 32, 150.3),
+        "flux_hlld": (275.8, 421.9, 1758 / 32, 162.2),
+        "update_full": (50.0, 71.0, 524 / 32, 260.6),
     },
     "fp64_df": {
-        "prim": (37.0, 53.0, 1456 / 32, 105.1),
-        "emf": (0.0, 0.0, 1371 / 32, 139.9),
-        "update_half": (49.0, 66.0, 2144 / 32, 282.9),
-        "recon": (0.0, 0.0, 4194 / 32, 150.7),
-        "flux_hlld": (0.0, 0.0, 3090 / 32, 162.4),
-        "update_full": (19.0, 22.0, 1376 / 32, 260.2),
+        "prim": (37.0, 53.0, 1479 / 32, 105.2),
+        "flux_pcm": (0.0, 0.0, 3137 / 32, 101.1),
+        "emf": (0.0, 0.0, 1515 / 32, 140.0),
+        "update_half": (49.0, 66.0, 2591 / 32, 282.4),
+        "recon": (0.0, 0.0, 4200 / 32, 150.7),
+        "flux_hlld": (0.0, 0.0, 3093 / 32, 162.4),
+        "update_full": (19.0, 22.0, 1520 / 32, 259.9),
     },
 }
 

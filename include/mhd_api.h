@@ -46,6 +46,8 @@ extern "C" {
 #define MHD_RECON_PCM 0  /* piecewise constant (Sec. 2.2.2)                   */
 #define MHD_RECON_PLMC 1 /* piecewise linear, characteristic (Sec. 2.2.6)     */
 #define MHD_RECON_PPMC 2 /* piecewise parabolic, characteristic (Felker & Stone 2018) */
+#define MHD_RECON_PLM_PRIM 3 /* piecewise linear limited in the primitive variables
+                                (Sec. 2.2.6, last paragraph); no adjoint */
 
 #define MHD_FP64 0      /* all arithmetic in float64                          */
 #define MHD_FP32_BULK 1 /* reconstruction, Riemann solver and EMFs in float32;
@@ -152,7 +154,8 @@ int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
  * gU_n = (dU^{n+1}/dU^n)^T gU_np1.  U_n_dev: the state the forward step
  * started from (read only); gU_np1_dev: cotangent of U^{n+1}; gU_n_dev:
  * output, same layout as U.  Recomputes the forward intermediates in the
- * workspace.  Asynchronous.  Periodic grids only (MHD_ERR_ARG otherwise). */
+ * workspace.  Asynchronous.  Periodic grids and MHD_RECON_PCM / PLMC / PPMC
+ * only (MHD_ERR_ARG otherwise). */
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const double* gU_np1_dev,
                      double* gU_n_dev);
 

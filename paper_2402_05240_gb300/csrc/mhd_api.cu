@@ -133,7 +133,7 @@ int check_cfg(const mhd_config* c) {
   if (!(c->dx > 0) || !(c->dy > 0) || !(c->dz > 0)) return MHD_ERR_ARG;
   if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) return MHD_ERR_ARG;
   if (!(c->cfl > 0.0) || c->cfl > 1.0) return MHD_ERR_ARG;
-  if (c->recon < MHD_RECON_PCM || c->recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
+  if (c->recon < MHD_RECON_PCM || c->recon > MHD_RECON_PLM_PRIM) return MHD_ERR_ARG;
   if (c->precision != MHD_FP64 && c->precision != MHD_FP32_BULK && c->precision != MHD_FP64_DF) return MHD_ERR_ARG;
   if (!(c->rho_floor > 0) || !(c->p_floor > 0)) return MHD_ERR_ARG;
   for (int a = 0; a < 3; ++a)
@@ -703,6 +703,7 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
 
 int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {
   if (!c || !U_n || !gU_np1 || !gU_n || gU_np1 == gU_n) return MHD_ERR_ARG;
+  if (c->cfg.recon == MHD_RECON_PLM_PRIM) return MHD_ERR_ARG;  // no reverse sweep for this variant
   if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
   return with_adj_type(c->cfg.precision, [&](auto t) { return adjoint_step<MHD_T>(c, U_n, dt, gU_np1, gU_n); });
@@ -791,7 +792,7 @@ int mhd_stage_primitives(mhd_ctx* c, const double* U, double* W) {
 
 
 int mhd_stage_fluxes(mhd_ctx* c, const double* U, int recon, double* F) {
-  if (!c || !U || !F || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC) return MHD_ERR_ARG;
+  if (!c || !U || !F || recon < MHD_RECON_PCM || recon > MHD_RECON_PLM_PRIM) return MHD_ERR_ARG;
   if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_fluxes<MHD_T>(c, U, recon, F); });
 }
@@ -807,7 +808,7 @@ int mhd_stage_edges(mhd_ctx* c, const double* U, const double* F, double* E) {
 
 
 int mhd_stage_recon(mhd_ctx* c, const double* U, int axis, int recon, double* WL, double* WR) {
-  if (!c || !U || !WL || !WR || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PPMC)
+  if (!c || !U || !WL || !WR || axis < 0 || axis > 2 || recon < MHD_RECON_PCM || recon > MHD_RECON_PLM_PRIM)
     return MHD_ERR_ARG;
   if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   return with_type(c->cfg.precision, [&](auto t) { return stage_recon<MHD_T>(c, U, axis, recon, WL, WR); });

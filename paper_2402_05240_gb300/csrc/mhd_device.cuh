@@ -345,6 +345,25 @@ __device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T*
   }
 }
 
+// PLM with the limiter applied to the primitive differences themselves (the
+// variant named at the end of Sec. 2.2.6): the same slopes and limiter as
+// plmc, without the characteristic projection.
+template <class T>
+__device__ __forceinline__ void plm_prim(const T* wm, const T* w0, const T* wp, T* wl, T* wr) {
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const T dL = w0[q] - wm[q], dR = wp[q] - w0[q], dC = T(0.5) * (wp[q] - wm[q]);
+    const T pr = dL * dR;
+    T dm = T(0);
+    if (pr > T(0)) {
+      const T dG = T(2) * pr * trcp<T>(dL + dR);
+      dm = sgn0<T>(dC) * fmin(fmin(T(2) * fabs(dL), T(2) * fabs(dR)), fmin(fabs(dC), fabs(dG)));
+    }
+    wl[q] = w0[q] + T(0.5) * dm;
+    wr[q] = w0[q] - T(0.5) * dm;
+  }
+}
+
 // ------------------------------------------------------- PPMC (Sec. 2.2.6) --
 // Fourth-order interface values, Colella & Sekora (2008) interface limiter,
 // McCorquodale & Colella (2011) cell limiter (C = 1.25), in characteristic

@@ -222,12 +222,13 @@ __global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(G
     load_dir<A>(W, N, c, wl);
 #pragma unroll
     for (int q = 0; q < 7; ++q) wr[q] = wl[q];
-  } else if (RECON == 1) {
+  } else if (RECON == 1 || RECON == 3) {
     T wm[7], w0[7], wp[7];
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
     load_dir<A>(W, N, c, w0);
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
-    plmc<T>(T(g.gamma), wm, w0, wp, bn, wl, wr);
+    if (RECON == 1) plmc<T>(T(g.gamma), wm, w0, wp, bn, wl, wr);
+    else plm_prim<T>(wm, w0, wp, wl, wr);
   } else {
     T w[5][7];
 #pragma unroll
@@ -622,10 +623,14 @@ void Launch<T>::recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cu
       if (a == 0) k_recon<T, 1, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
       if (a == 1) k_recon<T, 1, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
       if (a == 2) k_recon<T, 1, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
-    } else {
+    } else if (rc == 2) {
       if (a == 0) k_recon<T, 2, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
       if (a == 1) k_recon<T, 2, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
       if (a == 2) k_recon<T, 2, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
+    } else {
+      if (a == 0) k_recon<T, 3, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 1) k_recon<T, 3, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
+      if (a == 2) k_recon<T, 3, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
     }
   }
 template <class T>

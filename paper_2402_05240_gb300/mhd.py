@@ -24,7 +24,7 @@ MHD_ERR_NONFINITE = -4
 MHD_ERR_DT = -5
 MHD_ERR_TOO_LARGE = -6
 
-RECON = {"pcm": 0, "plmc": 1, "ppmc": 2}
+RECON = {"pcm": 0, "plmc": 1, "ppmc": 2, "plm_prim": 3}
 PRECISION = {"fp64": 0, "fp32_bulk": 1, "fp64_df": 2}
 BC = {"periodic": 0, "outflow": 1, "halo": 2}
 

@@ -63,7 +63,7 @@ def test_dt(mhd, precision):
     assert abs(dt - ref) <= (1e-14 if precision == "fp64" else 1e-6) * ref
 
 
-@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc", "plm_prim"])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_recon_states(mhd, recon, axis):
     U = turb(RAGGED)
@@ -124,7 +124,7 @@ def test_config0_linear_wave_fp64(mhd):
     assert pert < 1e-8
 
 
-@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc", "plm_prim"])
 def test_turbulent_ragged_fp64(mhd, recon):
     U0 = turb(RAGGED, seed=7)
     got, dts = run_gpu(mhd, U0, RAGGED, 10, 0.3, recon=recon)

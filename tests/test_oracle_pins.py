@@ -263,7 +263,7 @@ def _wave_state(box, f_rho):
     return I.assemble(box, rho, (0.2, -0.1, 0.3), 0.9, (0.6, 0.5, -0.4))
 
 
-@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+@pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 def test_recon_uniform_has_zero_slope(recon):
     box = I.Box(8, 6, 5)
     U = I.uniform(box, 1.3, (0.2, -0.4, 0.1), 0.8, (0.7, -0.3, 0.5))
@@ -288,7 +288,7 @@ def test_plmc_linear_entropy_profile_gives_centred_slope():
         np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
 
 
-@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+@pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 def test_recon_flat_at_extremum(recon):
     """A local extremum of the cell averages gets no slope (Eq. limiter; MC11)."""
     box = I.Box(16, 4, 4)
@@ -297,11 +297,32 @@ def test_recon_flat_at_extremum(recon):
     i = 7  # the peak cell
     rho = U[0, 0, 0, :]
     assert rho[i] > rho[i - 1] and rho[i] > rho[i + 1]
-    if recon == "plmc":
+    if recon in ("plmc", "plm_prim"):
         assert WL[0, 0, 0, i] == rho[i] and WR[0, 0, 0, i] == rho[i]
     else:  # the MC11 limiter may keep a bounded curvature; the state stays within the local range
         assert min(rho[i - 1], rho[i + 1]) <= WL[0, 0, 0, i] <= rho[i] + 1e-15
         assert min(rho[i - 1], rho[i + 1]) <= WR[0, 0, 0, i] <= rho[i] + 1e-15
+
+
+def test_plm_prim_linear_profiles_give_centred_slopes():
+    """The primitive-limiting PLM (Sec. 2.2.6, last paragraph) limits each
+    primitive by itself: for data linear in x in every primitive (rho, P and
+    a transverse velocity here) all slope candidates coincide and the face
+    states are the means of the neighbouring cells."""
+    box = I.Box(16, 4, 4)
+    x, _, _ = box.centres()
+    sh = box.shape
+    rho = np.broadcast_to(1.0 + 0.3 * x, sh)
+    pres = np.broadcast_to(0.9 - 0.2 * x, sh)
+    vy = np.broadcast_to(-0.1 + 0.5 * x, sh)
+    U = I.assemble(box, rho, (0.2, vy, 0.3), pres, (0.6, 0.5, -0.4))
+    WL, WR = O.Oracle(16, 4, 4, recon="plm_prim").recon(U, 0)
+    W = O.Oracle(16, 4, 4).primitives(U)
+    # solver frame along x: (rho, vx, vy, vz, P, By, Bz)
+    for q, f in ((0, 0), (2, 2), (4, 4)):
+        for i in range(1, 14):
+            assert abs(WL[q, 0, 0, i] - 0.5 * (W[f, 0, 0, i] + W[f, 0, 0, i + 1])) < 1e-14
+            assert abs(WR[q, 0, 0, i] - 0.5 * (W[f, 0, 0, i] + W[f, 0, 0, i - 1])) < 1e-14
 
 
 def test_ppmc_exact_for_cubics():
