@@ -219,7 +219,8 @@ def time_adjoint(mhd, torch, U0, n, steps, warmup, recon, precision, barrier, fw
     code, _ = mhd.mhd_status(sim.ctx)
     sim.close()
     return {"value": n ** 3 / (ms * 1e-3), "ms_per_step": ms, "ratio_to_forward": ms / fwd_ms,
-            "dtype": "f64" if precision == "fp64" else "f32 (FP64 state)", "adjoint_workspace_gb": ws / 1e9,
+            "dtype": {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)", "fp64_df": "df64 (float pairs, FP64 state)"}[
+                precision], "adjoint_workspace_gb": ws / 1e9,
             "status": code}
 
 
@@ -447,6 +448,8 @@ def main():
         variants["adjoint_fp64"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64", barrier, ms64)
         variants["adjoint_fp32_bulk"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp32_bulk",
                                                      barrier, ms32)
+        variants["adjoint_fp64_df"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64_df",
+                                                   barrier, msdf)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -57,8 +57,9 @@ extern "C" {
                            relative error per operation, float exponent range)
                            on the FP32 pipes; state, pressure recovery and
                            accumulation in float64.  Differs from MHD_FP64 at
-                           the 1e-13 level.  The adjoint of this mode is the
-                           float64 adjoint. */
+                           the 1e-13 level; so does its adjoint (reverse sweep
+                           in double-float, cotangents of the state in
+                           float64). */
 
 /* Boundary condition of each axis (mhd_config.bc).  Periodic: wrap-around
  * indexing inside the kernels, no ghost cells.  Outflow (zero gradient, the
@@ -161,7 +162,7 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const doubl
 
 /* Bytes of device memory the first mhd_adjoint_step call allocates (once per
  * context, freed by mhd_destroy): forward intermediates of one step plus
- * cotangent buffers, 197 words of the compute type (float64 for
+ * cotangent buffers, 197 words of the compute type (a float pair for
  * MHD_FP64_DF) + 10 doubles per cell. */
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
@@ -250,7 +251,8 @@ int mhd_stage_recon_vjp(mhd_ctx* ctx, const double* U_dev, int axis, int recon, 
  * Miyoshi & Kusano 2005): wl_dev, wr_dev [n][7] solver-frame primitive states
  * (rho, u, v, w, P, B_t1, B_t2), bn_dev [n] longitudinal fields, gf_dev [n][7]
  * flux cotangents; writes gwl_dev, gwr_dev [n][7], gbn_dev [n] and the flux
- * f_dev [n][7].  precision: MHD_FP64 or MHD_FP32_BULK (arithmetic in float).
+ * f_dev [n][7].  precision: MHD_FP64, MHD_FP32_BULK (arithmetic in float) or
+ * MHD_FP64_DF (float pairs).
  * No context needed; asynchronous on stream. */
 int mhd_stage_hlld_vjp(int n, double gamma, int precision, const double* wl_dev, const double* wr_dev,
                        const double* bn_dev, const double* gf_dev, double* gwl_dev, double* gwr_dev, double* gbn_dev,

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libmhd.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_df.cu", "adj_f64.cu", "adj_f32.cu", "mhd_api.cu", "mhd_static.cu"]
+UNITS = ["kernels_f64.cu", "kernels_f32.cu", "kernels_df.cu", "adj_f64.cu", "adj_f32.cu", "adj_df.cu", "mhd_api.cu", "mhd_static.cu"]
 
 
 def nvcc() -> str:

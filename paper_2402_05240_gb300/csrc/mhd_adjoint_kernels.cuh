@@ -84,9 +84,9 @@ template <class T, int A>
 __device__ __forceinline__ double face_cot(const Grid& g, const double* __restrict__ gUpF, const T* __restrict__ gBcc,
                                            const T* __restrict__ gBfx, int i, int j, int k) {
   const long long N = g.N, c = cidx(g, i, j, k);
-  double v = 0.5 * ((double)gBcc[A * N + c] + (double)gBcc[A * N + nb<A>(g, i, j, k, 1)]);
+  double v = 0.5 * (to_d<T>(gBcc[A * N + c]) + to_d<T>(gBcc[A * N + nb<A>(g, i, j, k, 1)]));
   if (gUpF) v += gUpF[A * N + c];
-  if (gBfx) v += (double)gBfx[A * N + c];
+  if (gBfx) v += to_d<T>(gBfx[A * N + c]);
   return v;
 }
 
@@ -169,10 +169,10 @@ __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict_
   const T* Fb = F + (long long)B * 7 * N;  // mass flux of b-faces: Fb[x]
   const T* Fc = F + (long long)C * 7 * N;
   const T* gEk = gE + (long long)K * N;
-  const double g00 = gEk[c00], gmb = gEk[cb], gmc = gEk[cc], gmbc = gEk[cbc];
+  const double g00 = to_d<T>(gEk[c00]), gmb = to_d<T>(gEk[cb]), gmc = to_d<T>(gEk[cc]), gmbc = to_d<T>(gEk[cbc]);
   // mass fluxes: mc(q), mc(q + e_b), mc(q - e_c), mc(q - e_c + e_b); mb(q), mb(q + e_c), mb(q - e_b), mb(q - e_b + e_c)
-  const double mc0 = Fc[c00], mc_pb = Fc[cpb], mc_mc = Fc[cc], mc_mcpb = Fc[cmcpb];
-  const double mb0 = Fb[c00], mb_pc = Fb[cpc], mb_mb = Fb[cb], mb_mbpc = Fb[cmbpc];
+  const double mc0 = to_d<T>(Fc[c00]), mc_pb = to_d<T>(Fc[cpb]), mc_mc = to_d<T>(Fc[cc]), mc_mcpb = to_d<T>(Fc[cmcpb]);
+  const double mb0 = to_d<T>(Fb[c00]), mb_pc = to_d<T>(Fb[cpc]), mb_mb = to_d<T>(Fb[cb]), mb_mbpc = to_d<T>(Fb[cmbpc]);
   const double gbf = 0.25 * g00 * (1.0 + upw_lo(mc_pb) + upw_lo(mc0)) +
                      0.25 * gmc * (1.0 + (1.0 - upw_lo(mc_mcpb)) + (1.0 - upw_lo(mc_mc)));
   const double gcf = 0.25 * g00 * (1.0 + upw_lo(mb_pc) + upw_lo(mb0)) +
@@ -184,8 +184,8 @@ __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict_
   gF[((long long)B * 7 + 5) * N + c00] = T(-gbf);
   gF[((long long)C * 7 + 6) * N + c00] = T(gcf);
   // ref_K = -(v_B B_C - v_C B_B)
-  const double vB = W[(1 + B) * N + c00], vC = W[(1 + C) * N + c00];
-  const double BB = W[(5 + B) * N + c00], BC = W[(5 + C) * N + c00];
+  const double vB = to_d<T>(W[(1 + B) * N + c00]), vC = to_d<T>(W[(1 + C) * N + c00]);
+  const double BB = to_d<T>(W[(5 + B) * N + c00]), BC = to_d<T>(W[(5 + C) * N + c00]);
   gW8[1 + B] += -grf * BC;
   gW8[5 + C] += -grf * vB;
   gW8[1 + C] += grf * BB;
@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __res
   if (HALF) {
 #pragma unroll
     for (int f = 0; f < 5; ++f) h5[f] = Uh[f * N + c];
-    b[0] = 0.5 * ((double)Bh[nb<0>(g, i, j, k, -1)] + (double)Bh[c]);
-    b[1] = 0.5 * ((double)Bh[N + nb<1>(g, i, j, k, -1)] + (double)Bh[N + c]);
-    b[2] = 0.5 * ((double)Bh[2 * N + nb<2>(g, i, j, k, -1)] + (double)Bh[2 * N + c]);
+    b[0] = 0.5 * (to_d<T>(Bh[nb<0>(g, i, j, k, -1)]) + to_d<T>(Bh[c]));
+    b[1] = 0.5 * (to_d<T>(Bh[N + nb<1>(g, i, j, k, -1)]) + to_d<T>(Bh[N + c]));
+    b[2] = 0.5 * (to_d<T>(Bh[2 * N + nb<2>(g, i, j, k, -1)]) + to_d<T>(Bh[2 * N + c]));
   } else {
 #pragma unroll
     for (int f = 0; f < 5; ++f) h5[f] = U[f * N + c];
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __res
   }
   double gw8[8];
 #pragma unroll
-  for (int f = 0; f < 8; ++f) gw8[f] = (double)gW[f * N + c];
+  for (int f = 0; f < 8; ++f) gw8[f] = to_d<T>(gW[f * N + c]);
   double o5[5], gb[3] = {0.0, 0.0, 0.0};
   prim_vjp(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
 #pragma unroll
@@ -449,11 +449,11 @@ __global__ void k_hlld_vjp_batch(int n, double gamma, const double* __restrict__
   hlld<T>(T(gamma), a, b, T(bn[t]), ff);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    gwl[7 * t + q] = ga[q];
-    gwr[7 * t + q] = gb[q];
-    f[7 * t + q] = ff[q];
+    gwl[7 * t + q] = to_d<T>(ga[q]);
+    gwr[7 * t + q] = to_d<T>(gb[q]);
+    f[7 * t + q] = to_d<T>(ff[q]);
   }
-  gbn[t] = gn;
+  gbn[t] = to_d<T>(gn);
 }
 
 // --------------------------------------------------------------- launchers --

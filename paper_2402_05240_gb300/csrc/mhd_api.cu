@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/mhd_api.h"
+#include "mhd_df.cuh"
 #include "mhd_launch.h"
 
 using mhd::Grid;
@@ -54,11 +55,7 @@ template <class Fn> int with_type(int precision, Fn&& fn) {
   if (precision == MHD_FP64_DF) return fn(Tag<mhd::df>{});
   return fn(Tag<double>{});
 }
-// the adjoint of the double-float mode is the float64 adjoint
-template <class Fn> int with_adj_type(int precision, Fn&& fn) {
-  if (precision == MHD_FP32_BULK) return fn(Tag<float>{});
-  return fn(Tag<double>{});
-}
+template <class Fn> int with_adj_type(int precision, Fn&& fn) { return with_type(precision, fn); }
 #define MHD_T typename decltype(t)::type
 
 constexpr size_t kAlign = 256;
@@ -731,10 +728,10 @@ int mhd_stage_hlld_vjp(int n, double gamma, int precision, const double* wl, con
   if (n < 0 || !wl || !wr || !bn || !gf || !gwl || !gwr || !gbn || !f || !(gamma > 1.0)) return MHD_ERR_ARG;
   if (n == 0) return MHD_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == MHD_FP32_BULK)
-    mhd::AdjLaunch<float>::hlld_batch(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f, s);
-  else
-    mhd::AdjLaunch<double>::hlld_batch(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f, s);
+  with_type(precision, [&](auto t) {
+    mhd::AdjLaunch<MHD_T>::hlld_batch(n, gamma, wl, wr, bn, gf, gwl, gwr, gbn, f, s);
+    return 0;
+  });
   return cuda_status();
 }
 

@@ -51,6 +51,17 @@ template <> __device__ __forceinline__ df tsqrt<df>(df x) { return df_sqrt(x); }
 template <> __device__ __forceinline__ df trcp<df>(df x) { return df(1.0f, 0.0f) / x; }
 template <> __device__ __forceinline__ df trsqrt<df>(df x) { return df_rsqrt(x); }
 
+// Conversions between the compute type and double without the conversion
+// instructions, which issue at the FP64 rate on this GPU (mhd_df.cuh).
+template <class T> __device__ __forceinline__ double to_d(T x);
+template <> __device__ __forceinline__ double to_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_d<float>(float x) { return f2d_bits(x); }
+template <> __device__ __forceinline__ double to_d<df>(df x) { return (double)x; }
+template <class T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return d2f_bits(x); }
+template <> __device__ __forceinline__ df from_d<df>(double x) { return df(x); }
+
 // Exact<T>: the full update widens each flux and edge value to double before
 // differencing (a difference of two floats is exact in double).  df values
 // already carry ~48 bits, so their differences and increments are formed in

@@ -41,6 +41,26 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)b);
 }
 
+// double -> float, rounded to nearest even, on the bit pattern (integer
+// instructions only): exact IEEE rounding for results in the normal float
+// range; results below 2^-126 flush to a signed zero, overflow gives an
+// infinity and NaN stays NaN.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned eb = (hw >> 20) & 0x7ffu;
+  const unsigned s = hw & 0x80000000u;
+  const unsigned m = ((hw & 0xfffffu) << 3) | (lw >> 29);  // kept 23 bits
+  const unsigned r = lw & 0x1fffffffu;                     // dropped 29 bits
+  unsigned v = ((eb - 896u) << 23) | m;
+  // a carry out of the significand raises the exponent (to infinity at the top)
+  v += (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  v = eb < 897u ? 0u : v;
+  const unsigned nan = (eb == 0x7ffu && ((hw & 0xfffffu) | lw)) ? 0x7fc00000u : 0x7f800000u;
+  v = eb > 1150u ? nan : v;
+  return __uint_as_float(s | v);
+}
+
 struct df;
 __device__ __forceinline__ df df_from_double(double x);
 
@@ -114,6 +134,11 @@ __device__ __forceinline__ df operator*(df x, df y) {
   return fast_two_sum(p.hi, l);
 }
 __device__ __forceinline__ df operator/(df x, df y) {
+  // below 2^-100 the reciprocal of the leading float would overflow for
+  // subnormal divisors: scale both operands by 2^100 (exact)
+  const float sc = fabsf(y.hi) < 7.888609052210118e-31f ? 1.2676506002282294e30f : 1.0f;
+  x = df(x.hi * sc, x.lo * sc);
+  y = df(y.hi * sc, y.lo * sc);
   const float r = __frcp_rn(y.hi);
   const float q1 = x.hi * r;
   // remainder x - q1 y, formed with an exact product
@@ -146,11 +171,13 @@ __device__ __forceinline__ df df_sqrt(df x) {
   return fast_two_sum(s, c);
 }
 
-// 1/sqrt(x): r = rsqrt(hi), one Newton step r + r (1 - x r^2) / 2 in df
+// 1/sqrt(x): r = rsqrt(hi), one Newton step r + r (1 - x r^2) / 2 in df;
+// the residual is formed as (x r) r, which stays near 1, so r^2 never
+// overflows for tiny x
 __device__ __forceinline__ df df_rsqrt(df x) {
   const float r = rsqrtf(x.hi);
   const df rr(r, 0.0f);
-  const df e = df(1.0f) - x * (rr * rr);
+  const df e = df(1.0f) - (x * rr) * rr;
   return rr + df(0.5f * r, 0.0f) * e;
 }
 

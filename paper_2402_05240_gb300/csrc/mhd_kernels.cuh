@@ -70,8 +70,8 @@ template <class T> __device__ __forceinline__ T cell_inv_crossing(const Grid& g,
   T best = T(0);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const T cf = fast_speed<T>(T(g.gamma), w8[0], w8[4], w8[5 + l], w8[5 + (l + 1) % 3], w8[5 + (l + 2) % 3]);
-    best = fmax(best, (fabs(w8[1 + l]) + cf) * T(g.id[l]));
+    const T cf = fast_speed<T>(from_d<T>(g.gamma), w8[0], w8[4], w8[5 + l], w8[5 + (l + 1) % 3], w8[5 + (l + 2) % 3]);
+    best = fmax(best, (fabs(w8[1 + l]) + cf) * from_d<T>(g.id[l]));
   }
   return best;
 }
@@ -102,14 +102,14 @@ __device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, d
 
 template <class T>
 __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
-  w8[0] = T(p.rho);
-  w8[1] = T(p.v[0]);
-  w8[2] = T(p.v[1]);
-  w8[3] = T(p.v[2]);
-  w8[4] = T(p.p);
-  w8[5] = T(p.b[0]);
-  w8[6] = T(p.b[1]);
-  w8[7] = T(p.b[2]);
+  w8[0] = from_d<T>(p.rho);
+  w8[1] = from_d<T>(p.v[0]);
+  w8[2] = from_d<T>(p.v[1]);
+  w8[3] = from_d<T>(p.v[2]);
+  w8[4] = from_d<T>(p.p);
+  w8[5] = from_d<T>(p.b[0]);
+  w8[6] = from_d<T>(p.b[1]);
+  w8[7] = from_d<T>(p.b[2]);
 #pragma unroll
   for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
 }
@@ -181,7 +181,7 @@ __device__ __forceinline__ void pcm_face(const Grid& g, const T* __restrict__ W,
   T wl[7], wr[7], f[7];
   load_dir<A>(W, N, c, wl);
   load_dir<A>(W, N, cn, wr);
-  hlld<T>(T(g.gamma), wl, wr, T(U[(5 + A) * N + c]), f);
+  hlld<T>(from_d<T>(g.gamma), wl, wr, from_d<T>(U[(5 + A) * N + c]), f);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, const T* __restrict
 
 // ------------------------------------------------------------------ Step 6 --
 template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* w) {
-  w[0] = fmax(w[0], T(g.rho_floor));
-  w[4] = fmax(w[4], T(g.p_floor));
+  w[0] = fmax(w[0], from_d<T>(g.rho_floor));
+  w[4] = fmax(w[4], from_d<T>(g.p_floor));
 }
 
 // blocks of 128 threads per SM requested from the register allocator (4:
@@ -227,13 +227,13 @@ __global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(G
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
     load_dir<A>(W, N, c, w0);
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
-    if (RECON == 1) plmc<T>(T(g.gamma), wm, w0, wp, bn, wl, wr);
+    if (RECON == 1) plmc<T>(from_d<T>(g.gamma), wm, w0, wp, bn, wl, wr);
     else plm_prim<T>(wm, w0, wp, wl, wr);
   } else {
     T w[5][7];
 #pragma unroll
     for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
-    ppmc<T>(T(g.gamma), w, bn, wl, wr);
+    ppmc<T>(from_d<T>(g.gamma), w, bn, wl, wr);
   }
   floor_face<T>(g, wl);
   floor_face<T>(g, wr);
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
     wl[q] = WL[q * N + c];
     wr[q] = WR[q * N + cn];
   }
-  hlld<T>(T(g.gamma), wl, wr, Bf[A * N + c], f);
+  hlld<T>(from_d<T>(g.gamma), wl, wr, Bf[A * N + c], f);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
@@ -321,10 +321,11 @@ __device__ __forceinline__ double face_curl(const Grid& g, const T* __restrict__
   const T* EB = E + (long long)B * N;
   const T* EC = E + (long long)C * N;
   if (EXACT) {
-    return ((double)EC[c] - (double)EC[nb<B>(g, i, j, k, -1)]) * g.id[B] -
-           ((double)EB[c] - (double)EB[nb<C>(g, i, j, k, -1)]) * g.id[C];
+    return (to_d<T>(EC[c]) - to_d<T>(EC[nb<B>(g, i, j, k, -1)])) * g.id[B] -
+           (to_d<T>(EB[c]) - to_d<T>(EB[nb<C>(g, i, j, k, -1)])) * g.id[C];
   }
-  return (double)((EC[c] - EC[nb<B>(g, i, j, k, -1)]) * T(g.id[B]) - (EB[c] - EB[nb<C>(g, i, j, k, -1)]) * T(g.id[C]));
+  return to_d<T>((EC[c] - EC[nb<B>(g, i, j, k, -1)]) * from_d<T>(g.id[B]) -
+                 (EB[c] - EB[nb<C>(g, i, j, k, -1)]) * from_d<T>(g.id[C]));
 }
 
 // solver-frame component of the global field f (0 rho, 1-3 m, 4 E) in the flux of axis a
@@ -351,7 +352,7 @@ __device__ __forceinline__ void hydro_update(const Grid& g, const double* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        acc -= hd[a] * ((double)Fa[c] - (double)Fa[cm[a]]);
+        acc -= hd[a] * (to_d<T>(Fa[c]) - to_d<T>(Fa[cm[a]]));
       }
       out5[f] = acc;
     } else {
@@ -359,9 +360,9 @@ __device__ __forceinline__ void hydro_update(const Grid& g, const double* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        inc -= T(hd[a]) * (Fa[c] - Fa[cm[a]]);
+        inc -= from_d<T>(hd[a]) * (Fa[c] - Fa[cm[a]]);
       }
-      out5[f] = U0[f * N + c] + (double)inc;
+      out5[f] = U0[f * N + c] + to_d<T>(inc);
     }
   }
 }
@@ -394,9 +395,9 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
   const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
   const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
-  Bh[c] = T(bx);
-  Bh[N + c] = T(by);
-  Bh[2 * N + c] = T(bz);
+  Bh[c] = from_d<T>(bx);
+  Bh[N + c] = from_d<T>(by);
+  Bh[2 * N + c] = from_d<T>(bz);
   const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   // (the outer ghost layers of a padded grid see the wrap and carry no check)
   if ((!(u5[0] > 0.0) || !isfinite(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);

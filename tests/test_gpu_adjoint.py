@@ -48,7 +48,7 @@ def face_states(n, seed):
     return wl, wr, bn
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_bulk", 2e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32_bulk", 2e-3), ("fp64_df", 1e-10)])
 def test_hlld_vjp_dot_product(mhd, precision, tol):
     n = 3000
     wl, wr, bn = face_states(n, 1)
@@ -121,7 +121,8 @@ def test_recon_vjp_dot_product(mhd, recon, axis):
 
 @pytest.mark.parametrize("recon,precision,tol", [("pcm", "fp64", 1e-10), ("plmc", "fp64", 1e-10),
                                                  ("ppmc", "fp64", 1e-10), ("plmc", "fp32_bulk", 1e-3),
-                                                 ("ppmc", "fp32_bulk", 1e-3)])
+                                                 ("ppmc", "fp32_bulk", 1e-3), ("plmc", "fp64_df", 1e-10),
+                                                 ("ppmc", "fp64_df", 1e-10)])
 def test_adjoint_step_dot_product(mhd, recon, precision, tol):
     n = (26, 18, 14)
     U = turb(n, 41)
@@ -172,7 +173,7 @@ def test_adjoint_step_with_floors(mhd):
     assert abs(lhs - rhs) <= 1e-9 * float(np.sum(np.abs(JdU * g)))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk", "fp64_df"])
 @pytest.mark.parametrize("recon", ["plmc", "ppmc"])
 def test_adjoint_finite_on_quiet_regions(mhd, precision, recon):
     """The blast (uniform B along x) leaves cells with velocities and
