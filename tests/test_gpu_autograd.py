@@ -160,3 +160,59 @@ def test_fp32_bulk_gradient_close_to_fp64(mods):
     # the velocity gradient is small (the loss is magnetic): looser relative bound
     assert np.linalg.norm(out[1][0] - out[0][0]) / np.linalg.norm(out[0][0]) <= 1e-2
     assert math.isfinite(float(np.sum(out[1][0])))
+
+
+def test_rollout_adjoint_128_cubed_20_steps(mods):
+    """The adjoint configuration at full size: 128^3 turbulent box (the
+    benchmark recipe), PLMC, 20 steps at the recorded dts.  (1) Dot test of
+    the 20-step adjoint chain against the oracle's dual-number JVP of the
+    same 20 steps along 2 seeded directions (a velocity-like and a
+    divergence-free face-field one): <g_20, J v> = <J^T g_20, v>.  Central
+    differences are no check at this size: 2M cells x 20 steps put a limiter
+    or upwind switch between x + eps d and x - eps d for every direction
+    tried.  (2) The FP32-bulk rollout gradient of the magnetic energy agrees
+    with the FP64 one to 1e-3."""
+    import oracle as O
+    mhd, A = mods
+    n = (128, 128, 128)
+    nsteps = 20
+    U0 = I.turbulent_box(I.Box(*n), seed_v=1, seed_b=2)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    sim = mhd.Sim(*n, cfl=0.3, recon="plmc")
+    Ut = t(U0)
+    dts, states = [], [U0]
+    for _ in range(nsteps):
+        d = torch.zeros(1, dtype=torch.float64, device="cuda")
+        mhd.mhd_run(sim.ctx, Ut, 1, d)
+        dts.append(float(d.item()))
+        states.append(Ut.cpu().numpy())
+    rng = np.random.default_rng(5)
+    gN = rng.normal(size=U0.shape)
+    g = t(gN)
+    for s in range(nsteps - 1, -1, -1):
+        g = sim.adjoint_step(t(states[s]), dts[s], g)
+    g0 = g.cpu().numpy()
+    orc = O.Oracle(*n, recon="plmc")
+    for trial in range(2):
+        v = np.zeros_like(U0)
+        if trial == 0:
+            v[1:4] = rng.normal(size=(3,) + U0.shape[1:]) * 1e-2
+        else:
+            v[5:8] = div_free_direction(n, rng) * 1e-2
+        V, dV = U0, v
+        for s in range(nsteps):
+            V, dV = orc.step_jvp(V, dV, dts[s])
+        lhs, rhs = float(np.sum(gN * dV)), float(np.sum(g0 * v))
+        assert abs(lhs - rhs) <= 1e-8 * float(np.sum(np.abs(gN * dV))), (trial, lhs, rhs)
+    # FP32-bulk against FP64 rollout gradients of the magnetic energy
+    rho, vel, bf = U0[0], U0[1:4] / U0[0], U0[5:8]
+    pres = np.ones_like(rho)
+    grads = {}
+    for precision in ("fp64", "fp32_bulk"):
+        s = sim if precision == "fp64" else mhd.Sim(*n, cfl=0.3, recon="plmc", precision=precision)
+        vv = t(vel).requires_grad_(True)
+        b = t(bf).requires_grad_(True)
+        L = loss_of(A, s, n, t(rho), vv, t(pres), b, nsteps, dts, k=5)
+        L.backward()
+        grads[precision] = np.concatenate([vv.grad.cpu().numpy().ravel(), b.grad.cpu().numpy().ravel()])
+    assert np.linalg.norm(grads["fp32_bulk"] - grads["fp64"]) / np.linalg.norm(grads["fp64"]) <= 1e-3
