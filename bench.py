@@ -316,8 +316,33 @@ def run_reference(args):
                          "sample": f"{n}^3 per step, {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if args.ref_sweep:
+        line["cpu_baseline"]["sweep"] = oracle_sweep(args.recon)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def oracle_sweep(recon, sizes=((32, 10), (128, 1), (256, 1)), single=((32, 2), (128, 1))):
+    """Per-step time and cell-updates/s of the oracle on this host: all cores
+    (OpenMP over cells) at 32^3, 128^3 and 256^3, and one thread at 32^3 and
+    128^3 (the turbulent recipe, the CFL dt of the initial state)."""
+    import oracle
+    out = []
+    allc = oracle.set_threads(0)
+    for threads, cases in ((allc, sizes), (1, single)):
+        oracle.set_threads(threads)
+        for n, steps in cases:
+            U = make_state(n)
+            orc = oracle.Oracle(n, n, n, recon=recon)
+            dt = orc.dt(U, 0.3)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                U = orc.step(U, dt)
+            el = (time.perf_counter() - t0) / steps
+            out.append({"n": n, "threads": threads, "s_per_step": round(el, 4),
+                        "cell_updates_per_s": n ** 3 / el})
+    oracle.set_threads(allc)
+    return out
 
 
 def run_workload(args, mhd, torch, rank):
@@ -359,6 +384,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--recon", default="plmc", choices=["plmc", "ppmc"])
     ap.add_argument("--ref-n", type=int, default=96)
+    ap.add_argument("--ref-sweep", action="store_true",
+                    help="with --impl reference: also time the oracle at 32^3-256^3, all cores and one thread")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp64_df"],
                     help="precision of the headline timed run (default: the FP64 step)")

@@ -55,6 +55,8 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lib.oracle_dt.restype = ctypes.c_double
             lib.oracle_dt.argtypes = [P, dp, ctypes.c_double]
+            lib.oracle_set_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             ip3 = ctypes.POINTER(ctypes.c_int)
             lib.oracle_dt_box.restype = ctypes.c_double
             lib.oracle_dt_box.argtypes = [P, dp, ctypes.c_double, ip3, ip3]
@@ -126,6 +128,11 @@ class OutflowOracle:
             V = self.step(V, dt)
             used.append(dt)
         return V, used
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (n <= 0: unchanged); returns the previous count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):

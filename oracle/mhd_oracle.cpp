@@ -31,6 +31,10 @@
 #include <limits>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------- scalars --
@@ -851,6 +855,18 @@ void oracle_primitives(const Params* P, const double* U, double* W) {
 }
 
 double oracle_dt(const Params* P, const double* U, double cfl) { return cfl_dt(*P, U, cfl); }
+
+// threads of the OpenMP loops (for timing the oracle single-threaded); returns the previous count
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  const int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 double oracle_dt_box(const Params* P, const double* U, double cfl, const int* lo, const int* hi) {
   return cfl_dt(*P, U, cfl, lo, hi);
