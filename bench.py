@@ -81,6 +81,15 @@ COUNTERS = {
         "flux_hlld": (275.8, 421.9, 1758 / 32, 162.2),
         "update_full": (50.0, 71.0, 524 / 32, 260.6),
     },
+    "fp32_bulk": {
+        "prim": (36.0, 52.0, 796 / 32, 81.4),
+        "flux_pcm": (0.0, 0.0, 572 / 32, 46.0),
+        "emf": (0.0, 0.0, 570 / 32, 66.8),
+        "update_half": (38.0, 55.0, 1591 / 32, 171.9),
+        "recon": (0.0, 0.0, 807 / 32, 62.9),
+        "flux_hlld": (0.0, 0.0, 545 / 32, 74.3),
+        "update_full": (19.0, 22.0, 1433 / 32, 180.5),
+    },
     "fp64_df": {
         "prim": (37.0, 53.0, 1479 / 32, 105.2),
         "flux_pcm": (0.0, 0.0, 3137 / 32, 101.1),
@@ -227,15 +236,16 @@ def time_adjoint(mhd, torch, U0, n, steps, warmup, recon, precision, barrier, fw
 def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     """Roofline of the dominant stage (largest share of the timed region).
 
-    FP64: the stage is bound by the FP64 pipe; achieved = counted FP64 pipe
-    operations (DFMA + DADD + DMUL) per launch / live launch time, against the
-    measured FP64 pipe rate (the same ratio in flop terms is reported too).
-    Double-float: bound by instruction issue; achieved = counted warp
-    instructions per launch / launch time against the 4-per-clock-per-SM
-    issue limit.  FP32-bulk (and any stage without counters): algorithmic
-    bytes per launch / launch time against the measured HBM copy bandwidth.
-    `traffic` is the ncu DRAM bytes per cell of the profiled 128^3 launch
-    scaled to this launch's cells (null without counters).
+    With per-cell counters of the stage (PLMC runs; ncu capture at 128^3):
+    the stage is bound by the FP64 pipe or by instruction issue, whichever
+    runs closer to its peak -- achieved = counted FP64-pipe operations
+    (DFMA + DADD + DMUL) per launch / live launch time against the measured
+    FP64 pipe rate, or counted warp instructions per launch / launch time
+    against the 4-per-clock-per-SM issue limit; both are reported, with the
+    HBM view and the flop view.  Without counters: algorithmic bytes per
+    launch / launch time against the measured HBM copy bandwidth.  `traffic`
+    is the ncu DRAM bytes per cell of the profiled 128^3 launch scaled to
+    this launch's cells (null without counters).
     """
     T = 4 if precision == "fp32_bulk" else 8
     sb = stage_bytes(T)
@@ -249,22 +259,22 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
            "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                    "peak_source": peak_kind}}
     cnt = COUNTERS.get(precision, {}).get(name) if recon == "plmc" else None
-    if cnt and precision == "fp64":
+    if cnt:
         gi = cnt[0] * n3 / per_launch_s / 1e9
-        gf = cnt[1] * n3 / per_launch_s / 1e9
-        out.update({"bound": "alu", "achieved": round(gi, 1), "peak": FP64_PIPE_GINST,
-                    "unit": "G FP64-pipe op/s (DFMA+DADD+DMUL)", "frac": round(gi / FP64_PIPE_GINST, 4),
-                    "peak_source": "measured (FP64 FMA-chain probe)", "traffic": round(cnt[3] * n3),
-                    "flop": {"achieved_gflops": round(gf, 1), "peak_gflops": FP64_PEAK_GFLOPS,
-                             "frac": round(gf / FP64_PEAK_GFLOPS, 4), "flop_per_cell": cnt[1]},
-                    "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
-    elif cnt and precision == "fp64_df":
         gw = cnt[2] * n3 / per_launch_s / 1e9
-        out.update({"bound": "alu", "achieved": round(gw, 1), "peak": round(ISSUE_PEAK_GWARPINST, 1),
-                    "unit": "G warp-inst/s issued", "frac": round(gw / ISSUE_PEAK_GWARPINST, 4),
-                    "peak_source": "nominal (4 issue slots per clock per SM, 152 SMs, 2.07 GHz)",
+        fp64 = {"achieved": round(gi, 1), "peak": FP64_PIPE_GINST, "unit": "G FP64-pipe op/s (DFMA+DADD+DMUL)",
+                "frac": round(gi / FP64_PIPE_GINST, 4), "peak_source": "measured (FP64 FMA-chain probe)"}
+        issue = {"achieved": round(gw, 1), "peak": round(ISSUE_PEAK_GWARPINST, 1), "unit": "G warp-inst/s issued",
+                 "frac": round(gw / ISSUE_PEAK_GWARPINST, 4),
+                 "peak_source": "nominal (4 issue slots per clock per SM, 152 SMs, 2.07 GHz)"}
+        main = fp64 if fp64["frac"] >= issue["frac"] else issue
+        out.update({"bound": "alu", **main, "fp64_pipe": fp64, "issue": issue,
                     "traffic": round(cnt[3] * n3),
                     "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
+        if cnt[1]:
+            gf = cnt[1] * n3 / per_launch_s / 1e9
+            out["flop"] = {"achieved_gflops": round(gf, 1), "peak_gflops": FP64_PEAK_GFLOPS,
+                           "frac": round(gf / FP64_PEAK_GFLOPS, 4), "flop_per_cell": cnt[1]}
     else:
         out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(gbs / hbm_peak, 4), "peak_source": peak_kind, "traffic": None})
