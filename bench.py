@@ -77,7 +77,7 @@ COUNTERS = {
         "flux_pcm": (276.9, 423.3, 1766 / 32, 100.9),
         "emf": (96.0, 111.0, 1028 / 32, 139.8),
         "update_half": (88.0, 126.0, 826 / 32, 282.8),
-        "recon": (355.0, 475.1, 2453 / 32, 150.3),
+        "recon": (341.2, 467.4, 2335 / 32, 150.3),
         "flux_hlld": (275.8, 421.9, 1758 / 32, 162.2),
         "update_full": (50.0, 71.0, 524 / 32, 260.6),
     },
@@ -95,7 +95,7 @@ COUNTERS = {
         "flux_pcm": (0.0, 0.0, 3137 / 32, 101.1),
         "emf": (0.0, 0.0, 1515 / 32, 140.0),
         "update_half": (49.0, 66.0, 2591 / 32, 282.4),
-        "recon": (0.0, 0.0, 4200 / 32, 150.7),
+        "recon": (0.0, 0.0, 4162 / 32, 150.8),
         "flux_hlld": (0.0, 0.0, 3093 / 32, 162.4),
         "update_full": (19.0, 22.0, 1520 / 32, 259.9),
     },

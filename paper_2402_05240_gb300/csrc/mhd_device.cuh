@@ -318,6 +318,48 @@ template <class T> __device__ __forceinline__ void eig_right(const Eig<T>& E, co
 
 template <class T> __device__ __forceinline__ T sgn0(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 
+// Sign tests and magnitude minima of the limiters.  The generic forms use
+// floating-point instructions; for double they run on the bit patterns
+// (integer pipes), because the FP64 pipe bounds the FP64 step on this GPU.
+// Both give the same result for finite values whose products do not
+// underflow.
+template <class T> __device__ __forceinline__ bool pos_prod(T a, T b) { return a * b > T(0); }
+template <class T> __device__ __forceinline__ bool neg_prod(T a, T b) { return a * b < T(0); }
+template <class T> __device__ __forceinline__ T min_abs(T a, T b) { return fmin(fabs(a), fabs(b)); }
+// sgn0(s) m for m >= 0
+template <class T> __device__ __forceinline__ T with_sign(T s, T m) { return sgn0<T>(s) * m; }
+template <class T> __device__ __forceinline__ bool abs_ge_twice(T a, T b) { return fabs(a) >= T(2) * fabs(b); }
+template <class T> __device__ __forceinline__ T twice(T x) { return T(2) * x; }
+template <> __device__ __forceinline__ df twice<df>(df x) { return df(2.0f * x.hi, 2.0f * x.lo); }
+
+constexpr long long kAbsBits = 0x7fffffffffffffffLL;
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+template <> __device__ __forceinline__ bool pos_prod<double>(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  return ((x ^ y) >= 0) & ((x & kAbsBits) != 0) & ((y & kAbsBits) != 0);
+}
+template <> __device__ __forceinline__ bool neg_prod<double>(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  return ((x ^ y) < 0) & ((x & kAbsBits) != 0) & ((y & kAbsBits) != 0);
+}
+template <> __device__ __forceinline__ double min_abs<double>(double a, double b) {
+  const long long x = dbits(a) & kAbsBits, y = dbits(b) & kAbsBits;
+  return __longlong_as_double(x < y ? x : y);
+}
+template <> __device__ __forceinline__ double with_sign<double>(double s, double m) {
+  const long long x = dbits(s);
+  return (x & kAbsBits) ? __longlong_as_double(dbits(m) | (x & ~kAbsBits)) : 0.0;
+}
+// |a| >= 2 |b|: the exponent of |b| raised by one (normal b; b = 0 stays 0)
+template <> __device__ __forceinline__ bool abs_ge_twice<double>(double a, double b) {
+  const long long x = dbits(a) & kAbsBits, y = dbits(b) & kAbsBits;
+  return x >= (y ? y + (1LL << 52) : 0LL);
+}
+template <> __device__ __forceinline__ double twice<double>(double v) {
+  const long long x = dbits(v);
+  return (x & kAbsBits) ? __longlong_as_double(x + (1LL << 52)) : v;
+}
+
 // ------------------------------------------------------- PLMC (Sec. 2.2.6) --
 // wm, w0, wp: primitive 7-vectors of cells i-1, i, i+1; bn: cell-centred
 // longitudinal field of cell i.  Outputs W_{L,i+1/2} and W_{R,i-1/2}.
@@ -329,8 +371,7 @@ __device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T*
     dL[q] = w0[q] - wm[q];
     dR[q] = wp[q] - w0[q];
     dC[q] = T(0.5) * (wp[q] - wm[q]);
-    const T pr = dL[q] * dR[q];
-    dG[q] = pr > T(0) ? T(2) * pr * trcp<T>(dL[q] + dR[q]) : T(0);
+    dG[q] = pos_prod<T>(dL[q], dR[q]) ? T(2) * (dL[q] * dR[q]) * trcp<T>(dL[q] + dR[q]) : T(0);
   }
   Eig<T> E;
   eig_build<T>(gamma, w0, bn, E);
@@ -341,9 +382,9 @@ __device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T*
   eig_left<T>(E, dG, aG);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    if (aL[q] * aR[q] > T(0)) {
-      const T m = fmin(fmin(T(2) * fabs(aL[q]), T(2) * fabs(aR[q])), fmin(fabs(aC[q]), fabs(aG[q])));
-      am[q] = sgn0<T>(aC[q]) * m;
+    if (pos_prod<T>(aL[q], aR[q])) {
+      const T m = min_abs<T>(min_abs<T>(twice<T>(aL[q]), twice<T>(aR[q])), min_abs<T>(aC[q], aG[q]));
+      am[q] = with_sign<T>(aC[q], m);
     } else {
       am[q] = T(0);
     }
@@ -379,16 +420,15 @@ __device__ __forceinline__ void plm_prim(const T* wm, const T* w0, const T* wp, 
 // Fourth-order interface values, Colella & Sekora (2008) interface limiter,
 // McCorquodale & Colella (2011) cell limiter (C = 1.25), in characteristic
 // deviations q_m - q_0 = L (W_m - W_0) of cell i.
+// sgn(x) min(|x|, C|y|, C|z|) when x, y, z share a strict sign, else 0 (C = 1.25)
 template <class T> __device__ __forceinline__ T d2lim3(T x, T y, T z) {
-  const T sx = sgn0<T>(x);
-  if (sx != T(0) && sx == sgn0<T>(y) && sx == sgn0<T>(z))
-    return sx * fmin(fabs(x), fmin(T(1.25) * fabs(y), T(1.25) * fabs(z)));
+  if (pos_prod<T>(x, y) && pos_prod<T>(x, z))
+    return with_sign<T>(x, min_abs<T>(x, min_abs<T>(T(1.25) * y, T(1.25) * z)));
   return T(0);
 }
 template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
-  const T sx = sgn0<T>(x);
-  if (sx != T(0) && sx == sgn0<T>(y) && sx == sgn0<T>(z) && sx == sgn0<T>(t))
-    return sx * fmin(fmin(fabs(x), T(1.25) * fabs(y)), fmin(T(1.25) * fabs(z), T(1.25) * fabs(t)));
+  if (pos_prod<T>(x, y) && pos_prod<T>(x, z) && pos_prod<T>(x, t))
+    return with_sign<T>(x, min_abs<T>(min_abs<T>(x, T(1.25) * y), min_abs<T>(T(1.25) * z, T(1.25) * t)));
   return T(0);
 }
 
@@ -401,24 +441,24 @@ template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T&
   const T d2m1 = q[0] - T(2) * q[1] + q[2];
   const T d20 = q[1] - T(2) * q[2] + q[3];
   const T d2p1 = q[2] - T(2) * q[3] + q[4];
-  if ((qm - q[1]) * (q[2] - qm) < T(0)) {
+  if (neg_prod<T>(qm - q[1], q[2] - qm)) {
     const T d2c = T(3) * (q[1] - T(2) * qm + q[2]);
     qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) / T(6);
   }
-  if ((qp - q[2]) * (q[3] - qp) < T(0)) {
+  if (neg_prod<T>(qp - q[2], q[3] - qp)) {
     const T d2c = T(3) * (q[2] - T(2) * qp + q[3]);
     qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) / T(6);
   }
   const T dqm = q[2] - qm, dqp = qp - q[2];
-  if (dqm * dqp <= T(0) || (q[2] - q[1]) * (q[3] - q[2]) <= T(0)) {
+  if (!pos_prod<T>(dqm, dqp) || !pos_prod<T>(q[2] - q[1], q[3] - q[2])) {
     const T d2f = T(6) * (qm - T(2) * q[2] + qp);
     T r = T(0);
     if (d2f != T(0)) r = d2lim4<T>(d2f, d2m1, d20, d2p1) / d2f;
     qm = q[2] - r * dqm;
     qp = q[2] + r * dqp;
   } else {
-    if (fabs(dqm) >= T(2) * fabs(dqp)) qm = q[2] - T(2) * dqp;
-    if (fabs(dqp) >= T(2) * fabs(dqm)) qp = q[2] + T(2) * dqm;
+    if (abs_ge_twice<T>(dqm, dqp)) qm = q[2] - twice<T>(dqp);
+    if (abs_ge_twice<T>(dqp, dqm)) qp = q[2] + twice<T>(dqm);
   }
 }
 

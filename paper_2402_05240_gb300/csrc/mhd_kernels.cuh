@@ -15,6 +15,8 @@
 // cells exist.  Threads map to cells with x fastest (coalesced rows).
 #pragma once
 
+#include <type_traits>
+
 #include "mhd_device.cuh"
 
 namespace mhd {
@@ -320,7 +322,12 @@ __device__ __forceinline__ double face_curl(const Grid& g, const T* __restrict__
   const long long N = g.N, c = cidx(g, i, j, k);
   const T* EB = E + (long long)B * N;
   const T* EC = E + (long long)C * N;
-  if (EXACT) {
+  if constexpr (EXACT && std::is_same<T, float>::value) {
+    // float edge values: each difference is exact as a float pair (TwoSum)
+    const df dc = two_sum(EC[c], -EC[nb<B>(g, i, j, k, -1)]);
+    const df db = two_sum(EB[c], -EB[nb<C>(g, i, j, k, -1)]);
+    return (double)(dc * df(g.id[B]) - db * df(g.id[C]));
+  } else if (EXACT) {
     return (to_d<T>(EC[c]) - to_d<T>(EC[nb<B>(g, i, j, k, -1)])) * g.id[B] -
            (to_d<T>(EB[c]) - to_d<T>(EB[nb<C>(g, i, j, k, -1)])) * g.id[C];
   }
@@ -334,20 +341,33 @@ __device__ __forceinline__ int comp_of(int f, int a) {
 }
 
 // new hydro state of one cell: U0 - h sum_a (F_a(p) - F_a(p - e_a)) / d_a.
-// EXACT: fluxes widened to double before differencing (a difference of two
-// floats is exact in double), so sums over the periodic box telescope to
-// double round-off: the FP32-bulk full update conserves rho, m, E like FP64.
-// Otherwise (FP32-bulk half step) the increment is formed in T and added to
-// the double state.
+// EXACT: every flux difference is exact -- in double for double fluxes, as a
+// float pair (TwoSum, FP32 pipes) for float fluxes -- and the increment is
+// accumulated in double or float pairs, so sums over the periodic box
+// telescope to round-off: the FP32-bulk full update conserves rho, m, E at
+// the FP64 level.  Otherwise (FP32-bulk half step) the increment is formed in
+// T and added to the double state.
 template <class T, bool EXACT>
 __device__ __forceinline__ void hydro_update(const Grid& g, const double* __restrict__ U0, const T* __restrict__ F,
                                              double h, int i, int j, int k, double* out5) {
   const long long N = g.N, c = cidx(g, i, j, k);
   const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
   const double hd[3] = {h * g.id[0], h * g.id[1], h * g.id[2]};
+  df hdf[3];
+  if constexpr (EXACT && std::is_same<T, float>::value) {
+    for (int a = 0; a < 3; ++a) hdf[a] = df(hd[a]);
+  }
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
-    if (EXACT) {
+    if constexpr (EXACT && std::is_same<T, float>::value) {
+      df inc(0.0f, 0.0f);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
+        inc += hdf[a] * two_sum(Fa[c], -Fa[cm[a]]);
+      }
+      out5[f] = U0[f * N + c] - (double)inc;
+    } else if (EXACT) {
       double acc = U0[f * N + c];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
