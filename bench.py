@@ -254,10 +254,24 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     per_launch_s = ms / max(launches, 1) * 1e-3
     shares = {k: round(v[0] / total, 4) for k, v in prof.items() if v[1]}
     gbs = sb[name] * n3 / per_launch_s / 1e9
+    steps = max(1, prof["update_full"][1])
+    step_s = total * 1e-3 / steps
+    counted = sum(sb[k] * v[1] for k, v in prof.items()) / steps
     out = {"kernel": name, "per_launch_ms": round(per_launch_s * 1e3, 4), "stage_share": shares,
-           "bytes_per_cell_counted": sum(sb[k] * v[1] for k, v in prof.items()) / max(1, prof["update_full"][1]),
+           "bytes_per_cell_counted": counted,
            "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                    "peak_source": peak_kind}}
+    # the whole step against HBM: counted bytes, the 128 B/cell minimum (read
+    # and write the state), and the ncu DRAM bytes of the profiled kernels
+    cells_per_s = n3 / step_s
+    step_hbm = {"cells_per_s": round(cells_per_s), "frac_counted": round(cells_per_s * counted / 1e9 / hbm_peak, 4),
+                "frac_min_128B": round(cells_per_s * 128 / 1e9 / hbm_peak, 4)}
+    table = COUNTERS.get(precision, {}) if recon == "plmc" else {}
+    if table and all(k in table for k in prof if k != "dt" and prof[k][1]):
+        ncu_b = sum(table[k][3] * v[1] for k, v in prof.items() if k != "dt") / steps
+        step_hbm.update({"ncu_dram_bytes_per_cell": round(ncu_b, 1),
+                         "frac_ncu": round(cells_per_s * ncu_b / 1e9 / hbm_peak, 4)})
+    out["step_hbm"] = step_hbm
     cnt = COUNTERS.get(precision, {}).get(name) if recon == "plmc" else None
     if cnt:
         gi = cnt[0] * n3 / per_launch_s / 1e9

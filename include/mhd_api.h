@@ -107,8 +107,11 @@ void mhd_destroy(mhd_ctx* ctx);
 int mhd_dt(mhd_ctx* ctx, const double* U_dev, double* dt_host);
 
 /* One VL+CT step (Steps 2-9) at the given dt, in place: U_dev holds U^n on
- * entry and U^{n+1} on return.  Asynchronous on the context's stream. */
-int mhd_step(mhd_ctx* ctx, double* U_dev, double dt);
+ * entry and U^{n+1} on return.  Asynchronous on the context's stream when
+ * next_dt_host is NULL; otherwise the CFL dt of U^{n+1} (Step 1 of the next
+ * step, from the same pass that applies the floors) is written there and the
+ * call synchronises (MHD_ERR_DT if it is not positive and finite). */
+int mhd_step(mhd_ctx* ctx, double* U_dev, double dt, double* next_dt_host);
 
 /* nsteps VL+CT steps, each with dt from Step 1 computed on the device (the
  * reduction of the full update of one step gives the dt of the next), in
@@ -196,6 +199,11 @@ int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev, void* str
  * triggers of the full updates since the last call.  Returns MHD_OK or
  * MHD_ERR_NONFINITE. */
 int mhd_status(mhd_ctx* ctx, long long counts_host[2]);
+
+/* Synchronise and read the density / pressure floor triggers (D-12) since
+ * the last call of this function or of mhd_status, then reset them; the
+ * error flags are left for mhd_status. */
+int mhd_floor_count(mhd_ctx* ctx, long long* n_rho_host, long long* n_p_host);
 
 /* Static message for a status code. */
 const char* mhd_strerror(int code);

@@ -268,7 +268,7 @@ template <class T> int evolve_to(mhd_ctx* c, double* U, double t_end, int max_st
   return cuda_status();
 }
 
-template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
+template <class T> int one_step(mhd_ctx* c, double* U, double dt, double* next_dt) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
   mhd::launch_set_dt(c->scal, dt, s);
@@ -276,9 +276,17 @@ template <class T> int one_step(mhd_ctx* c, double* U, double dt) {
   Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, nullptr, s);
   step_body<T>(c, S, c->cfg.recon);
   refill(c, S);
-  Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, c->floors, s);
+  if (next_dt) cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
+  Launch<T>::prim(g, S, as<T>(c->W), next_dt ? c->dtbits : nullptr, c->flags, c->floors, s);
   leave(c, U);
-  return cuda_status();
+  if (!next_dt) return cuda_status();
+  mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
+  double v = 0;
+  if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  *next_dt = v;
+  if (!(v > 0.0) || !std::isfinite(v)) return MHD_ERR_DT;
+  return MHD_OK;
 }
 
 template <class T> int step_sub(mhd_ctx* c, const double* Ug, const int gn[3], const int off[3], double dt,
@@ -618,11 +626,23 @@ const char* mhd_stage_name(int stage) {
   return names[stage];
 }
 
-int mhd_step(mhd_ctx* c, double* U, double dt) {
+int mhd_step(mhd_ctx* c, double* U, double dt, double* next_dt_host) {
   if (!c || !U) return MHD_ERR_ARG;
   if (has_halo(c->cfg)) return MHD_ERR_ARG;  // subdomains step through mhd_step_sub
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
-  return with_type(c->cfg.precision, [&](auto t) { return one_step<MHD_T>(c, U, dt); });
+  return with_type(c->cfg.precision, [&](auto t) { return one_step<MHD_T>(c, U, dt, next_dt_host); });
+}
+
+int mhd_floor_count(mhd_ctx* c, long long* n_rho, long long* n_p) {
+  if (!c) return MHD_ERR_ARG;
+  unsigned long long fc[2] = {0, 0};
+  cudaStream_t s = c->stream;
+  if (cudaMemcpyAsync(fc, c->floors, sizeof(fc), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  cudaMemsetAsync(c->floors, 0, 2 * sizeof(unsigned long long), s);
+  if (n_rho) *n_rho = (long long)fc[0];
+  if (n_p) *n_p = (long long)fc[1];
+  return cuda_status();
 }
 
 int mhd_run(mhd_ctx* c, double* U, int nsteps, double* dt_dev) {

@@ -50,7 +50,8 @@ def _load_library():
         "mhd_init": (ip, [ctypes.POINTER(vp), ctypes.POINTER(mhd_config), vp]),
         "mhd_destroy": (None, [vp]),
         "mhd_dt": (ip, [vp, vp, dp]),
-        "mhd_step": (ip, [vp, vp, ctypes.c_double]),
+        "mhd_step": (ip, [vp, vp, ctypes.c_double, dp]),
+        "mhd_floor_count": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "mhd_run": (ip, [vp, vp, ip, vp]),
         "mhd_run_host": (ip, [vp, vp, ip, dp]),
         "mhd_evolve": (ip, [vp, vp, ctypes.c_double, ip, dp, ctypes.POINTER(ip)]),
@@ -122,8 +123,21 @@ def mhd_dt(ctx, U: torch.Tensor) -> float:
     return v.value
 
 
-def mhd_step(ctx, U: torch.Tensor, dt: float):
-    _check(LIB.mhd_step(ctx, _ptr(U), float(dt)), "mhd_step")
+def mhd_step(ctx, U: torch.Tensor, dt: float, want_next_dt: bool = False):
+    """One step at dt in place; with want_next_dt, returns the CFL dt of the new state (synchronises)."""
+    if not want_next_dt:
+        _check(LIB.mhd_step(ctx, _ptr(U), float(dt), None), "mhd_step")
+        return None
+    v = ctypes.c_double(0)
+    _check(LIB.mhd_step(ctx, _ptr(U), float(dt), ctypes.byref(v)), "mhd_step")
+    return v.value
+
+
+def mhd_floor_count(ctx):
+    """(density, pressure) floor triggers since the last call; resets them."""
+    a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(LIB.mhd_floor_count(ctx, ctypes.byref(a), ctypes.byref(b)), "mhd_floor_count")
+    return a.value, b.value
 
 
 def mhd_run(ctx, U: torch.Tensor, nsteps: int, dt_log: torch.Tensor | None = None):
@@ -272,8 +286,11 @@ class Sim:
     def dt(self, U):
         return mhd_dt(self.ctx, U)
 
-    def step(self, U, dt):
-        mhd_step(self.ctx, U, dt)
+    def step(self, U, dt, want_next_dt=False):
+        return mhd_step(self.ctx, U, dt, want_next_dt)
+
+    def floor_count(self):
+        return mhd_floor_count(self.ctx)
 
     def run(self, U, nsteps, dt_log=None):
         mhd_run(self.ctx, U, nsteps, dt_log)

@@ -67,8 +67,8 @@ def test_config_validation_without_gpu():
 
 
 def test_null_arguments_rejected(lib):
-    lib.mhd_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]
+    lib.mhd_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
     lib.mhd_step.restype = ctypes.c_int
-    assert lib.mhd_step(None, None, 0.1) == -1
+    assert lib.mhd_step(None, None, 0.1, None) == -1
     lib.mhd_strerror.restype = ctypes.c_char_p
     assert lib.mhd_strerror(-4).startswith(b"non-finite")

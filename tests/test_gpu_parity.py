@@ -143,6 +143,18 @@ def test_turbulent_fp32_bulk(mhd, recon):
     assert np.all(err <= 1e-5), err
 
 
+def test_step_returns_next_dt_and_floor_counts(mhd):
+    n = (16, 12, 8)
+    U0 = turb(n, seed=12)
+    sim = mhd.Sim(*n, cfl=0.3)
+    U = cuda(U0)
+    nxt = sim.step(U, 1e-3, want_next_dt=True)
+    ref = O.Oracle(*n).step(U0, 1e-3)
+    assert abs(nxt - O.Oracle(*n).dt(ref, 0.3)) <= 1e-14 * nxt
+    assert sim.dt(U) == nxt
+    assert sim.floor_count() == (0, 0)
+
+
 def test_fixed_dt_step_matches_run(mhd):
     n = (16, 12, 8)
     U0 = turb(n, seed=11)
