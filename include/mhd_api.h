@@ -163,6 +163,20 @@ int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
 int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const double* gU_np1_dev,
                      double* gU_n_dev);
 
+/* Vector-Jacobian product of one step whose dt is the CFL dt of its own
+ * start state (not in the paper): U^{n+1} = S(U^n, dt(U^n)) with
+ * dt(U) = C_CFL / max over cells and axes of (|v_l| + c_f,l) / d_l (Eq. dt,
+ * Step 1), so gU_n = (dS/dU^n)^T gU_np1 + g_dt (d dt/dU^n)^T with
+ * g_dt = <gU_np1, dS/d dt>.  The maximum is differentiated at the lowest
+ * cell index that reaches it (then the lowest axis): one element of the
+ * subdifferential where cells tie.  Arguments as in mhd_adjoint_step;
+ * *dt_host and *g_dt_host (each may be NULL) receive dt (the value mhd_dt
+ * returns for U_n) and g_dt.  Synchronous (dt is read back before the
+ * recompute).  Errors: as mhd_adjoint_step, MHD_ERR_NONFINITE /
+ * MHD_ERR_DT from the reduction. */
+int mhd_adjoint_step_cfl(mhd_ctx* ctx, const double* U_n_dev, const double* gU_np1_dev, double* gU_n_dev,
+                         double* dt_host, double* g_dt_host);
+
 /* Bytes of device memory the first mhd_adjoint_step call allocates (once per
  * context, freed by mhd_destroy): forward intermediates of one step plus
  * cotangent buffers, 197 words of the compute type (a float pair for

@@ -73,6 +73,9 @@ def _load():
             lib.oracle_update.argtypes = [P, dp, dp, dp, ctypes.c_double, dp]
             lib.oracle_step.argtypes = [P, dp, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_step_jvp.argtypes = [P, dp, dp, ctypes.c_double]
+            lib.oracle_step_cfl_jvp.argtypes = [P, dp, dp, ctypes.c_double, dp]
+            lib.oracle_dt_jvp.restype = ctypes.c_double
+            lib.oracle_dt_jvp.argtypes = [P, dp, dp, ctypes.c_double, dp]
             lib.oracle_diagnostics.argtypes = [P, dp, dp, dp]
             lib.oracle_hlld_jvp.argtypes = [ctypes.c_double, dp, dp, ctypes.c_double, dp, dp, ctypes.c_double, dp, dp]
             lib.oracle_recon_jvp.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
@@ -234,6 +237,21 @@ class Oracle:
         dV = self._chk(dU).copy()
         self.lib.oracle_step_jvp(ctypes.byref(self.p), _ptr(V), _ptr(dV), dt)
         return V, dV
+
+    def dt_jvp(self, U, dU, cfl):
+        """(dt, d dt) of Eq. dt and its derivative along dU."""
+        d = ctypes.c_double(0)
+        dt = self.lib.oracle_dt_jvp(ctypes.byref(self.p), _ptr(self._chk(U)), _ptr(self._chk(dU)), cfl, ctypes.byref(d))
+        return dt, d.value
+
+    def step_cfl_jvp(self, U, dU, cfl):
+        """(U^{n+1}, J dU, dt) for one step at the CFL dt of U, the dt's
+        dependence on U differentiated too."""
+        V = self._chk(U).copy()
+        dV = self._chk(dU).copy()
+        dt = ctypes.c_double(0)
+        self.lib.oracle_step_cfl_jvp(ctypes.byref(self.p), _ptr(V), _ptr(dV), cfl, ctypes.byref(dt))
+        return V, dV, dt.value
 
     def recon_jvp(self, U, dU, axis, recon=None):
         """(WL, WR, dWL, dWR) of U -> (W_L, W_R) along ``axis`` and its derivative along dU."""

@@ -743,8 +743,9 @@ template <class S> void edge_emf(const Params& P, const Grid& g, const S* U, con
 // difference form, x then y then z) and face B_a -= h [(E_c(p) - E_c(p-e_b))/d_b
 // - (E_b(p) - E_b(p-e_c))/d_c]; h = dt/2 in Step 5 (D-1), dt in Step 9.
 // Index typos of the printed equations read per D-2 and D-3.
-template <class S>
-void update(const Params& P, const Grid& g, const S* U0, const S* F, const S* E, double h, S* Uout) {
+// (h is a double, or a dual number when the step size itself is differentiated)
+template <class S, class H>
+void update(const Params& P, const Grid& g, const S* U0, const S* F, const S* E, H h, S* Uout) {
   const long N = g.N;
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < N; ++c) {
@@ -803,7 +804,7 @@ template <class S> void apply_floors(const Params& P, const Grid& g, S* U, long 
 }
 
 // ------------------------------------------------------ O11. one VL+CT step --
-template <class S> void step(const Params& P, S* U, double dt, long long* counts) {
+template <class S, class H> void step(const Params& P, S* U, H dt, long long* counts) {
   Grid g(P);
   const long N = g.N;
   std::vector<S> U0(U, U + 8 * N), Uh(8 * N), F(21 * N), E(3 * N);
@@ -835,6 +836,42 @@ double cfl_dt(const Params& P, const double* U, double cfl, const int* lo = null
       best = std::min(best, t);
     }
   }
+  return cfl * best;
+}
+
+// Eq. dt with its directional derivative along dU: the minimum is taken at
+// its first attaining (cell, axis) in index order, as in cfl_dt's loop, and
+// differentiated there with dual numbers (one element of the subdifferential
+// where cells tie).  Returns dt; *ddt receives the derivative.
+double cfl_dt_jvp(const Params& P, const double* U, const double* dU, double cfl, double* ddt) {
+  Grid g(P);
+  double best = std::numeric_limits<double>::infinity();
+  long bc = -1;
+  int bl = 0;
+  for (long c = 0; c < g.N; ++c) {
+    int p[3];
+    g.coords(c, p);
+    Prim<double> w = primitive(P, g, U, p);
+    for (int l = 0; l < 3; ++l) {
+      double cf = fast_speed(P.gamma, w.rho, w.p, w.b[l], w.b[(l + 1) % 3], w.b[(l + 2) % 3]);
+      double t = P.d[l] / (std::fabs(w.v[l]) + cf);
+      if (t < best) {
+        best = t;
+        bc = c;
+        bl = l;
+      }
+    }
+  }
+  *ddt = 0.0;
+  if (bc < 0) return cfl * best;
+  std::vector<Dual> X(8 * g.N);
+  for (long i = 0; i < 8 * g.N; ++i) X[i] = Dual(U[i], dU[i]);
+  int p[3];
+  g.coords(bc, p);
+  Prim<Dual> w = primitive(P, g, X.data(), p);
+  Dual cf = fast_speed(P.gamma, w.rho, w.p, w.b[bl], w.b[(bl + 1) % 3], w.b[(bl + 2) % 3]);
+  Dual t = P.d[bl] / (S_abs(w.v[bl]) + cf);
+  *ddt = cfl * t.d;
   return cfl * best;
 }
 
@@ -965,6 +1002,28 @@ void oracle_step_jvp(const Params* P, double* U, double* dU, double dt) {
     U[i] = X[i].v;
     dU[i] = X[i].d;
   }
+}
+
+// Jacobian-vector product of one step at the CFL dt of its start state:
+// U^{n+1} = step(U, dt(U)), so J dU = (dstep/dU) dU + (dstep/d dt) (d dt/dU) dU.
+// *dt_out receives dt.
+void oracle_step_cfl_jvp(const Params* P, double* U, double* dU, double cfl, double* dt_out) {
+  Grid g(*P);
+  double ddt = 0.0;
+  const double dt = cfl_dt_jvp(*P, U, dU, cfl, &ddt);
+  const long M = 8 * g.N;
+  std::vector<Dual> X(M);
+  for (long i = 0; i < M; ++i) X[i] = Dual(U[i], dU[i]);
+  step(*P, X.data(), Dual(dt, ddt), nullptr);
+  for (long i = 0; i < M; ++i) {
+    U[i] = X[i].v;
+    dU[i] = X[i].d;
+  }
+  *dt_out = dt;
+}
+
+double oracle_dt_jvp(const Params* P, const double* U, const double* dU, double cfl, double* ddt) {
+  return cfl_dt_jvp(*P, U, dU, cfl, ddt);
 }
 
 // Forward-mode derivative of the HLLD flux: f = HLLD(wl, wr, bn), df = J (dwl, dwr, dbn).

@@ -7,9 +7,11 @@ recomputes each segment from its checkpoint (with the recorded dt sequence)
 and runs the adjoint steps of the segment in reverse, so at most
 ``checkpoint_every + n / checkpoint_every`` states are held at once.
 
-The time steps are fixed during differentiation: when ``dts`` is not given,
-the forward takes dt from the device CFL reduction of each step (Step 1) and
-records it; the derivative treats that sequence as constant.
+When ``dts`` is not given, the forward takes dt from the device CFL
+reduction of each step (Step 1) and records it.  By default the derivative
+treats that sequence as constant; with ``dt_grad=True`` each step's dt is
+differentiated as the function of its start state that it is
+(mhd_adjoint_step_cfl), so the gradient is that of the rollout as run.
 """
 from __future__ import annotations
 
@@ -39,7 +41,7 @@ class MHDStep(torch.autograd.Function):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, sim, nsteps, dts, k):
+    def forward(ctx, U0, sim, nsteps, dts, k, dt_grad=False):
         U = U0.detach().contiguous().clone()
         ckpt = {0: U.clone()}
         dts_used = []
@@ -58,6 +60,7 @@ class _Rollout(torch.autograd.Function):
         ctx.nsteps = nsteps
         ctx.dts = dts_used
         ctx.ckpt = ckpt
+        ctx.dt_grad = bool(dt_grad) and dts is None
         return U
 
     @staticmethod
@@ -74,22 +77,30 @@ class _Rollout(torch.autograd.Function):
                 sim.step(U, dts[s])
                 states.append(U.clone())
             for s in range(b - 1, a - 1, -1):
-                g = sim.adjoint_step(states[s - a], dts[s], g)
+                if ctx.dt_grad:
+                    g, dt, _ = sim.adjoint_step_cfl(states[s - a], g)
+                    if dt != dts[s]:
+                        raise RuntimeError(f"step {s}: recomputed CFL dt {dt!r} differs from the forward's {dts[s]!r}")
+                else:
+                    g = sim.adjoint_step(states[s - a], dts[s], g)
             del states
         ctx.ckpt = None
-        return g, None, None, None, None
+        return g, None, None, None, None, None
 
 
-def rollout(sim, U0: torch.Tensor, nsteps: int, dts=None, checkpoint_every: int | None = None) -> torch.Tensor:
+def rollout(sim, U0: torch.Tensor, nsteps: int, dts=None, checkpoint_every: int | None = None,
+            dt_grad: bool = False) -> torch.Tensor:
     """``nsteps`` VL+CT steps from U0, differentiable with respect to U0.
 
     dts: fixed dt sequence (else the device CFL dt of each step, recorded).
     checkpoint_every: segment length k of the step-level checkpointing
     (default: no intermediate checkpoints, one segment of nsteps).
+    dt_grad: with dts=None, also differentiate each CFL dt through its
+    start state (else the recorded dts are constants of the derivative).
     Returns U^{n}; ``rollout.last_dts`` is not kept: pass ``dts`` to control them.
     """
     k = int(checkpoint_every) if checkpoint_every else max(int(nsteps), 1)
-    return _Rollout.apply(U0, sim, int(nsteps), None if dts is None else [float(x) for x in dts], k)
+    return _Rollout.apply(U0, sim, int(nsteps), None if dts is None else [float(x) for x in dts], k, bool(dt_grad))
 
 
 def magnetic_energy(U: torch.Tensor, dV: float) -> torch.Tensor:

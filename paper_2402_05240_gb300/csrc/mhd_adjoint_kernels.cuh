@@ -39,13 +39,14 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   const int i = ci.i, j = ci.j, k = ci.k;
   const long long N = g.N, c = cidx(g, i, j, k);
   double u5[5];
-  hydro_update<T, true>(g, U, F, dt, i, j, k, u5);
-  const double bx = face_update<T, true, 0>(g, U, E, dt, i, j, k);
-  const double by = face_update<T, true, 1>(g, U, E, dt, i, j, k);
-  const double bz = face_update<T, true, 2>(g, U, E, dt, i, j, k);
-  const double bxm = face_update<T, true, 0>(g, U, E, dt, wrapi(i - 1, g.n[0]), j, k);
-  const double bym = face_update<T, true, 1>(g, U, E, dt, i, wrapi(j - 1, g.n[1]), k);
-  const double bzm = face_update<T, true, 2>(g, U, E, dt, i, j, wrapi(k - 1, g.n[2]));
+  constexpr bool X = Exact<T>::full;  // the arithmetic of k_update_full
+  hydro_update<T, X>(g, U, F, dt, i, j, k, u5);
+  const double bx = face_update<T, X, 0>(g, U, E, dt, i, j, k);
+  const double by = face_update<T, X, 1>(g, U, E, dt, i, j, k);
+  const double bz = face_update<T, X, 2>(g, U, E, dt, i, j, k);
+  const double bxm = face_update<T, X, 0>(g, U, E, dt, wrapi(i - 1, g.n[0]), j, k);
+  const double bym = face_update<T, X, 1>(g, U, E, dt, i, wrapi(j - 1, g.n[1]), k);
+  const double bzm = face_update<T, X, 2>(g, U, E, dt, i, j, wrapi(k - 1, g.n[2]));
   const double b[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   double g5[5];
 #pragma unroll
@@ -90,16 +91,53 @@ __device__ __forceinline__ double face_cot(const Grid& g, const double* __restri
   return v;
 }
 
-// MODE 0 (Step 9): gface from gUp faces + floor gBcc; writes gU faces = gface.
-// MODE 1 (Step 5): gface from gBf (HLLD B_n) + gBcc (W^{n+1/2}); gU faces += gface.
-template <class T, int MODE>
-__global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const double* g5src,
-                                                       const double* __restrict__ gUpF, const T* __restrict__ gBcc,
-                                                       const T* __restrict__ gBfx, double* gU,
-                                                       T* __restrict__ gF, T* __restrict__ gE) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
+// Fixed-order block sum (shuffle tree, then the warps in order): one partial
+// per block, so a later fixed-order sum of the partials is deterministic.
+__device__ __forceinline__ void block_sum_to(double v, double* part) {
+  __shared__ double red[BX * BY / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double m = red[0];
+    for (int w = 1; w < BX * BY / 32; ++w) m += red[w];
+    part[blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)] = m;
+  }
+}
+
+// d(update increment)/d(h) paired with the cotangents of the updated cell:
+// sum_f g_f D_f + sum_a g_face_a curl_a, with D_f = sum_a (F_a(p) - F_a(p - e_a))/d_a
+// and curl_a the face curl of E (the update is U' = U - h D, B' = B - h curl).
+template <class T>
+__device__ __forceinline__ double update_rate_dot(const Grid& g, const T* __restrict__ F, const T* __restrict__ E,
+                                                  const double* g5, const double* gf, int i, int j, int k) {
+  const long long N = g.N, c = cidx(g, i, j, k);
+  const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
+  double s = 0.0;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    double d = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
+      d += g.id[a] * (to_d<T>(Fa[c]) - to_d<T>(Fa[cm[a]]));
+    }
+    s += g5[f] * d;
+  }
+  s += gf[0] * face_curl<T, true, 0>(g, E, i, j, k);
+  s += gf[1] * face_curl<T, true, 1>(g, E, i, j, k);
+  s += gf[2] * face_curl<T, true, 2>(g, E, i, j, k);
+  return s;
+}
+
+// one cell of k_adj_update; returns its update_rate_dot term when SENS
+template <class T, int MODE, bool SENS>
+__device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const double* g5src,
+                                                  const double* __restrict__ gUpF, const T* __restrict__ gBcc,
+                                                  const T* __restrict__ gBfx, double* gU, T* __restrict__ gF,
+                                                  T* __restrict__ gE, const T* __restrict__ Fs,
+                                                  const T* __restrict__ Es, int i, int j, int k) {
   const long long N = g.N, c = cidx(g, i, j, k);
   const long long cp[3] = {nb<0>(g, i, j, k, 1), nb<1>(g, i, j, k, 1), nb<2>(g, i, j, k, 1)};
   // hydro: U'_f(p) has -h/d_a F_a(p) and +h/d_a F_a(p - e_a), so
@@ -146,6 +184,31 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
     gU[6 * N + c] += gf1;
     gU[7 * N + c] += gf2;
   }
+  if (SENS) {
+    double g5[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) g5[f] = g5src[f * N + c];
+    const double gf[3] = {gf0, gf1, gf2};
+    return update_rate_dot<T>(g, Fs, Es, g5, gf, i, j, k);
+  }
+  return 0.0;
+}
+
+// MODE 0 (Step 9): gface from gUp faces + floor gBcc; writes gU faces = gface.
+// MODE 1 (Step 5): gface from gBf (HLLD B_n) + gBcc (W^{n+1/2}); gU faces += gface.
+// SENS: also the block partials of sum_p update_rate_dot(Fs, Es) (the
+// cotangent of the step size h, up to the sign) into part.
+template <class T, int MODE, bool SENS>
+__global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const double* g5src,
+                                                       const double* __restrict__ gUpF, const T* __restrict__ gBcc,
+                                                       const T* __restrict__ gBfx, double* gU,
+                                                       T* __restrict__ gF, T* __restrict__ gE,
+                                                       const T* __restrict__ Fs, const T* __restrict__ Es,
+                                                       double* __restrict__ part) {
+  const CellIdx ci = cell_of_thread(g);
+  double sens = 0.0;
+  if (ci.ok) sens = adj_update_cell<T, MODE, SENS>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, Fs, Es, ci.i, ci.j, ci.k);
+  if (SENS) block_sum_to(sens, part);
 }
 
 // ---------------------------------------------------- R3 / R8: edge EMF --
@@ -409,7 +472,7 @@ __global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* 
   const int i = ci.i, j = ci.j, k = ci.k;
   const double h = 0.5 * dt;
   const long long N = g.N, c = cidx(g, i, j, k);
-  constexpr bool X = sizeof(T) == 8;
+  constexpr bool X = sizeof(T) == 8 && Exact<T>::full;  // the arithmetic of k_update_half
   double u5[5];
   hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
   const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
@@ -418,15 +481,126 @@ __global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* 
   const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
   const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
   const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
-  Bh[c] = T(bx);
-  Bh[N + c] = T(by);
-  Bh[2 * N + c] = T(bz);
+  Bh[c] = from_d<T>(bx);
+  Bh[N + c] = from_d<T>(by);
+  Bh[2 * N + c] = from_d<T>(bz);
 #pragma unroll
   for (int f = 0; f < 5; ++f) Uh[f * N + c] = u5[f];
   const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
   T w8[8];
   store_w<T>(g, W, c, p, w8);
+}
+
+// ------------------------------------- the CFL dt as a function of U^n --
+// dt(U) = C_CFL / r_max, r_max = max over cells p and axes l of
+// (|v_l| + c_f,l)(p) / d_l (Eq. dt, Step 1).  Its reverse adds
+// g_dt * d dt/dU to gU, where g_dt = <gU^{n+1}, dU^{n+1}/d dt> =
+// -sum_p [update_rate_dot of Step 9 + 1/2 update_rate_dot of Step 5], and
+// d dt/dU = -(dt / r_max) d r_max/dU is nonzero only at the maximising cell.
+// The maximum is differentiated at the lowest cell index reaching it (then
+// the lowest axis): one element of the subdifferential where cells tie.
+
+// c_f of Eq. c_f on forward-mode numbers (the formula of fast_speed)
+__device__ __forceinline__ Dl<double> fast_speed_dl(double gamma, Dl<double> rho, Dl<double> p, Dl<double> bl,
+                                                    Dl<double> bt1, Dl<double> bt2) {
+  const Dl<double> ir = Dl<double>(1.0) / rho;
+  const Dl<double> a2 = Dl<double>(gamma) * p * ir;
+  const Dl<double> t2 = (bt1 * bt1 + bt2 * bt2) * ir;
+  const Dl<double> b2 = bl * bl * ir + t2;
+  const Dl<double> dd = a2 - b2;
+  return dsqrt(Dl<double>(0.5) * (a2 + b2 + dsqrt(dd * dd + Dl<double>(4.0) * a2 * t2)));
+}
+
+// cells whose inverse crossing time (computed as in k_prim) equals r_max
+// post their index; the integer minimum is the maximising cell
+template <class T>
+__global__ void __launch_bounds__(BX* BY) k_adj_cfl_argmax(Grid g, const T* __restrict__ W,
+                                                           const unsigned long long* __restrict__ rbits,
+                                                           unsigned long long* __restrict__ idx) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok || !interior(g, ci.i, ci.j, ci.k)) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T w8[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) w8[f] = W[f * N + c];
+  const double r = to_d<T>(cell_inv_crossing<T>(g, w8));
+  if ((unsigned long long)__double_as_longlong(r) == *rbits) atomicMin(idx, (unsigned long long)c);
+}
+
+// one block: g_dt from the partials of both update reverses (fixed order),
+// then d dt/dU at the maximising cell into gU.  out = {g_dt, dt, cell}.
+constexpr int kCflThreads = 256;
+template <class T>  // (instantiated once per compute type's translation unit)
+__global__ void __launch_bounds__(kCflThreads) k_adj_cfl_term(Grid g, const double* __restrict__ U,
+                                                              const double* __restrict__ part, long long nparts,
+                                                              const unsigned long long* __restrict__ rbits,
+                                                              const unsigned long long* __restrict__ idx,
+                                                              double* __restrict__ gU, double* __restrict__ out) {
+  __shared__ double red[kCflThreads];
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  for (long long q = t; q < nparts; q += kCflThreads) acc += part[q] + 0.5 * part[nparts + q];
+  red[t] = acc;
+  __syncthreads();
+  for (int w = kCflThreads / 2; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  if (t != 0) return;
+  const double gdt = -red[0];
+  const double rmax = __longlong_as_double((long long)*rbits);
+  const double dt = g.cfl / rmax;
+  out[0] = gdt;
+  out[1] = dt;
+  out[2] = -1.0;
+  const unsigned long long cu = *idx;
+  if (cu >= (unsigned long long)g.N || !(rmax > 0.0)) return;
+  const long long N = g.N, c = (long long)cu;
+  const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long long)g.n[0] * g.n[1]));
+  const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
+  double b[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) b[a] = 0.5 * (U[(5 + a) * N + cm[a]] + U[(5 + a) * N + c]);
+  const double r0 = U[c], m[3] = {U[N + c], U[2 * N + c], U[3 * N + c]}, e = U[4 * N + c];
+  const PrimD p = prim_core(g, r0, m[0], m[1], m[2], e, b);
+  // the axis of the maximum (first on ties), in double
+  int l = 0;
+  double best = -1.0;
+  for (int a = 0; a < 3; ++a) {
+    const double cf = fast_speed_dl(g.gamma, Dl<double>(p.rho), Dl<double>(p.p), Dl<double>(p.b[a]),
+                                    Dl<double>(p.b[(a + 1) % 3]), Dl<double>(p.b[(a + 2) % 3])).v;
+    const double ra = (fabs(p.v[a]) + cf) * g.id[a];
+    if (ra > best) {
+      best = ra;
+      l = a;
+    }
+  }
+  // d r / d (rho, P, B_l, B_t1, B_t2): one forward-mode pass per input
+  double dcf[5];
+  for (int q = 0; q < 5; ++q) {
+    const Dl<double> x0(p.rho, q == 0 ? 1.0 : 0.0), x1(p.p, q == 1 ? 1.0 : 0.0), x2(p.b[l], q == 2 ? 1.0 : 0.0),
+        x3(p.b[(l + 1) % 3], q == 3 ? 1.0 : 0.0), x4(p.b[(l + 2) % 3], q == 4 ? 1.0 : 0.0);
+    dcf[q] = fast_speed_dl(g.gamma, x0, x1, x2, x3, x4).d;
+  }
+  const double coef = gdt * (-dt / rmax) * g.id[l];
+  double gw8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  gw8[0] = coef * dcf[0];
+  gw8[1 + l] = coef * (p.v[l] > 0.0 ? 1.0 : (p.v[l] < 0.0 ? -1.0 : 0.0));
+  gw8[4] = coef * dcf[1];
+  gw8[5 + l] = coef * dcf[2];
+  gw8[5 + (l + 1) % 3] = coef * dcf[3];
+  gw8[5 + (l + 2) % 3] = coef * dcf[4];
+  double o5[5], gb[3] = {0.0, 0.0, 0.0};
+  prim_vjp(g, r0, m[0], m[1], m[2], e, b, gw8, o5, gb);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) gU[f * N + c] += o5[f];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gU[(5 + a) * N + c] += 0.5 * gb[a];
+    gU[(5 + a) * N + cm[a]] += 0.5 * gb[a];
+  }
+  out[2] = (double)c;
 }
 
 // ---------------------------------------------- batch HLLD VJP (testing) --
@@ -465,11 +639,30 @@ void AdjLaunch<T>::floors(const Grid& g, const double* U, const T* F, const T* E
   }
 template <class T>
 void AdjLaunch<T>::update(const Grid& g, int mode, double h, const double* g5src, const double* gUpF, const T* gBcc,
-                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s) {
-    if (mode == 0)
-      k_adj_update<T, 0><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE);
-    else
-      k_adj_update<T, 1><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE);
+                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s, const T* Fs, const T* Es,
+                     double* part) {
+    const dim3 gr = grid_of(g), bl(BX, BY);
+    if (part) {
+      if (mode == 0)
+        k_adj_update<T, 0, true><<<gr, bl, 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, Fs, Es, part);
+      else
+        k_adj_update<T, 1, true><<<gr, bl, 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, Fs, Es, part);
+    } else {
+      if (mode == 0)
+        k_adj_update<T, 0, false><<<gr, bl, 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, nullptr, nullptr,
+                                                     nullptr);
+      else
+        k_adj_update<T, 1, false><<<gr, bl, 0, s>>>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, nullptr, nullptr,
+                                                     nullptr);
+    }
+  }
+template <class T>
+void AdjLaunch<T>::cfl_term(const Grid& g, const double* U, const T* W, const unsigned long long* rbits,
+                            const double* part, long long nparts, unsigned long long* idx, double* gU, double* out,
+                            cudaStream_t s) {
+    cudaMemsetAsync(idx, 0xff, sizeof(unsigned long long), s);
+    k_adj_cfl_argmax<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, rbits, idx);
+    k_adj_cfl_term<T><<<1, kCflThreads, 0, s>>>(g, U, part, nparts, rbits, idx, gU, out);
   }
 template <class T>
 void AdjLaunch<T>::emf(const Grid& g, const T* W, const T* F, const T* gE, T* gF, T* gW, cudaStream_t s) {

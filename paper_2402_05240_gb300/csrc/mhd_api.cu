@@ -336,16 +336,24 @@ int check_sub(mhd_ctx* c, const int gn[3], const int off[3]) {
 // Adjoint workspace (compute type T): forward intermediates W^n[8], F^n[21],
 // W^{n+1/2}[8], B^{n+1/2}[3], W_L/W_R of the three axes [21+21], F^{n+1/2}[21],
 // E[3]; cotangents gF[21], gE[3], gW[8], gWL[7], gWR[7], recon slots[36],
-// gBf[3], gBcc[3], gBccF[3]; in double the half-step hydro state[5] and g5[5].
+// gBf[3], gBcc[3], gBccF[3]; in double the half-step hydro state[5] and g5[5];
+// then the per-block partials of the dt cotangent (two per block) and a few
+// scalars for the reverse of the CFL dt.
+size_t adj_part_count(const mhd_config& c) { return (size_t)mhd::cell_blocks(c.nx, c.ny, c.nz); }
 size_t adj_bytes_of(const mhd_config& c) {
   const size_t N = (size_t)c.nx * c.ny * c.nz;
   const size_t ts = c.precision == MHD_FP32_BULK ? 4 : 8;
-  return up(197 * N * ts) + up(10 * N * sizeof(double)) + 4 * kAlign;
+  return up(197 * N * ts) + up(10 * N * sizeof(double)) + up((2 * adj_part_count(c) + 8) * sizeof(double)) +
+         4 * kAlign;
 }
 
 template <class T> struct AdjView {
   T *Wn, *Fn, *Wh, *Bh, *WLa, *WRa, *Fh, *Eh, *gF, *gE, *gW, *gWL, *gWR, *gS, *gBf, *gBcc, *gBccF;
   double *Uh, *g5;
+  double* part;              // [2][nparts] dt-cotangent partials of the Step 9 and Step 5 reverses
+  long long nparts;
+  double* out;               // [3] g_dt, dt, maximising cell
+  unsigned long long* idx;   // argmax word
 };
 
 template <class T> int adj_view(mhd_ctx* c, AdjView<T>& v) {
@@ -386,10 +394,19 @@ template <class T> int adj_view(mhd_ctx* c, AdjView<T>& v) {
   char* d = reinterpret_cast<char*>(c->adj_ws) + up(197 * N * sizeof(T));
   v.Uh = reinterpret_cast<double*>(d);
   v.g5 = v.Uh + 5 * N;
+  v.nparts = (long long)adj_part_count(c->cfg);
+  v.part = reinterpret_cast<double*>(d + up(10 * N * sizeof(double)));
+  v.out = v.part + 2 * v.nparts;
+  v.idx = reinterpret_cast<unsigned long long*>(v.out + 4);
   return MHD_OK;
 }
 
-template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, const double* gUp, double* gU) {
+// cfl: dt is the CFL dt of U^n (Step 1) and its reverse is added: the
+// update reverses also produce the dt cotangent, and cfl_term adds
+// g_dt d dt/dU^n.  dt_host/gdt_host (may be null) receive dt and g_dt.
+template <class T>
+int adjoint_step(mhd_ctx* c, const double* Un, double dt, const double* gUp, double* gU, bool cfl = false,
+                 double* dt_host = nullptr, double* gdt_host = nullptr) {
   AdjView<T> b;
   int st = adj_view<T>(c, b);
   if (st != MHD_OK) return st;
@@ -398,6 +415,23 @@ template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, con
   const long long N = g.N;
   double* U = const_cast<double*>(Un);  // read only: k_prim writes U only with floors on
   const int rc = c->cfg.recon;
+  if (cfl) {
+    // Step 1's reduction, read back for the host-side dt of the recompute
+    cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
+    Launch<T>::prim(g, U, b.Wn, c->dtbits, c->flags, nullptr, s);
+    unsigned long long bits = 0;
+    unsigned fl = 0;
+    if (cudaMemcpyAsync(&bits, c->dtbits, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+    if (fl & 1u) return MHD_ERR_NONFINITE;
+    double r;
+    std::memcpy(&r, &bits, sizeof(r));
+    dt = g.cfl / r;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
+  }
+  double* part0 = cfl ? b.part : nullptr;
+  double* part1 = cfl ? b.part + b.nparts : nullptr;
   // forward recompute (Steps 1-8)
   Launch<T>::prim(g, U, b.Wn, nullptr, c->flags, nullptr, s);
   for (int a = 0; a < 3; ++a) Launch<T>::flux_pcm(g, a, b.Wn, U, b.Fn, s);
@@ -410,7 +444,7 @@ template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, con
   Launch<T>::emf(g, b.Wh, b.Fh, b.Eh, s);
   // reverse: Step 9 (floors, full update)
   mhd::AdjLaunch<T>::floors(g, U, b.Fh, b.Eh, dt, gUp, gU, b.gBccF, s);
-  mhd::AdjLaunch<T>::update(g, 0, dt, gU, gUp + 5 * N, b.gBccF, nullptr, gU, b.gF, b.gE, s);
+  mhd::AdjLaunch<T>::update(g, 0, dt, gU, gUp + 5 * N, b.gBccF, nullptr, gU, b.gF, b.gE, s, b.Fh, b.Eh, part0);
   // Step 8 (edge fields, half-step reference fields)
   mhd::AdjLaunch<T>::emf(g, b.Wh, b.Fh, b.gE, b.gF, b.gW, s);
   // Steps 7-6 per axis (HLLD, reconstruction)
@@ -421,7 +455,9 @@ template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, con
   }
   // Step 5 (primitives of the half state, half update)
   mhd::AdjLaunch<T>::prim(g, true, U, b.Uh, b.Bh, b.gW, b.g5, b.gBcc, s);
-  mhd::AdjLaunch<T>::update(g, 1, 0.5 * dt, b.g5, nullptr, b.gBcc, b.gBf, gU, b.gF, b.gE, s);
+  // (the predictor edge fields, overwritten by Step 8's, again for the dt cotangent)
+  if (cfl) Launch<T>::emf(g, b.Wn, b.Fn, b.Eh, s);
+  mhd::AdjLaunch<T>::update(g, 1, 0.5 * dt, b.g5, nullptr, b.gBcc, b.gBf, gU, b.gF, b.gE, s, b.Fn, b.Eh, part1);
   // Step 4 (edge fields, reference fields of W^n)
   mhd::AdjLaunch<T>::emf(g, b.Wn, b.Fn, b.gE, b.gF, b.gW, s);
   // Steps 3-2 (HLLD on PCM states)
@@ -432,6 +468,14 @@ template <class T> int adjoint_step(mhd_ctx* c, const double* Un, double dt, con
   // Step 1 (primitives of U^n) and the face cotangents
   mhd::AdjLaunch<T>::prim(g, false, U, nullptr, nullptr, b.gW, b.g5, b.gBcc, s);
   mhd::AdjLaunch<T>::faces_n(g, b.g5, b.gBcc, b.gBf, gU, s);
+  if (!cfl) return cuda_status();
+  mhd::AdjLaunch<T>::cfl_term(g, U, b.Wn, c->dtbits, b.part, b.nparts, b.idx, gU, b.out, s);
+  double o[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(o, b.out, sizeof(o), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (dt_host) *dt_host = o[1];
+  if (gdt_host) *gdt_host = o[0];
+  if (!(o[2] >= 0.0)) return MHD_ERR_DT;  // no cell reached the maximum
   return cuda_status();
 }
 
@@ -724,6 +768,16 @@ int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_
   if (c->Up) return MHD_ERR_ARG;  // periodic grids only
   if (!(dt > 0.0) || !std::isfinite(dt)) return MHD_ERR_DT;
   return with_adj_type(c->cfg.precision, [&](auto t) { return adjoint_step<MHD_T>(c, U_n, dt, gU_np1, gU_n); });
+}
+
+int mhd_adjoint_step_cfl(mhd_ctx* c, const double* U_n, const double* gU_np1, double* gU_n, double* dt_host,
+                         double* g_dt_host) {
+  if (!c || !U_n || !gU_np1 || !gU_n || gU_np1 == gU_n) return MHD_ERR_ARG;
+  if (c->cfg.recon == MHD_RECON_PLM_PRIM) return MHD_ERR_ARG;
+  if (c->Up) return MHD_ERR_ARG;
+  return with_adj_type(c->cfg.precision, [&](auto t) {
+    return adjoint_step<MHD_T>(c, U_n, 0.0, gU_np1, gU_n, true, dt_host, g_dt_host);
+  });
 }
 
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes) {

@@ -21,8 +21,6 @@
 
 namespace mhd {
 
-constexpr int BX = 32, BY = 4;
-
 struct CellIdx {
   int i, j, k;
   bool ok;

@@ -7,6 +7,12 @@ namespace mhd {
 
 struct df;  // double-float number (mhd_df.cuh)
 
+// thread block of the per-cell kernels: BX x BY cells of one z plane
+constexpr int BX = 32, BY = 4;
+inline long long cell_blocks(int nx, int ny, int nz) {
+  return (long long)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
+}
+
 struct Grid {
   int n[3];          // nx, ny, nz
   long long N;       // nx * ny * nz
@@ -42,8 +48,16 @@ template <class T> struct Launch {
 template <class T> struct AdjLaunch {
   static void floors(const Grid& g, const double* U, const T* F, const T* E, double dt, const double* gUp, double* gU,
                      T* gBccF, cudaStream_t s);
+  // part != nullptr: also the block partials of the step-size cotangent
+  // (fluxes Fs and edge fields Es of the update being reversed)
   static void update(const Grid& g, int mode, double h, const double* g5src, const double* gUpF, const T* gBcc,
-                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s);
+                     const T* gBfx, double* gU, T* gF, T* gE, cudaStream_t s, const T* Fs = nullptr,
+                     const T* Es = nullptr, double* part = nullptr);
+  // reverse of dt = C_CFL / r_max: argmax cell of the rate, g_dt from the
+  // partials of both update reverses (nparts per mode), g_dt d dt/dU into gU;
+  // out = {g_dt, dt, cell}
+  static void cfl_term(const Grid& g, const double* U, const T* W, const unsigned long long* rbits, const double* part,
+                       long long nparts, unsigned long long* idx, double* gU, double* out, cudaStream_t s);
   static void emf(const Grid& g, const T* W, const T* F, const T* gE, T* gF, T* gW, cudaStream_t s);
   static void hlld(const Grid& g, int a, bool pcm, const T* WL, const T* WR, const T* Wn, const double* U, const T* Bh,
                    const T* gF, T* gWL, T* gWR, T* gBf, cudaStream_t s);

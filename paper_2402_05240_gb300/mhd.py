@@ -58,6 +58,7 @@ def _load_library():
         "mhd_step_sub": (ip, [vp, vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.c_double, vp]),
         "mhd_dt_sub": (ip, [vp, vp, ctypes.POINTER(ip), ctypes.POINTER(ip), dp]),
         "mhd_adjoint_step": (ip, [vp, vp, ctypes.c_double, vp, vp]),
+        "mhd_adjoint_step_cfl": (ip, [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "mhd_diagnostics": (ip, [vp, vp, dp, dp]),
         "mhd_status": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
         "mhd_strerror": (ctypes.c_char_p, [ip]),
@@ -178,6 +179,14 @@ def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:
 
 def mhd_adjoint_step(ctx, U_n: torch.Tensor, dt: float, gU_np1: torch.Tensor, gU_n: torch.Tensor):
     _check(LIB.mhd_adjoint_step(ctx, _ptr(U_n), float(dt), _ptr(gU_np1), _ptr(gU_n)), "mhd_adjoint_step")
+
+
+def mhd_adjoint_step_cfl(ctx, U_n: torch.Tensor, gU_np1: torch.Tensor, gU_n: torch.Tensor):
+    """Returns (dt, g_dt)."""
+    dt, gdt = ctypes.c_double(0), ctypes.c_double(0)
+    _check(LIB.mhd_adjoint_step_cfl(ctx, _ptr(U_n), _ptr(gU_np1), _ptr(gU_n), ctypes.byref(dt), ctypes.byref(gdt)),
+           "mhd_adjoint_step_cfl")
+    return dt.value, gdt.value
 
 
 def mhd_diagnostics(ctx, U: torch.Tensor):
@@ -327,6 +336,13 @@ class Sim:
         gU = torch.empty_like(gU_np1)
         mhd_adjoint_step(self.ctx, U_n, dt, gU_np1.contiguous(), gU)
         return gU
+
+    def adjoint_step_cfl(self, U_n, gU_np1):
+        """(gU_n, dt, g_dt) for one step at the CFL dt of U_n, the dt's own
+        dependence on U_n included."""
+        gU = torch.empty_like(gU_np1)
+        dt, gdt = mhd_adjoint_step_cfl(self.ctx, U_n, gU_np1.contiguous(), gU)
+        return gU, dt, gdt
 
     def recon_vjp(self, U, axis, gWL, gWR, recon=None):
         r = self.cfg.recon if recon is None else (RECON[recon] if isinstance(recon, str) else recon)

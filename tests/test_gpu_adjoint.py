@@ -187,3 +187,50 @@ def test_adjoint_finite_on_quiet_regions(mhd, precision, recon):
     dt = sim.dt(U0)
     gU = sim.adjoint_step(U0, dt, torch.ones_like(U0))
     assert bool(torch.isfinite(gU).all())
+
+
+@pytest.mark.parametrize("recon,precision,tol", [("plmc", "fp64", 1e-10), ("ppmc", "fp64", 1e-10),
+                                                 ("pcm", "fp64", 1e-10), ("plmc", "fp64_df", 1e-10),
+                                                 ("ppmc", "fp32_bulk", 1e-3)])
+def test_adjoint_step_cfl_dot_product(mhd, recon, precision, tol):
+    """The step at the CFL dt of its own start state: <J dU, g> from the
+    oracle's dual numbers (the dt's derivative included) equals <dU, J^T g>
+    from mhd_adjoint_step_cfl; the fixed-dt adjoint misses the dt term by far
+    more than the FP64 tolerance; dt is mhd_dt's and g_dt = <g, dstep/d dt>
+    matches a central difference of the oracle in dt."""
+    n = (26, 18, 14)
+    U = generic(n, 43)
+    orc = O.Oracle(*n, recon=recon)
+    rng = np.random.default_rng(15)
+    dU = rng.normal(size=U.shape)
+    g = rng.normal(size=U.shape)
+    _, JdU, dt_o = orc.step_cfl_jvp(U, dU, 0.3)
+    sim = mhd.Sim(*n, cfl=0.3, recon=recon, precision=precision)
+    gU, dt, gdt = sim.adjoint_step_cfl(cuda(U), cuda(g))
+    gU = gU.cpu().numpy()
+    assert dt == sim.dt(cuda(U))
+    assert abs(dt - dt_o) <= (1e-14 if precision != "fp32_bulk" else 1e-6) * dt
+    lhs = float(np.sum(JdU * g))
+    rhs = float(np.sum(dU * gU))
+    scale = float(np.sum(np.abs(JdU * g)))
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs, abs(lhs - rhs) / scale)
+    gU0 = sim.adjoint_step(cuda(U), dt, cuda(g)).cpu().numpy()
+    # the dt term is about 2e-4 of the scale here: resolved at the FP64 tolerance
+    assert abs(float(np.sum(dU * gU0)) - lhs) > (100 * tol * scale if tol < 1e-6 else 0.0)
+    if precision == "fp64":
+        delta = 1e-6
+        Sp = orc.step(U, dt * (1 + delta))
+        Sm = orc.step(U, dt * (1 - delta))
+        fd = float(np.sum(g * (Sp - Sm))) / (2 * delta * dt)
+        # (smooth rho and P: no limiter switch within dt (1 +- 1e-6))
+        assert abs(gdt - fd) <= 1e-6 * abs(fd), (gdt, fd)
+
+
+def test_adjoint_step_cfl_deterministic(mhd):
+    n = (40, 24, 20)
+    U = cuda(turb(n, 44))
+    g = cuda(np.random.default_rng(3).normal(size=(8, n[2], n[1], n[0])))
+    sim = mhd.Sim(*n, cfl=0.3, recon="ppmc")
+    a = sim.adjoint_step_cfl(U, g)
+    b = sim.adjoint_step_cfl(U, g)
+    assert torch.equal(a[0], b[0]) and a[1:] == b[1:]

@@ -123,6 +123,68 @@ def test_rollout_gradient_vs_finite_differences(mods, recon, state, eps):
     assert worst <= 1e-4, worst
 
 
+def test_rollout_dt_grad_dot_product_and_finite_differences(mods):
+    """rollout(dt_grad=True): each step's CFL dt is differentiated through its
+    start state.  (1) Dot test of the 3-step gradient against the oracle's
+    dual-number chain of CFL-coupled steps (1e-10); the fixed-dt gradient
+    misses it.  (2) Central differences of the loss whose every run takes its
+    own CFL dts, along 8 random directions (redrawn where the quotients at
+    eps and 2 eps disagree)."""
+    import oracle as O
+    mhd, A = mods
+    n = (20, 16, 12)
+    nsteps = 3
+    rho, vel, pres, bf = setup_generic(n)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    sim = mhd.Sim(*n, cfl=0.3, recon="plmc")
+    U0 = A.conserved_from(t(rho), t(vel), t(pres), t(bf), G).cpu().numpy()
+    rng = np.random.default_rng(21)
+    gN = rng.normal(size=U0.shape)
+    grads = {}
+    for dt_grad in (True, False):
+        U = t(U0).requires_grad_(True)
+        L = torch.sum(A.rollout(sim, U, nsteps, checkpoint_every=2, dt_grad=dt_grad) * t(gN))
+        L.backward()
+        grads[dt_grad] = U.grad.cpu().numpy()
+    orc = O.Oracle(*n, recon="plmc")
+    v = rng.normal(size=U0.shape)
+    V, dV = U0.copy(), v.copy()
+    for _ in range(nsteps):
+        V, dV, _ = orc.step_cfl_jvp(V, dV, 0.3)
+    lhs = float(np.sum(gN * dV))
+    scale = float(np.sum(np.abs(gN * dV)))
+    assert abs(lhs - float(np.sum(v * grads[True]))) <= 1e-10 * scale
+    assert abs(lhs - float(np.sum(v * grads[False]))) > 1e-8 * scale
+
+    vv = t(vel).requires_grad_(True)
+    b = t(bf).requires_grad_(True)
+    U = A.conserved_from(t(rho), vv, t(pres), b, G)
+    L = A.magnetic_energy(A.rollout(sim, U, nsteps, checkpoint_every=2, dt_grad=True), 1.0 / (n[0] * n[1] * n[2]))
+    L.backward()
+    gv, gb = vv.grad.cpu().numpy(), b.grad.cpu().numpy()
+    ok, worst = 0, 0.0
+    for trial in range(8):
+        dv = rng.normal(size=vel.shape) if trial % 2 == 0 else np.zeros_like(vel)
+        db = np.zeros_like(bf) if trial % 2 == 0 else div_free_direction(n, rng)
+        if trial % 2 == 0:
+            dv /= np.max(np.abs(dv))
+        adj = float(np.sum(gv * dv) + np.sum(gb * db))
+
+        def fd(eps):
+            with torch.no_grad():
+                lp = loss_of(A, sim, n, t(rho), t(vel + eps * dv), t(pres), t(bf + eps * db), nsteps, None)
+                lm = loss_of(A, sim, n, t(rho), t(vel - eps * dv), t(pres), t(bf - eps * db), nsteps, None)
+            return (float(lp) - float(lm)) / (2 * eps)
+
+        f1, f2 = fd(1e-7), fd(2e-7)
+        if abs(f1 - f2) > 3e-5 * max(abs(f1), 1e-12):
+            continue
+        ok += 1
+        worst = max(worst, abs(f1 - adj) / max(abs(f1), 1e-12))
+    assert ok >= 5, ok
+    assert worst <= 1e-4, worst
+
+
 def test_checkpointing_does_not_change_the_gradient(mods):
     mhd, A = mods
     n = (16, 12, 10)

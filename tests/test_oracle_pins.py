@@ -486,3 +486,71 @@ def test_jvp_matches_central_difference(recon):
     fd = (orc.step(U + eps * d, dt) - orc.step(U - eps * d, dt)) / (2 * eps)
     err = np.max(np.abs(fd - JV)) / np.max(np.abs(JV))
     assert err < 1e-6
+
+
+def _cfl_argmin(U, orc, d):
+    """(cell, axis) of the smallest d_l / (|v_l| + c_f,l), from the oracle's
+    primitives and the textbook fast speed written out here."""
+    W = orc.primitives(U)
+    rho, v, p, b = W[0], W[1:4], W[4], W[5:8]
+    best, arg = np.inf, None
+    for l in range(3):
+        a2 = G * p / rho
+        b2 = (b[0] ** 2 + b[1] ** 2 + b[2] ** 2) / rho
+        cf = np.sqrt(0.5 * (a2 + b2 + np.sqrt((a2 + b2) ** 2 - 4 * a2 * b[l] ** 2 / rho)))
+        t = d[l] / (np.abs(v[l]) + cf)
+        c = int(np.argmin(t))
+        if t.flat[c] < best:
+            best, arg = t.flat[c], (c, l)
+    return arg
+
+
+def test_dt_jvp_matches_central_difference_and_is_local():
+    """d dt along dU: equals a central difference of Eq. dt; is zero for a
+    direction that leaves the minimising cell (and its lower faces) alone."""
+    n = 8
+    U = I.turbulent_box(I.Box(n, n, n), seed_v=41, seed_b=42, kmax=2)
+    orc = O.Oracle(n, n, n)
+    rng = np.random.default_rng(12)
+    d = rng.normal(size=U.shape)
+    dt, ddt = orc.dt_jvp(U, d, 0.3)
+    assert dt == orc.dt(U, 0.3)
+    eps = 1e-7
+    fd = (orc.dt(U + eps * d, 0.3) - orc.dt(U - eps * d, 0.3)) / (2 * eps)
+    assert abs(fd - ddt) <= 1e-6 * abs(ddt), (fd, ddt)
+    c, _ = _cfl_argmin(U, orc, (1.0 / n,) * 3)
+    k, j, i = np.unravel_index(c, U.shape[1:])
+    away = d.copy()
+    away[:, k, j, i] = 0.0
+    away[5, k, j, (i - 1) % n] = 0.0
+    away[6, k, (j - 1) % n, i] = 0.0
+    away[7, (k - 1) % n, j, i] = 0.0
+    assert orc.dt_jvp(U, away, 0.3)[1] == 0.0
+    at = d - away
+    _, ddt_at = orc.dt_jvp(U, at, 0.3)
+    assert abs(ddt_at - ddt) <= 1e-12 * abs(ddt)
+
+
+def test_step_cfl_jvp_matches_central_difference():
+    """The derivative of U -> step(U, dt(U)) (dt the CFL dt of U) equals a
+    central difference of the oracle's own CFL-stepped run, and differs from
+    the fixed-dt derivative by the dt term (which this direction excites)."""
+    n = 8
+    U = I.turbulent_box(I.Box(n, n, n), seed_v=31, seed_b=32, kmax=2)
+    orc = O.Oracle(n, n, n, recon="plmc")
+    rng = np.random.default_rng(8)
+    d = rng.normal(size=U.shape)
+    d[5:] = 0  # hydro directions keep div B = 0
+    V, JV, dt = orc.step_cfl_jvp(U, d, 0.3)
+    assert dt == orc.dt(U, 0.3)
+    assert np.array_equal(V, orc.step(U, dt))
+
+    def run1(X):
+        return orc.step(X, orc.dt(X, 0.3))
+
+    eps = 1e-8
+    fd = (run1(U + eps * d) - run1(U - eps * d)) / (2 * eps)
+    scale = np.max(np.abs(JV))
+    assert np.max(np.abs(fd - JV)) / scale < 1e-6
+    _, J0 = orc.step_jvp(U, d, dt)
+    assert np.max(np.abs(JV - J0)) / scale > 1e-3
