@@ -251,23 +251,22 @@ __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const
 template <class T>
 __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* w0, const T* wp, T bn,
                          const T* gwl_in, const T* gwr_in, T* gwm, T* gw0, T* gwp, T& gbn) {
-  T dL[7], dR[7], dC[7], dG[7];
+  T dL[7], dR[7], dG[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     dL[q] = w0[q] - wm[q];
     dR[q] = wp[q] - w0[q];
-    dC[q] = T(0.5) * (wp[q] - wm[q]);
-    const T pr = dL[q] * dR[q];
-    dG[q] = pr > T(0) ? T(2) * pr * trcp<T>(dL[q] + dR[q]) : T(0);
   }
+  van_leer7<T>(dL, dR, dG);  // the forward's arithmetic (plmc)
   Eig<T> E;
   eig_build<T>(gamma, w0, bn, E);
   const T ir = E.ir;
   T aL[7], aR[7], aC[7], aG[7], am[7], dW[7];
   eig_left<T>(E, dL, aL);
   eig_left<T>(E, dR, aR);
-  eig_left<T>(E, dC, aC);
   eig_left<T>(E, dG, aG);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) aC[q] = T(0.5) * (aL[q] + aR[q]);
   int sel[7];  // -1: zero slope; 0..3: candidate 2|aL|, 2|aR|, |aC|, |aG|
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -318,12 +317,16 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
       if (sel[q] == 3) gaG[q] = s * sgn0<T>(aG[q]);
     }
   }
-  T gdL[7], gdR[7], gdC[7], gdG[7];
+  T gdL[7], gdR[7], gdG[7];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) gdL[q] = gdR[q] = gdC[q] = gdG[q] = T(0);
+  for (int q = 0; q < 7; ++q) {
+    gdL[q] = gdR[q] = gdG[q] = T(0);
+    // aC = (aL + aR)/2
+    gaL[q] += T(0.5) * gaC[q];
+    gaR[q] += T(0.5) * gaC[q];
+  }
   eig_left_vjp<T>(E, ir, dL, gaL, gdL, gE);
   eig_left_vjp<T>(E, ir, dR, gaR, gdR, gE);
-  eig_left_vjp<T>(E, ir, dC, gaC, gdC, gE);
   eig_left_vjp<T>(E, ir, dG, gaG, gdG, gE);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -336,8 +339,8 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
       gdL[q] += gdG[q] * T(2) * rR * rR;
       gdR[q] += gdG[q] * T(2) * rL * rL;
     }
-    gwp[q] += T(0.5) * gdC[q] + gdR[q];
-    gwm[q] += -T(0.5) * gdC[q] - gdL[q];
+    gwp[q] += gdR[q];
+    gwm[q] += -gdL[q];
     gw0[q] += gdL[q] - gdR[q];
   }
   eig_fields_vjp<T>(gamma, w0, bn, gE, gw0, gbn);

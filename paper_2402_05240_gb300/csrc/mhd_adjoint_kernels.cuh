@@ -620,7 +620,7 @@ __global__ void k_hlld_vjp_batch(int n, double gamma, const double* __restrict__
   }
   T gn = T(0);
   hlld_vjp<T>(T(gamma), a, b, T(bn[t]), g, ga, gb, gn);
-  hlld<T>(T(gamma), a, b, T(bn[t]), ff);
+  hlld<T>(T(gamma), T(1.0 / (gamma - 1.0)), a, b, T(bn[t]), ff);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     gwl[7 * t + q] = to_d<T>(ga[q]);

@@ -86,24 +86,27 @@ struct PrimD {
 // b2 = |B|^2 / rho, bt2 = |B_t|^2 / rho: the printed discriminant
 // (gamma P + B^2)^2 - 4 gamma P B_l^2 (over rho^2) as a sum of non-negative terms.
 template <class T>
-__device__ __forceinline__ T fast_speed(T gamma, T rho, T p, T bl, T bt1, T bt2) {
+__device__ __forceinline__ T fast_speed_sq(T gamma, T rho, T p, T bl, T bt1, T bt2) {
   T ir = trcp<T>(rho);
   T a2 = gamma * p * ir;
   T t2 = (bt1 * bt1 + bt2 * bt2) * ir;
   T b2 = bl * bl * ir + t2;
   T dd = a2 - b2;
-  return tsqrt<T>(T(0.5) * (a2 + b2 + tsqrt<T>(dd * dd + T(4) * a2 * t2)));
+  return T(0.5) * (a2 + b2 + tsqrt<T>(dd * dd + T(4) * a2 * t2));
+}
+template <class T>
+__device__ __forceinline__ T fast_speed(T gamma, T rho, T p, T bl, T bt1, T bt2) {
+  return tsqrt<T>(fast_speed_sq<T>(gamma, rho, p, bl, bt1, bt2));
 }
 
 // ------------------------------------------------------------------- HLLD --
 // Miyoshi & Kusano (2005) in the solver frame; w = (rho, u, v, w, P, By, Bz),
 // bn = longitudinal face field.  Outer speeds S_L = min(u) - max(c_f),
 // S_R = max(u) + max(c_f); degenerate star / double-star states below
-// Eps<T>::hlld * p_T*; flux selection with ties to the left.
+// Eps<T>::hlld * p_T*; flux selection with ties to the left.  gm1i = 1/(gamma - 1).
 template <class T>
-__device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T* f) {
+__device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, T bn, T* f) {
   const T bn2 = bn * bn;
-  const T gm1i = T(1) / (gamma - T(1));
   // left / right conserved energy, total pressure, physical flux
   T eL, eR, ptL, ptR;
   {
@@ -114,9 +117,9 @@ __device__ __forceinline__ void hlld(T gamma, const T* wl, const T* wr, T bn, T*
     eR = wr[4] * gm1i + T(0.5) * wr[0] * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) + T(0.5) * bb;
     ptR = wr[4] + T(0.5) * bb;
   }
-  const T cfL = fast_speed<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
-  const T cfR = fast_speed<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
-  const T cmax = fmax(cfL, cfR);
+  // max(c_f,L, c_f,R) as the root of the larger square (the root is monotone)
+  const T cmax = tsqrt<T>(fmax(fast_speed_sq<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
+                               fast_speed_sq<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6])));
   const T SL = fmin(wl[1], wr[1]) - cmax;
   const T SR = fmax(wl[1], wr[1]) + cmax;
 
@@ -363,23 +366,71 @@ template <> __device__ __forceinline__ double twice<double>(double v) {
 // ------------------------------------------------------- PLMC (Sec. 2.2.6) --
 // wm, w0, wp: primitive 7-vectors of cells i-1, i, i+1; bn: cell-centred
 // longitudinal field of cell i.  Outputs W_{L,i+1/2} and W_{R,i-1/2}.
+// van Leer differences dG = 2 dL dR / (dL + dR) where dL dR > 0, else 0
+// (reading D-5), for the 7 fields of one cell
+template <class T> __device__ __forceinline__ void van_leer7(const T* dL, const T* dR, T* dG) {
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    dG[q] = pos_prod<T>(dL[q], dR[q]) ? T(2) * (dL[q] * dR[q]) * trcp<T>(dL[q] + dR[q]) : T(0);
+}
+// Double: the seven reciprocals from one (Montgomery's simultaneous
+// inversion: prefix products, one reciprocal, back-substitution), when every
+// denominator lies in [2^-140, 2^140] so that no partial product leaves the
+// normal range; otherwise one reciprocal each.  The FP64 pipe bounds the
+// FP64 step and a reciprocal costs about 7 of its multiplies.
+template <> __device__ __forceinline__ void van_leer7<double>(const double* dL, const double* dR, double* dG) {
+  double s[7], p[7], inv[7];
+  bool act[7];
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    act[q] = pos_prod<double>(dL[q], dR[q]);
+    s[q] = act[q] ? dL[q] + dR[q] : 1.0;
+    const long long e = (dbits(s[q]) >> 52) & 0x7ff;
+    ok &= (e >= 1023 - 140) & (e <= 1023 + 140);
+  }
+  if (ok) {
+    p[0] = s[0];
+#pragma unroll
+    for (int q = 1; q < 7; ++q) p[q] = p[q - 1] * s[q];
+    double r = trcp<double>(p[6]);
+#pragma unroll
+    for (int q = 6; q > 0; --q) {
+      inv[q] = r * p[q - 1];
+      r = r * s[q];
+    }
+    inv[0] = r;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) inv[q] = trcp<double>(s[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    // (a product that underflows gives 0, also where 1/s would overflow)
+    const double pr = dL[q] * dR[q];
+    dG[q] = (act[q] && (dbits(pr) & kAbsBits) != 0) ? twice<double>(pr) * inv[q] : 0.0;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void plmc(T gamma, const T* wm, const T* w0, const T* wp, T bn, T* wl, T* wr) {
-  T dL[7], dR[7], dC[7], dG[7];
+  T dL[7], dR[7], dG[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     dL[q] = w0[q] - wm[q];
     dR[q] = wp[q] - w0[q];
-    dC[q] = T(0.5) * (wp[q] - wm[q]);
-    dG[q] = pos_prod<T>(dL[q], dR[q]) ? T(2) * (dL[q] * dR[q]) * trcp<T>(dL[q] + dR[q]) : T(0);
   }
+  van_leer7<T>(dL, dR, dG);
   Eig<T> E;
   eig_build<T>(gamma, w0, bn, E);
   T aL[7], aR[7], aC[7], aG[7], am[7], dW[7];
   eig_left<T>(E, dL, aL);
   eig_left<T>(E, dR, aR);
-  eig_left<T>(E, dC, aC);
   eig_left<T>(E, dG, aG);
+  // the centred difference (W_{i+1} - W_{i-1})/2 projected: L is linear, so
+  // its amplitudes are the mean of the left and right ones
+#pragma unroll
+  for (int q = 0; q < 7; ++q) aC[q] = T(0.5) * (aL[q] + aR[q]);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     if (pos_prod<T>(aL[q], aR[q])) {
@@ -435,7 +486,7 @@ template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
 // q[0..4] = characteristic deviations of cells i-2..i+2 from cell i (q[2] = 0);
 // returns the limited deviations of the two interface values.
 template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T& qp) {
-  const T c7 = T(7) / T(12), c1 = T(1) / T(12);
+  const T c7 = from_d<T>(7.0 / 12.0), c1 = from_d<T>(1.0 / 12.0), c6 = from_d<T>(1.0 / 6.0);
   qm = c7 * (q[1] + q[2]) - c1 * (q[0] + q[3]);
   qp = c7 * (q[2] + q[3]) - c1 * (q[1] + q[4]);
   const T d2m1 = q[0] - T(2) * q[1] + q[2];
@@ -443,16 +494,17 @@ template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T&
   const T d2p1 = q[2] - T(2) * q[3] + q[4];
   if (neg_prod<T>(qm - q[1], q[2] - qm)) {
     const T d2c = T(3) * (q[1] - T(2) * qm + q[2]);
-    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) / T(6);
+    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) * c6;
   }
   if (neg_prod<T>(qp - q[2], q[3] - qp)) {
     const T d2c = T(3) * (q[2] - T(2) * qp + q[3]);
-    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) / T(6);
+    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) * c6;
   }
   const T dqm = q[2] - qm, dqp = qp - q[2];
   if (!pos_prod<T>(dqm, dqp) || !pos_prod<T>(q[2] - q[1], q[3] - q[2])) {
     const T d2f = T(6) * (qm - T(2) * q[2] + qp);
     T r = T(0);
+    // (a true division: |d2lim4 / d2f| <= 1 even where d2f is too small to invert)
     if (d2f != T(0)) r = d2lim4<T>(d2f, d2m1, d20, d2p1) / d2f;
     qm = q[2] - r * dqm;
     qp = q[2] + r * dqp;

@@ -66,11 +66,18 @@ template <> __device__ __forceinline__ void block_max_to<df>(df v, unsigned long
 
 // inverse crossing time max over l of (|v_l| + c_f,l) / d_l of one cell; the
 // step is dt = C_CFL / (max over cells) (Eq. dt)
+// (c_f of Eq. c_f per axis, with 1/rho and a^2 = gamma P / rho shared by the three axes)
 template <class T> __device__ __forceinline__ T cell_inv_crossing(const Grid& g, const T* w8) {
+  const T ir = trcp<T>(w8[0]);
+  const T a2 = from_d<T>(g.gamma) * w8[4] * ir;
+  const T sq[3] = {w8[5] * w8[5], w8[6] * w8[6], w8[7] * w8[7]};
   T best = T(0);
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const T cf = fast_speed<T>(from_d<T>(g.gamma), w8[0], w8[4], w8[5 + l], w8[5 + (l + 1) % 3], w8[5 + (l + 2) % 3]);
+    const T t2 = (sq[(l + 1) % 3] + sq[(l + 2) % 3]) * ir;
+    const T b2 = sq[l] * ir + t2;
+    const T dd = a2 - b2;
+    const T cf = tsqrt<T>(T(0.5) * (a2 + b2 + tsqrt<T>(dd * dd + T(4) * a2 * t2)));
     best = fmax(best, (fabs(w8[1 + l]) + cf) * from_d<T>(g.id[l]));
   }
   return best;
@@ -181,7 +188,7 @@ __device__ __forceinline__ void pcm_face(const Grid& g, const T* __restrict__ W,
   T wl[7], wr[7], f[7];
   load_dir<A>(W, N, c, wl);
   load_dir<A>(W, N, cn, wr);
-  hlld<T>(from_d<T>(g.gamma), wl, wr, from_d<T>(U[(5 + A) * N + c]), f);
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, from_d<T>(U[(5 + A) * N + c]), f);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
     wl[q] = WL[q * N + c];
     wr[q] = WR[q * N + cn];
   }
-  hlld<T>(from_d<T>(g.gamma), wl, wr, Bf[A * N + c], f);
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, Bf[A * N + c], f);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
