@@ -107,16 +107,15 @@ __device__ __forceinline__ T fast_speed(T gamma, T rho, T p, T bl, T bt1, T bt2)
 template <class T>
 __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, T bn, T* f) {
   const T bn2 = bn * bn;
-  // left / right conserved energy, total pressure, physical flux
-  T eL, eR, ptL, ptR;
-  {
-    T bb = bn2 + wl[5] * wl[5] + wl[6] * wl[6];
-    eL = wl[4] * gm1i + T(0.5) * wl[0] * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]) + T(0.5) * bb;
-    ptL = wl[4] + T(0.5) * bb;
-    bb = bn2 + wr[5] * wr[5] + wr[6] * wr[6];
-    eR = wr[4] * gm1i + T(0.5) * wr[0] * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]) + T(0.5) * bb;
-    ptR = wr[4] + T(0.5) * bb;
-  }
+  // total pressures of both sides; the conserved energy is formed only for
+  // the side whose states the flux is taken from
+  const T bbL = bn2 + wl[5] * wl[5] + wl[6] * wl[6];
+  const T bbR = bn2 + wr[5] * wr[5] + wr[6] * wr[6];
+  const T ptL = wl[4] + T(0.5) * bbL;
+  const T ptR = wr[4] + T(0.5) * bbR;
+  auto energy = [&](const T* w, T bb) {
+    return w[4] * gm1i + T(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) + T(0.5) * bb;
+  };
   // max(c_f,L, c_f,R) as the root of the larger square (the root is monotone)
   const T cmax = tsqrt<T>(fmax(fast_speed_sq<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
                                fast_speed_sq<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6])));
@@ -134,11 +133,11 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     F[6] = w[6] * w[1] - bn * w[3];
   };
   if (SL >= T(0)) {
-    phys(wl, eL, ptL, f);
+    phys(wl, energy(wl, bbL), ptL, f);
     return;
   }
   if (SR <= T(0)) {
-    phys(wr, eR, ptR, f);
+    phys(wr, energy(wr, bbR), ptR, f);
     return;
   }
   const T dL = SL - wl[1], dR = SR - wr[1];
@@ -147,14 +146,15 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
   const T SM = (rdR * wr[1] - rdL * wl[1] - ptR + ptL) * iden;
   const T pts = (rdR * ptL - rdL * ptR + rdL * rdR * (wr[1] - wl[1])) * iden;
 
-  // single-star states of one side: returns rho*, v*, w*, By*, Bz*, E*
+  // single-star states of one side: rho*, v*, w*, By*, Bz* (both sides feed
+  // the double-star states)
   struct Star {
-    T r, v, w, by, bz, e, sq, rsq;
+    T r, v, w, by, bz, sq, rsq, iSM;
   };
-  auto star = [&](const T* w, T e, T pt, T S, T d, T rd) {
+  auto star = [&](const T* w, T S, T d, T rd) {
     Star s;
-    const T iSM = trcp<T>(S - SM);
-    s.r = rd * iSM;
+    s.iSM = trcp<T>(S - SM);
+    s.r = rd * s.iSM;
     const T D = rd * (S - SM) - bn2;
     if (fabs(D) < Eps<T>::hlld * pts) {
       s.v = w[2];
@@ -170,19 +170,29 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
       s.by = w[5] * q;
       s.bz = w[6] * q;
     }
-    const T vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
-    const T vbs = SM * bn + s.v * s.by + s.w * s.bz;
-    s.e = (d * e - pt * w[1] + pts * SM + bn * (vb - vbs)) * iSM;
     s.rsq = trsqrt<T>(s.r);
     s.sq = s.r * s.rsq;
     return s;
   };
-  const Star sL = star(wl, eL, ptL, SL, dL, rdL);
-  const Star sR = star(wr, eR, ptR, SR, dR, rdR);
+  const Star sL = star(wl, SL, dL, rdL);
+  const Star sR = star(wr, SR, dR, rdR);
+
+  // the region containing x/t = 0 lies on the side of S_M (ties to the left)
+  const bool left = SM >= T(0);
+  const T* w = left ? wl : wr;
+  const Star& s = left ? sL : sR;
+  const T S = left ? SL : SR;
+  const T d = left ? dL : dR;
+  const T pt = left ? ptL : ptR;
+  const T e = energy(w, left ? bbL : bbR);
+  // star energy E* of that side
+  const T vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
+  const T vbs = SM * bn + s.v * s.by + s.w * s.bz;
+  const T es = (d * e - pt * w[1] + pts * SM + bn * (vb - vbs)) * s.iSM;
 
   // double-star (rotational) states
   T SsL = SM, SsR = SM;
-  T vss, wss, byss, bzss, essL, essR;
+  T vss, wss, byss, bzss, ess;
   const bool dbl = !(T(0.5) * bn2 < Eps<T>::hlld * pts);
   if (dbl) {
     const T sg = bn > T(0) ? T(1) : T(-1);
@@ -195,24 +205,22 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     byss = (sL.sq * sR.by + sR.sq * sL.by + sL.sq * sR.sq * (sR.v - sL.v) * sg) * inv;
     bzss = (sL.sq * sR.bz + sR.sq * sL.bz + sL.sq * sR.sq * (sR.w - sL.w) * sg) * inv;
     const T vbss = SM * bn + vss * byss + wss * bzss;
-    essL = sL.e - sL.sq * (SM * bn + sL.v * sL.by + sL.w * sL.bz - vbss) * sg;
-    essR = sR.e + sR.sq * (SM * bn + sR.v * sR.by + sR.w * sR.bz - vbss) * sg;
+    // E** = E* -+ sqrt(rho*) (v*.B* - v**.B**) sgn(B_n), - on the left
+    if (left)
+      ess = es - s.sq * (SM * bn + s.v * s.by + s.w * s.bz - vbss) * sg;
+    else
+      ess = es + s.sq * (SM * bn + s.v * s.by + s.w * s.bz - vbss) * sg;
   }
-  // select the region containing x/t = 0
-  const bool left = SM >= T(0);
-  const T* w = left ? wl : wr;
-  const Star& s = left ? sL : sR;
-  const T S = left ? SL : SR;
   T F[7];
-  phys(w, left ? eL : eR, left ? ptL : ptR, F);
-  const T U0[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], left ? eL : eR, w[5], w[6]};
-  const T Us[7] = {s.r, s.r * SM, s.r * s.v, s.r * s.w, s.e, s.by, s.bz};
+  phys(w, e, pt, F);
+  const T U0[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], e, w[5], w[6]};
+  const T Us[7] = {s.r, s.r * SM, s.r * s.v, s.r * s.w, es, s.by, s.bz};
   // F* = F + S (U* - U)
   for (int q = 0; q < 7; ++q) f[q] = F[q] + S * (Us[q] - U0[q]);
   const T Ss = left ? SsL : SsR;
   const bool inner = left ? (SsL < T(0)) : (SsR >= T(0));
   if (dbl && inner) {
-    const T Uss[7] = {s.r, s.r * SM, s.r * vss, s.r * wss, left ? essL : essR, byss, bzss};
+    const T Uss[7] = {s.r, s.r * SM, s.r * vss, s.r * wss, ess, byss, bzss};
     for (int q = 0; q < 7; ++q) f[q] = f[q] + Ss * (Uss[q] - Us[q]);
   }
 }
