@@ -221,27 +221,131 @@ __device__ __forceinline__ void eig_right_vjp(const Eig<T>& E, const T* q, const
   gq[3] += gq3;
 }
 
-// Pushes the eigen-field cotangents back to (rho, P, B_t1, B_t2, B_n): five
-// forward-mode passes of the eigen-system build.
+// Pushes the eigen-field cotangents back to (rho, P, B_t1, B_t2, B_n): one
+// reverse sweep through the formulas of eig_build_dual (same branches, and
+// the same zero derivative where a root is zero or the field direction is
+// held fixed).
 template <class T>
 __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const EigG<T>& gE, T* gw0, T& gbn) {
-  const T x[5] = {w0[0], w0[4], w0[5], w0[6], bn};
-#pragma unroll 1
-  for (int k = 0; k < 5; ++k) {
-    EigD<T> D;
-    eig_build_dual<T>(gamma, Dl<T>(x[0], k == 0 ? T(1) : T(0)), Dl<T>(x[1], k == 1 ? T(1) : T(0)),
-                      Dl<T>(x[2], k == 2 ? T(1) : T(0)), Dl<T>(x[3], k == 3 ? T(1) : T(0)),
-                      Dl<T>(x[4], k == 4 ? T(1) : T(0)), D);
-    const T s = gE.rho * D.rho.d + gE.ir * D.ir.d + gE.sr * D.sr.d + gE.isr * D.isr.d + gE.a * D.a.d +
-                gE.a2 * D.a2.d + gE.ia2 * D.ia2.d + gE.af * D.af.d + gE.as * D.as.d + gE.cf * D.cf.d +
-                gE.cs * D.cs.d + gE.Qf * D.Qf.d + gE.Qs * D.Qs.d + gE.Af * D.Af.d + gE.As * D.As.d +
-                gE.b1 * D.b1.d + gE.b2 * D.b2.d;
-    if (k == 0) gw0[0] += s;
-    if (k == 1) gw0[4] += s;
-    if (k == 2) gw0[5] += s;
-    if (k == 3) gw0[6] += s;
-    if (k == 4) gbn += s;
+  const T rho = w0[0], p = w0[4], by = w0[5], bz = w0[6];
+  // forward values
+  const T ir = trcp<T>(rho);
+  const T a2 = gamma * p * ir;
+  const T ia2 = trcp<T>(a2);
+  const T ca2 = bn * bn * ir;
+  const T bt2r = by * by + bz * bz;
+  const T bt2 = bt2r * ir;
+  const T b2 = ca2 + bt2;
+  const T D = a2 - b2;
+  const T sd = tsqrt<T>(D * D + T(4) * a2 * bt2);
+  const T cf2 = T(0.5) * (a2 + b2 + sd);
+  const T icf2 = trcp<T>(cf2);
+  const T cs2 = a2 * ca2 * icf2;
+  const T cf = tsqrt<T>(cf2);
+  const T cs = tsqrt<T>(cs2);
+  const T sg = bn >= T(0) ? T(1) : T(-1);
+  const T sr = tsqrt<T>(rho);
+  const T isr = trcp<T>(sr);
+  const T a = tsqrt<T>(a2);
+  // magnetosonic normalisations: af = sqrt(uf), as = sqrt(us)
+  const int br = sd == T(0) ? 0 : (D >= T(0) ? 1 : 2);
+  T af = T(1), as = T(0), M = T(0), N = T(0), iM = T(0), r2s = T(0);
+  if (br != 0) {
+    N = T(2) * a2 * bt2;
+    M = br == 1 ? sd * (sd + D) : sd * (sd - D);
+    iM = trcp<T>(M);
+    r2s = trcp<T>(T(2) * sd);
+    const T big = (br == 1 ? sd + D : sd - D) * r2s;  // the root of the larger member
+    const T small = N * iM;
+    af = tsqrt<T>(br == 1 ? big : small);
+    as = tsqrt<T>(br == 1 ? small : big);
   }
+  const T bt = tsqrt<T>(bt2r);
+  const bool bfree = !(bt == T(0)) && !(bt2r < T(1e-12) * (bn * bn + gamma * p));
+
+  // reverse sweep
+  T g_rho = gE.rho, g_ir = gE.ir, g_sr = gE.sr, g_isr = gE.isr, g_a = gE.a, g_a2 = gE.a2, g_ia2 = gE.ia2;
+  T g_af = gE.af, g_as = gE.as, g_cf = gE.cf, g_cs = gE.cs;
+  T g_by = T(0), g_bz = T(0), g_bn = T(0), g_p = T(0);
+  // Qf = cf af sg, Qs = cs as sg, Af = a af sr, As = a as sr
+  g_cf += gE.Qf * af * sg;
+  g_af += gE.Qf * cf * sg;
+  g_cs += gE.Qs * as * sg;
+  g_as += gE.Qs * cs * sg;
+  g_a += gE.Af * af * sr + gE.As * as * sr;
+  g_af += gE.Af * a * sr;
+  g_as += gE.As * a * sr;
+  g_sr += gE.Af * a * af + gE.As * a * as;
+  // a = sqrt(a2), isr = 1/sr, sr = sqrt(rho)
+  if (a > T(0)) g_a2 += g_a * T(0.5) * trcp<T>(a);
+  g_sr += -g_isr * isr * isr;
+  if (sr > T(0)) g_rho += g_sr * T(0.5) * isr;
+  // b1 = by / bt, b2 = bz / bt, bt = sqrt(bt2r)
+  T g_bt2r = T(0);
+  if (bfree) {
+    const T ibt = trcp<T>(bt);
+    g_by += gE.b1 * ibt;
+    g_bz += gE.b2 * ibt;
+    const T g_bt = -(gE.b1 * by + gE.b2 * bz) * ibt * ibt;
+    g_bt2r += g_bt * T(0.5) * ibt;
+  }
+  // af, as
+  T g_sd = T(0), g_D = T(0), g_bt2 = T(0);
+  if (br != 0) {
+    // big = (sd +- D) / (2 sd), small = N / M
+    const T g_big = br == 1 ? (af > T(0) ? g_af * T(0.5) * trcp<T>(af) : T(0))
+                            : (as > T(0) ? g_as * T(0.5) * trcp<T>(as) : T(0));
+    const T g_small = br == 1 ? (as > T(0) ? g_as * T(0.5) * trcp<T>(as) : T(0))
+                              : (af > T(0) ? g_af * T(0.5) * trcp<T>(af) : T(0));
+    const T sD = br == 1 ? T(1) : T(-1);  // big = (sd + sD D) / (2 sd)
+    // d big / d sd = -sD D / (2 sd^2), d big / d D = sD / (2 sd)
+    g_sd += -g_big * sD * D * r2s * r2s * T(2);
+    g_D += g_big * sD * r2s;
+    const T g_N = g_small * iM;
+    const T g_M = -g_small * N * iM * iM;
+    g_a2 += g_N * T(2) * bt2;
+    g_bt2 += g_N * T(2) * a2;
+    // M = sd (sd + sD D)
+    g_sd += g_M * (T(2) * sd + sD * D);
+    g_D += g_M * sD * sd;
+  }
+  // cs = sqrt(cs2), cf = sqrt(cf2), cs2 = a2 ca2 / cf2, cf2 = (a2 + b2 + sd)/2
+  T g_cs2 = cs > T(0) ? g_cs * T(0.5) * trcp<T>(cs) : T(0);
+  T g_cf2 = cf > T(0) ? g_cf * T(0.5) * trcp<T>(cf) : T(0);
+  g_a2 += g_cs2 * ca2 * icf2;
+  T g_ca2 = g_cs2 * a2 * icf2;
+  g_cf2 += -g_cs2 * cs2 * icf2;
+  g_a2 += T(0.5) * g_cf2;
+  T g_b2 = T(0.5) * g_cf2;
+  g_sd += T(0.5) * g_cf2;
+  // sd = sqrt(D^2 + 4 a2 bt2)
+  if (sd > T(0)) {
+    const T g_X = g_sd * T(0.5) * trcp<T>(sd);
+    g_D += g_X * T(2) * D;
+    g_a2 += g_X * T(4) * bt2;
+    g_bt2 += g_X * T(4) * a2;
+  }
+  // D = a2 - b2, b2 = ca2 + bt2, bt2 = bt2r ir, bt2r = by^2 + bz^2, ca2 = bn^2 ir
+  g_a2 += g_D;
+  g_b2 += -g_D;
+  g_ca2 += g_b2;
+  g_bt2 += g_b2;
+  g_bt2r += g_bt2 * ir;
+  g_ir += g_bt2 * bt2r;
+  g_by += g_bt2r * T(2) * by;
+  g_bz += g_bt2r * T(2) * bz;
+  g_bn += g_ca2 * T(2) * bn * ir;
+  g_ir += g_ca2 * bn * bn;
+  // ia2 = 1/a2, a2 = gamma p ir, ir = 1/rho
+  g_a2 += -g_ia2 * ia2 * ia2;
+  g_p += g_a2 * gamma * ir;
+  g_ir += g_a2 * gamma * p;
+  g_rho += -g_ir * ir * ir;
+  gw0[0] += g_rho;
+  gw0[4] += g_p;
+  gw0[5] += g_by;
+  gw0[6] += g_bz;
+  gbn += g_bn;
 }
 
 
