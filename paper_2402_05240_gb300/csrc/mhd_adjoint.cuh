@@ -13,8 +13,8 @@
 namespace mhd {
 
 // ------------------------------------------------- forward-mode number --
-// value + one directional derivative; used for the small eigen-system
-// Jacobian (5 inputs) inside the PLMC / PPMC reverse sweep.
+// value + one directional derivative (the derivative of the CFL rate at one
+// cell in the reverse of the dt reduction).
 template <class T> struct Dl {
   T v, d;
   __device__ Dl() {}
@@ -34,63 +34,6 @@ template <class T> __device__ __forceinline__ Dl<T> operator/(Dl<T> a, Dl<T> b) 
 template <class T> __device__ __forceinline__ Dl<T> dsqrt(Dl<T> a) {
   const T s = tsqrt<T>(a.v);
   return Dl<T>(s, s > T(0) ? T(0.5) * a.d / s : T(0));
-}
-
-// Eigen-system fields as functions of (rho, P, B_t1, B_t2, B_n): the same
-// formulas as eig_build (mhd_device.cuh), on a generic number type.
-template <class T> struct EigD {
-  Dl<T> rho, ir, sr, isr, a, a2, ia2, af, as, cf, cs, Qf, Qs, Af, As, b1, b2;
-  T sg;
-};
-
-template <class T>
-__device__ __forceinline__ void eig_build_dual(T gamma, Dl<T> rho, Dl<T> p, Dl<T> by, Dl<T> bz, Dl<T> bn,
-                                               EigD<T>& E) {
-  E.rho = rho;
-  E.ir = Dl<T>(T(1)) / rho;
-  E.a2 = Dl<T>(gamma) * p * E.ir;
-  E.ia2 = Dl<T>(T(1)) / E.a2;
-  const Dl<T> ca2 = bn * bn * E.ir;
-  const Dl<T> bt2r = by * by + bz * bz;
-  const Dl<T> bt2 = bt2r * E.ir;
-  const Dl<T> b2 = ca2 + bt2;
-  const Dl<T> D = E.a2 - b2;
-  const Dl<T> sd = dsqrt(D * D + Dl<T>(T(4)) * E.a2 * bt2);
-  const Dl<T> cf2 = Dl<T>(T(0.5)) * (E.a2 + b2 + sd);
-  const Dl<T> cs2 = E.a2 * ca2 / cf2;
-  E.cf = dsqrt(cf2);
-  E.cs = dsqrt(cs2);
-  if (sd.v == T(0)) {
-    E.af = Dl<T>(T(1));
-    E.as = Dl<T>(T(0));
-  } else if (D.v >= T(0)) {
-    E.af = dsqrt((sd + D) / (Dl<T>(T(2)) * sd));
-    E.as = dsqrt(Dl<T>(T(2)) * E.a2 * bt2 / (sd * (sd + D)));
-  } else {
-    E.af = dsqrt(Dl<T>(T(2)) * E.a2 * bt2 / (sd * (sd - D)));
-    E.as = dsqrt((sd - D) / (Dl<T>(T(2)) * sd));
-  }
-  const Dl<T> bt = dsqrt(bt2r);
-  if (bt.v == T(0)) {
-    E.b1 = Dl<T>(T(0.70710678118654752440));
-    E.b2 = Dl<T>(T(0.70710678118654752440));
-  } else if (bt2r.v < T(1e-12) * (bn.v * bn.v + gamma * p.v)) {
-    // |B_t| below 1e-6 sqrt(B_n^2 + gamma P): the direction B_t/|B_t| is held
-    // fixed (its exact derivative grows like 1/|B_t| at the degeneracy)
-    E.b1 = Dl<T>(by.v / bt.v);
-    E.b2 = Dl<T>(bz.v / bt.v);
-  } else {
-    E.b1 = by / bt;
-    E.b2 = bz / bt;
-  }
-  E.sg = bn.v >= T(0) ? T(1) : T(-1);
-  E.sr = dsqrt(rho);
-  E.isr = Dl<T>(T(1)) / E.sr;
-  E.a = dsqrt(E.a2);
-  E.Qf = E.cf * E.af * Dl<T>(E.sg);
-  E.Qs = E.cs * E.as * Dl<T>(E.sg);
-  E.Af = E.a * E.af * E.sr;
-  E.As = E.a * E.as * E.sr;
 }
 
 // cotangents of the eigen-system fields used by eig_left / eig_right
@@ -222,9 +165,14 @@ __device__ __forceinline__ void eig_right_vjp(const Eig<T>& E, const T* q, const
 }
 
 // Pushes the eigen-field cotangents back to (rho, P, B_t1, B_t2, B_n): one
-// reverse sweep through the formulas of eig_build_dual (same branches, and
-// the same zero derivative where a root is zero or the field direction is
-// held fixed).
+// reverse sweep through the eigen-system formulas, written as plain roots
+// and quotients (the forward eig_build folds them into reciprocal roots):
+// ir = 1/rho, a2 = gamma P ir, ia2 = 1/a2, ca2 = B_n^2 ir, bt2 = |B_t|^2 ir,
+// D = a2 - ca2 - bt2, sd = sqrt(D^2 + 4 a2 bt2), c_f^2 = (a2 + ca2 + bt2 + sd)/2,
+// c_s^2 = a2 ca2 / c_f^2, the alpha pair sqrt((sd +- D)/(2 sd)) and
+// sqrt(2 a2 bt2 / (sd (sd +- D))), beta = B_t/|B_t|, sqrt(rho), 1/sqrt(rho),
+// a = sqrt(a2).  A root that is zero, and beta where |B_t|^2 < 1e-12 (B_n^2 +
+// gamma P) (reading D-23), carry no derivative.
 template <class T>
 __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const EigG<T>& gE, T* gw0, T& gbn) {
   const T rho = w0[0], p = w0[4], by = w0[5], bz = w0[6];
@@ -439,7 +387,8 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
       // d dG/d dL = 2 (dR/s)^2, d dG/d dR = 2 (dL/s)^2 with s = dL + dR; the
       // ratios are bounded by 1, so nothing under- or overflows when s is tiny
       const T s = dL[q] + dR[q];
-      const T rR = dR[q] / s, rL = dL[q] / s;
+      const T is = trcp<T>(s);  // (dL dR > 0 without underflow: s is far from 0)
+      const T rR = dR[q] * is, rL = dL[q] * is;
       gdL[q] += gdG[q] * T(2) * rR * rR;
       gdR[q] += gdG[q] * T(2) * rL * rL;
     }
@@ -476,7 +425,7 @@ template <class T> __device__ __forceinline__ int d2sel4(T x, T y, T z, T t) {
 }
 
 template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) {
-  const T c7 = T(7) / T(12), c1 = T(1) / T(12);
+  const T c7 = from_d<T>(7.0 / 12.0), c1 = from_d<T>(1.0 / 12.0), c6 = from_d<T>(1.0 / 6.0);
   // forward, recording the branches
   T qm = c7 * (q[1] + q[2]) - c1 * (q[0] + q[3]);
   T qp = c7 * (q[2] + q[3]) - c1 * (q[1] + q[4]);
@@ -488,13 +437,13 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
   if (limm) {
     const T d2c = T(3) * (q[1] - T(2) * qm + q[2]);
     sm_ = d2sel3<T>(d2c, d2m1, d20);
-    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) / T(6);
+    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) * c6;
   }
   const bool limp = (qp - q[2]) * (q[3] - qp) < T(0);
   if (limp) {
     const T d2c = T(3) * (q[2] - T(2) * qp + q[3]);
     sp_ = d2sel3<T>(d2c, d20, d2p1);
-    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) / T(6);
+    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) * c6;
   }
   const T dqm = q[2] - qm, dqp = qp - q[2];
   const bool ext = dqm * dqp <= T(0) || (q[2] - q[1]) * (q[3] - q[2]) <= T(0);
@@ -551,7 +500,7 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
     // qm = (q1 + q2)/2 - lim/6, lim in {d2c, C d2m1, C d20, 0}; d2c = 3 (q1 - 2 qm0 + q2)
     gq[1] += T(0.5) * g_qm;
     gq2 += T(0.5) * g_qm;
-    const T gl = -g_qm / T(6);
+    const T gl = -g_qm * c6;
     if (sm_ == 0) {
       gq[1] += T(3) * gl;
       gq2 += T(3) * gl;
@@ -574,7 +523,7 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
   if (limp) {
     gq2 += T(0.5) * g_qp;
     gq[3] += T(0.5) * g_qp;
-    const T gl = -g_qp / T(6);
+    const T gl = -g_qp * c6;
     if (sp_ == 0) {
       gq2 += T(3) * gl;
       gq[3] += T(3) * gl;
@@ -690,7 +639,7 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, const T (*w)[7], T bn,
 template <class T>
 __device__ __forceinline__ void fast_speed_vjp(T gamma, T rho, T p, T bl, T bt1, T bt2, T gcf, T& grho, T& gp, T& gbl,
                                                T& gbt1, T& gbt2) {
-  const T ir = T(1) / rho;
+  const T ir = trcp<T>(rho);
   const T a2 = gamma * p * ir;
   const T t2r = bt1 * bt1 + bt2 * bt2;
   const T t2 = t2r * ir;
@@ -700,12 +649,12 @@ __device__ __forceinline__ void fast_speed_vjp(T gamma, T rho, T p, T bl, T bt1,
   const T sX = tsqrt<T>(X);
   const T cf = tsqrt<T>(T(0.5) * (a2 + b2 + sX));
   if (!(cf > T(0))) return;
-  const T gcf2 = gcf * T(0.5) / cf;
+  const T gcf2 = gcf * T(0.5) * trcp<T>(cf);
   T ga2 = T(0.5) * gcf2, gb2 = T(0.5) * gcf2;
   const T gsX = T(0.5) * gcf2;
   T gt2 = T(0);
   if (sX > T(0)) {
-    const T gX = gsX * T(0.5) / sX;
+    const T gX = gsX * T(0.5) * trcp<T>(sX);
     const T gdd = gX * T(2) * dd;
     ga2 += gX * T(4) * t2 + gdd;
     gt2 += gX * T(4) * a2;
@@ -725,10 +674,10 @@ __device__ __forceinline__ void fast_speed_vjp(T gamma, T rho, T p, T bl, T bt1,
 // reverse of the physical flux F(w) and conserved vector U(w) of one side:
 // gF, gU cotangents; accumulates gw[7], gbn
 template <class T>
-__device__ __forceinline__ void phys_cons_vjp(T gamma, const T* w, T bn, const T* gF, const T* gU, T* gw, T& gbn) {
+__device__ __forceinline__ void phys_cons_vjp(T gm1i, const T* w, T bn, const T* gF, const T* gU, T* gw, T& gbn) {
   const T rho = w[0], u = w[1], v = w[2], ww = w[3], p = w[4], by = w[5], bz = w[6];
   const T bb = bn * bn + by * by + bz * bz;
-  const T e = p / (gamma - T(1)) + T(0.5) * rho * (u * u + v * v + ww * ww) + T(0.5) * bb;
+  const T e = p * gm1i + T(0.5) * rho * (u * u + v * v + ww * ww) + T(0.5) * bb;
   const T pt = p + T(0.5) * bb;
   const T mu = rho * u;
   const T vb = u * bn + v * by + ww * bz;
@@ -761,7 +710,7 @@ __device__ __forceinline__ void phys_cons_vjp(T gamma, const T* w, T bn, const T
   gby += gU[5];
   gbz += gU[6];
   // e, pt
-  T gp = ge / (gamma - T(1)) + gpt;
+  T gp = ge * gm1i + gpt;
   grho += ge * T(0.5) * (u * u + v * v + ww * ww);
   gu += ge * rho * u;
   gv += ge * rho * v;
@@ -785,7 +734,7 @@ __device__ __forceinline__ void phys_cons_vjp(T gamma, const T* w, T bn, const T
 template <class T>
 __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T* gwl, T* gwr, T& gbn) {
   const T bn2 = bn * bn;
-  const T gm1i = T(1) / (gamma - T(1));
+  const T gm1i = trcp<T>(gamma - T(1));
   T eL, eR, ptL, ptR;
   {
     T bb = bn2 + wl[5] * wl[5] + wl[6] * wl[6];
@@ -803,18 +752,18 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
   const T SR = fmax(wl[1], wr[1]) + cmax;
   const T zero7[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   if (SL >= T(0)) {
-    phys_cons_vjp<T>(gamma, wl, bn, gf, zero7, gwl, gbn);
+    phys_cons_vjp<T>(gm1i, wl, bn, gf, zero7, gwl, gbn);
     return;
   }
   if (SR <= T(0)) {
-    phys_cons_vjp<T>(gamma, wr, bn, gf, zero7, gwr, gbn);
+    phys_cons_vjp<T>(gm1i, wr, bn, gf, zero7, gwr, gbn);
     return;
   }
   const T uL = wl[1], uR = wr[1];
   const T dL = SL - uL, dR = SR - uR;
   const T rdL = wl[0] * dL, rdR = wr[0] * dR;
   const T den = rdR - rdL;
-  const T iden = T(1) / den;
+  const T iden = trcp<T>(den);
   const T numSM = rdR * uR - rdL * uL - ptR + ptL;
   const T SM = numSM * iden;
   const T numP = rdR * ptL - rdL * ptR + rdL * rdR * (uR - uL);
@@ -823,13 +772,13 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
   // star states of both sides (forward values)
   T Sv[2] = {SL, SR}, dv[2] = {dL, dR}, rdv[2] = {rdL, rdR}, ev[2] = {eL, eR}, ptv[2] = {ptL, ptR};
   const T* wv[2] = {wl, wr};
-  T rs[2], vs[2], ws[2], bys[2], bzs[2], es[2], sq[2], iSMv[2], Dv[2], iDv[2], tv[2], qv[2], vbv[2], vbsv[2];
+  T rs[2], vs[2], ws[2], bys[2], bzs[2], es[2], sq[2], rsq[2], iSMv[2], Dv[2], iDv[2], tv[2], qv[2], vbv[2], vbsv[2];
   bool degv[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const T* w = wv[s];
     const T Sd = Sv[s] - SM;
-    iSMv[s] = T(1) / Sd;
+    iSMv[s] = trcp<T>(Sd);
     rs[s] = rdv[s] * iSMv[s];
     Dv[s] = rdv[s] * Sd - bn2;
     degv[s] = fabs(Dv[s]) < Eps<T>::hlld * pts;
@@ -840,7 +789,7 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
       bzs[s] = w[6];
       iDv[s] = tv[s] = qv[s] = T(0);
     } else {
-      iDv[s] = T(1) / Dv[s];
+      iDv[s] = trcp<T>(Dv[s]);
       tv[s] = bn * (SM - w[1]) * iDv[s];
       vs[s] = w[2] - w[5] * tv[s];
       ws[s] = w[3] - w[6] * tv[s];
@@ -851,16 +800,18 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
     vbv[s] = w[1] * bn + w[2] * w[5] + w[3] * w[6];
     vbsv[s] = SM * bn + vs[s] * bys[s] + ws[s] * bzs[s];
     es[s] = (dv[s] * ev[s] - ptv[s] * w[1] + pts * SM + bn * (vbv[s] - vbsv[s])) * iSMv[s];
-    sq[s] = tsqrt<T>(rs[s]);
+    // sqrt(rho*) and its reciprocal as the forward solver forms them
+    rsq[s] = trsqrt<T>(rs[s]);
+    sq[s] = rs[s] * rsq[s];
   }
   const bool dbl = !(T(0.5) * bn2 < Eps<T>::hlld * pts);
   T SsL = SM, SsR = SM, vss = 0, wss = 0, byss = 0, bzss = 0, vbss = 0, ess[2] = {0, 0}, inv = 0, sg = 0, abn = 0;
   if (dbl) {
     sg = bn > T(0) ? T(1) : T(-1);
     abn = fabs(bn);
-    SsL = SM - abn / sq[0];
-    SsR = SM + abn / sq[1];
-    inv = T(1) / (sq[0] + sq[1]);
+    SsL = SM - abn * rsq[0];
+    SsR = SM + abn * rsq[1];
+    inv = trcp<T>(sq[0] + sq[1]);
     vss = (sq[0] * vs[0] + sq[1] * vs[1] + (bys[1] - bys[0]) * sg) * inv;
     wss = (sq[0] * ws[0] + sq[1] * ws[1] + (bzs[1] - bzs[0]) * sg) * inv;
     byss = (sq[0] * bys[1] + sq[1] * bys[0] + sq[0] * sq[1] * (vs[1] - vs[0]) * sg) * inv;
@@ -907,7 +858,7 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
     gsq[2] = {0, 0};
   T gvss = 0, gwss = 0, gbyss = 0, gbzss = 0, gvbss = 0, gess[2] = {0, 0}, ginv = 0;
   // physical flux and U0 of the selected side
-  phys_cons_vjp<T>(gamma, w, bn, gf, gU0, a == 0 ? gwl : gwr, gbn_loc);
+  phys_cons_vjp<T>(gm1i, w, bn, gf, gU0, a == 0 ? gwl : gwr, gbn_loc);
   // Uss
   if (inner) {
     grs[a] += gUss[0] + gUss[1] * SM + gUss[2] * vss + gUss[3] * wss;
@@ -933,12 +884,12 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
     if (inner) {
       if (left) {  // SsL = SM - abn/sqL
         gSM += gSs;
-        gsq[0] += gSs * abn / (sq[0] * sq[0]);
-        gbn_loc += -gSs * sg / sq[0];
+        gsq[0] += gSs * abn * rsq[0] * rsq[0];
+        gbn_loc += -gSs * sg * rsq[0];
       } else {  // SsR = SM + abn/sqR
         gSM += gSs;
-        gsq[1] += -gSs * abn / (sq[1] * sq[1]);
-        gbn_loc += gSs * sg / sq[1];
+        gsq[1] += -gSs * abn * rsq[1] * rsq[1];
+        gbn_loc += gSs * sg * rsq[1];
       }
     }
     // ess_L = es_L - sqL (vbs_L - vbss) sg ; ess_R = es_R + sqR (vbs_R - vbss) sg
@@ -1028,7 +979,7 @@ __device__ void hlld_vjp(T gamma, const T* wl, const T* wr, T bn, const T* gf, T
     const T* ws_in = wv[s];
     T* gw = s == 0 ? gwl : gwr;
     // sq = sqrt(rs)
-    if (sq[s] > T(0)) grs[s] += gsq[s] * T(0.5) / sq[s];
+    if (sq[s] > T(0)) grs[s] += gsq[s] * T(0.5) * rsq[s];
     // es = Ne iSM, Ne = d e - pt u + pts SM + bn (vb - vbs)
     const T Ne = dv[s] * ev[s] - ptv[s] * ws_in[1] + pts * SM + bn * (vbv[s] - vbsv[s]);
     const T gNe = ges[s] * iSMv[s];
