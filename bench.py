@@ -74,30 +74,30 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 COUNTERS = {
     "fp64": {
         "prim": (121.0, 171.0, 954 / 32, 105.1),
-        "flux_pcm": (276.9, 423.3, 1766 / 32, 100.9),
-        "emf": (96.0, 111.0, 1028 / 32, 139.8),
-        "update_half": (88.0, 126.0, 826 / 32, 282.8),
-        "recon": (341.2, 467.4, 2335 / 32, 150.3),
-        "flux_hlld": (275.8, 421.9, 1758 / 32, 162.2),
-        "update_full": (50.0, 71.0, 524 / 32, 260.6),
+        "flux_pcm": (236.5, 361.0, 1584 / 32, 100.9),
+        "emf": (96.0, 111.0, 1028 / 32, 139.5),
+        "update_half": (88.0, 126.0, 826 / 32, 282.9),
+        "recon": (295.9, 379.9, 2234 / 32, 150.2),
+        "flux_hlld": (235.6, 359.6, 1578 / 32, 162.1),
+        "update_full": (50.0, 71.0, 524 / 32, 260.8),
     },
     "fp32_bulk": {
-        "prim": (36.0, 52.0, 796 / 32, 81.4),
-        "flux_pcm": (0.0, 0.0, 572 / 32, 46.0),
+        "prim": (36.0, 52.0, 797 / 32, 81.4),
+        "flux_pcm": (0.0, 0.0, 554 / 32, 45.9),
         "emf": (0.0, 0.0, 570 / 32, 66.8),
         "update_half": (38.0, 55.0, 1591 / 32, 171.9),
-        "recon": (0.0, 0.0, 807 / 32, 62.9),
-        "flux_hlld": (0.0, 0.0, 545 / 32, 74.3),
+        "recon": (0.0, 0.0, 774 / 32, 62.7),
+        "flux_hlld": (0.0, 0.0, 530 / 32, 74.2),
         "update_full": (19.0, 22.0, 1433 / 32, 180.5),
     },
     "fp64_df": {
-        "prim": (37.0, 53.0, 1479 / 32, 105.2),
-        "flux_pcm": (0.0, 0.0, 3137 / 32, 101.1),
+        "prim": (37.0, 53.0, 1485 / 32, 105.1),
+        "flux_pcm": (0.0, 0.0, 3034 / 32, 101.1),
         "emf": (0.0, 0.0, 1515 / 32, 140.0),
-        "update_half": (49.0, 66.0, 2591 / 32, 282.4),
-        "recon": (0.0, 0.0, 4162 / 32, 150.8),
-        "flux_hlld": (0.0, 0.0, 3093 / 32, 162.4),
-        "update_full": (19.0, 22.0, 1520 / 32, 259.9),
+        "update_half": (49.0, 66.0, 2591 / 32, 282.5),
+        "recon": (0.0, 0.0, 3810 / 32, 150.7),
+        "flux_hlld": (0.0, 0.0, 3000 / 32, 162.5),
+        "update_full": (19.0, 22.0, 1520 / 32, 260.1),
     },
 }
 
