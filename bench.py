@@ -82,10 +82,8 @@ COUNTERS = {
         "update_full": (50.0, 71.0, 524 / 32, 260.8),
     },
     "fp32_bulk": {
-        "prim": (36.0, 52.0, 797 / 32, 81.4),
         "flux_pcm": (0.0, 0.0, 554 / 32, 45.9),
         "emf": (0.0, 0.0, 570 / 32, 66.8),
-        "update_half": (38.0, 55.0, 1591 / 32, 171.9),
         "recon": (0.0, 0.0, 774 / 32, 62.7),
         "flux_hlld": (0.0, 0.0, 530 / 32, 74.2),
         "update_full": (19.0, 22.0, 1433 / 32, 180.5),

@@ -121,6 +121,32 @@ __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long l
   for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
 }
 
+// FP32-bulk primitives of one cell: the gas-pressure recovery
+// P = max((gamma - 1)(E - |m|^2 / (2 rho') - |B_cc|^2 / 2), P_floor) in double,
+// the outputs that are stored as float (v = m / rho', B_cc) formed on the FP32
+// pipes from the rounded inputs.  bsum = twice the cell-centred field (sum of
+// the two face values).  Returns ke + me in double for the floor reset.
+__device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restrict__ W, long long c, double rho,
+                                                 double ir, double m0, double m1, double m2, double e,
+                                                 const double* bsum, float* w8) {
+  const double mm = m0 * m0 + m1 * m1 + m2 * m2;
+  const double bb = bsum[0] * bsum[0] + bsum[1] * bsum[1] + bsum[2] * bsum[2];
+  const double kem = 0.5 * (mm * ir + 0.25 * bb);  // ke + me
+  const double p = fmax(g.gm1 * (e - kem), g.p_floor);
+  const float irf = d2f_bits(ir);
+  w8[0] = d2f_bits(rho);
+  w8[1] = d2f_bits(m0) * irf;
+  w8[2] = d2f_bits(m1) * irf;
+  w8[3] = d2f_bits(m2) * irf;
+  w8[4] = d2f_bits(p);
+  w8[5] = 0.5f * d2f_bits(bsum[0]);
+  w8[6] = 0.5f * d2f_bits(bsum[1]);
+  w8[7] = 0.5f * d2f_bits(bsum[2]);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
+  return kem;
+}
+
 // ------------------------------------------------------------------ Step 1 --
 // Primitives W of a state, and optionally (floors != nullptr) the end-of-step
 // floors of the conserved state (D-12): rho < rho_floor is raised; if the
@@ -137,10 +163,6 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     const int i = ci.i, j = ci.j, k = ci.k;
     const long long c = cidx(g, i, j, k), N = g.N;
     const bool in = interior(g, i, j, k);
-    double b[3];
-    b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
-    b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
-    b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
     double r = U[c], e = U[4 * N + c];
     const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
     if ((!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) && in) atomicOr(flags, 1u);
@@ -151,19 +173,35 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     }
     const double rho = fmax(r, g.rho_floor);
     const double ir = __drcp_rn(rho);
-    if (floors) {
-      const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
-      const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-      if (g.gm1 * (e - ke - me) < g.p_floor) {
-        e = g.p_floor * g.igm1 + ke + me;
-        U[4 * N + c] = e;
+    T w8[8];
+    if constexpr (std::is_same<T, float>::value) {
+      const double bs[3] = {U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c],
+                            U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c],
+                            U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]};
+      const double kem = prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8);
+      if (floors && g.gm1 * (e - kem) < g.p_floor) {
+        U[4 * N + c] = g.p_floor * g.igm1 + kem;
         if (in) atomicAdd(&floors[1], 1ull);
       }
+      if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
+    } else {
+      double b[3];
+      b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
+      b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
+      b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
+      if (floors) {
+        const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
+        const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        if (g.gm1 * (e - ke - me) < g.p_floor) {
+          e = g.p_floor * g.igm1 + ke + me;
+          U[4 * N + c] = e;
+          if (in) atomicAdd(&floors[1], 1ull);
+        }
+      }
+      const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
+      store_w<T>(g, W, c, p, w8);
+      if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
     }
-    const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
-    T w8[8];
-    store_w<T>(g, W, c, p, w8);
-    if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
   }
   if (dtbits) block_max_to<T>(inv, dtbits);
 }
@@ -423,12 +461,18 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   Bh[c] = from_d<T>(bx);
   Bh[N + c] = from_d<T>(by);
   Bh[2 * N + c] = from_d<T>(bz);
-  const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   // (the outer ghost layers of a padded grid see the wrap and carry no check)
   if ((!(u5[0] > 0.0) || !isfinite(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);
-  const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
   T w8[8];
-  store_w<T>(g, W, c, p, w8);
+  if constexpr (std::is_same<T, float>::value) {
+    const double bs[3] = {bxm + bx, bym + by, bzm + bz};
+    const double rho = fmax(u5[0], g.rho_floor);
+    prim_store_f32(g, W, c, rho, __drcp_rn(rho), u5[1], u5[2], u5[3], u5[4], bs, w8);
+  } else {
+    const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
+    const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
+    store_w<T>(g, W, c, p, w8);
+  }
 }
 
 // Step 9: U^{n+1} in place.  Each thread reads and writes only its own cell of
