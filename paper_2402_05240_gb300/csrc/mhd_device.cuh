@@ -480,14 +480,15 @@ __device__ __forceinline__ void plm_prim(const T* wm, const T* w0, const T* wp, 
 // McCorquodale & Colella (2011) cell limiter (C = 1.25), in characteristic
 // deviations q_m - q_0 = L (W_m - W_0) of cell i.
 // sgn(x) min(|x|, C|y|, C|z|) when x, y, z share a strict sign, else 0 (C = 1.25)
+// (C min(|y|, |z|) is min(C|y|, C|z|) exactly: a rounded product is monotone)
 template <class T> __device__ __forceinline__ T d2lim3(T x, T y, T z) {
   if (pos_prod<T>(x, y) && pos_prod<T>(x, z))
-    return with_sign<T>(x, min_abs<T>(x, min_abs<T>(T(1.25) * y, T(1.25) * z)));
+    return with_sign<T>(x, min_abs<T>(x, T(1.25) * min_abs<T>(y, z)));
   return T(0);
 }
 template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
   if (pos_prod<T>(x, y) && pos_prod<T>(x, z) && pos_prod<T>(x, t))
-    return with_sign<T>(x, min_abs<T>(min_abs<T>(x, T(1.25) * y), min_abs<T>(T(1.25) * z, T(1.25) * t)));
+    return with_sign<T>(x, min_abs<T>(x, T(1.25) * min_abs<T>(y, min_abs<T>(z, t))));
   return T(0);
 }
 
