@@ -492,6 +492,13 @@ template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
   return T(0);
 }
 
+// a / b for |a| <= |b|, b != 0
+template <class T> __device__ __forceinline__ T ratio_le1(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ double ratio_le1<double>(double a, double b) {
+  // biased exponent >= 64: 1/b is finite and normal
+  return ((dbits(b) >> 52) & 0x7ff) >= 64 ? a * trcp<double>(b) : a / b;
+}
+
 // q[0..4] = characteristic deviations of cells i-2..i+2 from cell i (q[2] = 0);
 // returns the limited deviations of the two interface values.
 template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T& qp) {
@@ -513,8 +520,9 @@ template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T&
   if (!pos_prod<T>(dqm, dqp) || !pos_prod<T>(q[2] - q[1], q[3] - q[2])) {
     const T d2f = T(6) * (qm - T(2) * q[2] + qp);
     T r = T(0);
-    // (a true division: |d2lim4 / d2f| <= 1 even where d2f is too small to invert)
-    if (d2f != T(0)) r = d2lim4<T>(d2f, d2m1, d20, d2p1) / d2f;
+    // (|d2lim4 / d2f| <= 1: a reciprocal where d2f is far from the
+    // underflow range, else the division)
+    if (d2f != T(0)) r = ratio_le1<T>(d2lim4<T>(d2f, d2m1, d20, d2p1), d2f);
     qm = q[2] - r * dqm;
     qp = q[2] + r * dqp;
   } else {
