@@ -24,8 +24,6 @@ template <class T> struct AdjBufs {
   double* g5;  // [5][N]
 };
 
-__device__ __forceinline__ double upw_lo(double m) { return m > 0.0 ? 1.0 : (m < 0.0 ? 0.0 : 0.5); }
-
 // ------------------------------------------------- R1: floors of Step 9 --
 // Recomputes the pre-floor U^{n+1} of the cell; writes the pre-floor
 // cotangent of the hydro fields into gU and the floor's B_cc cotangent.
@@ -213,11 +211,16 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
 
 // ---------------------------------------------------- R3 / R8: edge EMF --
 // Gather-form reverse of Eq. emf-edge: writes gF[a][5], gF[a][6] and the
-// reference-field part of gW (v and B_cc components; rho, P zeroed).
+// reference-field part of gW (v and B_cc components; rho, P zeroed).  The
+// arithmetic is in the compute type (the cotangents are stored in it).
+template <class T> __device__ __forceinline__ T upw_lo_t(T m) {
+  return m > T(0) ? T(1) : (m < T(0) ? T(0) : T(0.5));
+}
+
 template <class T, int K>
 __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
                                              const T* __restrict__ gE, int i, int j, int k, T* __restrict__ gF,
-                                             double* gW8) {
+                                             T* gW8) {
   constexpr int B = (K + 1) % 3, C = (K + 2) % 3;
   const long long N = g.N;
   int q[3] = {i, j, k};
@@ -232,23 +235,24 @@ __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict_
   const T* Fb = F + (long long)B * 7 * N;  // mass flux of b-faces: Fb[x]
   const T* Fc = F + (long long)C * 7 * N;
   const T* gEk = gE + (long long)K * N;
-  const double g00 = to_d<T>(gEk[c00]), gmb = to_d<T>(gEk[cb]), gmc = to_d<T>(gEk[cc]), gmbc = to_d<T>(gEk[cbc]);
-  // mass fluxes: mc(q), mc(q + e_b), mc(q - e_c), mc(q - e_c + e_b); mb(q), mb(q + e_c), mb(q - e_b), mb(q - e_b + e_c)
-  const double mc0 = to_d<T>(Fc[c00]), mc_pb = to_d<T>(Fc[cpb]), mc_mc = to_d<T>(Fc[cc]), mc_mcpb = to_d<T>(Fc[cmcpb]);
-  const double mb0 = to_d<T>(Fb[c00]), mb_pc = to_d<T>(Fb[cpc]), mb_mb = to_d<T>(Fb[cb]), mb_mbpc = to_d<T>(Fb[cmbpc]);
-  const double gbf = 0.25 * g00 * (1.0 + upw_lo(mc_pb) + upw_lo(mc0)) +
-                     0.25 * gmc * (1.0 + (1.0 - upw_lo(mc_mcpb)) + (1.0 - upw_lo(mc_mc)));
-  const double gcf = 0.25 * g00 * (1.0 + upw_lo(mb_pc) + upw_lo(mb0)) +
-                     0.25 * gmb * (1.0 + (1.0 - upw_lo(mb_mbpc)) + (1.0 - upw_lo(mb_mb)));
-  const double grf = -0.25 * (g00 * (upw_lo(mc0) + upw_lo(mb0)) + gmb * (upw_lo(mc0) + (1.0 - upw_lo(mb_mb))) +
-                              gmc * ((1.0 - upw_lo(mc_mc)) + upw_lo(mb0)) +
-                              gmbc * ((1.0 - upw_lo(mc_mc)) + (1.0 - upw_lo(mb_mb))));
+  const T g00 = gEk[c00], gmb = gEk[cb], gmc = gEk[cc], gmbc = gEk[cbc];
+  // upwind weights of the mass fluxes mc(q), mc(q + e_b), mc(q - e_c), mc(q - e_c + e_b);
+  // mb(q), mb(q + e_c), mb(q - e_b), mb(q - e_b + e_c)
+  const T uc0 = upw_lo_t<T>(Fc[c00]), uc_pb = upw_lo_t<T>(Fc[cpb]), uc_mc = upw_lo_t<T>(Fc[cc]),
+          uc_mcpb = upw_lo_t<T>(Fc[cmcpb]);
+  const T ub0 = upw_lo_t<T>(Fb[c00]), ub_pc = upw_lo_t<T>(Fb[cpc]), ub_mb = upw_lo_t<T>(Fb[cb]),
+          ub_mbpc = upw_lo_t<T>(Fb[cmbpc]);
+  const T q4 = T(0.25);
+  const T gbf = q4 * g00 * (T(1) + uc_pb + uc0) + q4 * gmc * (T(1) + (T(1) - uc_mcpb) + (T(1) - uc_mc));
+  const T gcf = q4 * g00 * (T(1) + ub_pc + ub0) + q4 * gmb * (T(1) + (T(1) - ub_mbpc) + (T(1) - ub_mb));
+  const T grf = -q4 * (g00 * (uc0 + ub0) + gmb * (uc0 + (T(1) - ub_mb)) + gmc * ((T(1) - uc_mc) + ub0) +
+                       gmbc * ((T(1) - uc_mc) + (T(1) - ub_mb)));
   // bf = -F_B[5], cf = +F_C[6]
-  gF[((long long)B * 7 + 5) * N + c00] = T(-gbf);
-  gF[((long long)C * 7 + 6) * N + c00] = T(gcf);
+  gF[((long long)B * 7 + 5) * N + c00] = -gbf;
+  gF[((long long)C * 7 + 6) * N + c00] = gcf;
   // ref_K = -(v_B B_C - v_C B_B)
-  const double vB = to_d<T>(W[(1 + B) * N + c00]), vC = to_d<T>(W[(1 + C) * N + c00]);
-  const double BB = to_d<T>(W[(5 + B) * N + c00]), BC = to_d<T>(W[(5 + C) * N + c00]);
+  const T vB = W[(1 + B) * N + c00], vC = W[(1 + C) * N + c00];
+  const T BB = W[(5 + B) * N + c00], BC = W[(5 + C) * N + c00];
   gW8[1 + B] += -grf * BC;
   gW8[5 + C] += -grf * vB;
   gW8[1 + C] += grf * BB;
@@ -261,12 +265,12 @@ __global__ void __launch_bounds__(BX* BY) k_adj_emf(Grid g, const T* __restrict_
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
   const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
-  double gw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  T gw[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   emf_cot_edge<T, 0>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
   emf_cot_edge<T, 1>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
   emf_cot_edge<T, 2>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
 #pragma unroll
-  for (int f = 0; f < 8; ++f) gW[f * N + c] = T(gw[f]);
+  for (int f = 0; f < 8; ++f) gW[f * N + c] = gw[f];
 }
 
 // -------------------------------------------------- R4a / R9: HLLD reverse --
