@@ -1112,7 +1112,7 @@ __device__ __forceinline__ void prim_vjp(const Grid& g, double r, double m0, dou
                                          const double* b, const double* gW, double* g5, double* gb) {
   const bool rfl = !(r >= g.rho_floor);  // fmax(r, floor) takes the floor
   const double rho = fmax(r, g.rho_floor);
-  const double ir = 1.0 / rho;
+  const double ir = __drcp_rn(rho);  // (the correctly rounded 1/rho)
   const double v0 = m0 * ir, v1 = m1 * ir, v2 = m2 * ir;
   const double ke = 0.5 * (m0 * v0 + m1 * v1 + m2 * v2);
   const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);

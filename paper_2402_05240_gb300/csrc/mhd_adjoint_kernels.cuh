@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   if (rfl) g5[0] = 0.0;
 #pragma unroll
   for (int f = 0; f < 5; ++f) gU[f * N + c] = g5[f];
-  gBccF[c] = T(gb[0]);
-  gBccF[N + c] = T(gb[1]);
-  gBccF[2 * N + c] = T(gb[2]);
+  gBccF[c] = from_d<T>(gb[0]);
+  gBccF[N + c] = from_d<T>(gb[1]);
+  gBccF[2 * N + c] = from_d<T>(gb[2]);
 }
 
 // ------------------------------------------ R2 / R7: conservative update --
@@ -142,11 +142,12 @@ __device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const
   // gF_a[comp](p) = -(h/d_a)(g_f(p) - g_f(p + e_a))
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double s = -h * g.id[a];
+    const T s = from_d<T>(-h * g.id[a]);
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
+      // (the difference of the double cotangents in double, the product in T)
       const double gv = g5src[f * N + c] - g5src[f * N + cp[a]];
-      gF[((long long)a * 7 + comp_of(f, a)) * N + c] = T(s * gv);
+      gF[((long long)a * 7 + comp_of(f, a)) * N + c] = from_d<T>(gv) * s;
     }
   }
   // faces of this cell and of the upper neighbours needed by the edge cotangents
@@ -162,15 +163,13 @@ __device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const
   const double f1_z = face_cot<T, 1>(g, gUpF, gBcc, gBfx, i, j, wrapi(k + 1, g.n[2]));
   const double f2_x = face_cot<T, 2>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
   const double f2_y = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
+  const T hx = from_d<T>(h * g.id[0]), hy = from_d<T>(h * g.id[1]), hz = from_d<T>(h * g.id[2]);
   // k = 0 (E_x): B_y (a=1) with e_z, B_z (a=2) with e_y
-  const double gEx = -(h * g.id[2]) * (gf1 - f1_z) + (h * g.id[1]) * (gf2 - f2_y);
+  gE[c] = hy * from_d<T>(gf2 - f2_y) - hz * from_d<T>(gf1 - f1_z);
   // k = 1 (E_y): B_z with e_x, B_x with e_z
-  const double gEy = -(h * g.id[0]) * (gf2 - f2_x) + (h * g.id[2]) * (gf0 - f0_z);
+  gE[N + c] = hz * from_d<T>(gf0 - f0_z) - hx * from_d<T>(gf2 - f2_x);
   // k = 2 (E_z): B_x with e_y, B_y with e_x
-  const double gEz = -(h * g.id[1]) * (gf0 - f0_y) + (h * g.id[0]) * (gf1 - f1_x);
-  gE[c] = T(gEx);
-  gE[N + c] = T(gEy);
-  gE[2 * N + c] = T(gEz);
+  gE[2 * N + c] = hx * from_d<T>(gf1 - f1_x) - hy * from_d<T>(gf0 - f0_y);
   if (MODE == 0) {
     gU[5 * N + c] = gf0;
     gU[6 * N + c] = gf1;
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_hlld(Grid g, const T* __restrict
   if (PCM) {
     load_dir<A>(Wn, N, c, wl);
     load_dir<A>(Wn, N, cn, wr);
-    bn = T(U[(5 + A) * N + c]);
+    bn = from_d<T>(U[(5 + A) * N + c]);
   } else {
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
@@ -306,7 +305,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_hlld(Grid g, const T* __restrict
     gwl[q] = gwr[q] = T(0);
   }
   T gbn = T(0);
-  hlld_vjp<T>(T(g.gamma), wl, wr, bn, gf, gwl, gwr, gbn);
+  hlld_vjp<T>(from_d<T>(g.gamma), wl, wr, bn, gf, gwl, gwr, gbn);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     gWL[q * N + c] = gwl[q];
@@ -371,8 +370,8 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       T a = gl[q], b = gr[q];
-      if (q == 0 && w0[0] < T(g.rho_floor)) a = b = T(0);
-      if (q == 4 && w0[4] < T(g.p_floor)) a = b = T(0);
+      if (q == 0 && w0[0] < from_d<T>(g.rho_floor)) a = b = T(0);
+      if (q == 4 && w0[4] < from_d<T>(g.p_floor)) a = b = T(0);
       gw[1][q] = a + b;
     }
   } else if (RECON == 1) {
@@ -380,12 +379,13 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
     load_dir<A>(W, N, c, w0);
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
-    plmc_vjp<T>(T(g.gamma), T(g.rho_floor), T(g.p_floor), wm, w0, wp, bn, gl, gr, gw[0], gw[1], gw[2], gbn);
+    plmc_vjp<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), wm, w0, wp, bn, gl, gr, gw[0], gw[1],
+                gw[2], gbn);
   } else {
     T w[5][7];
 #pragma unroll
     for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
-    ppmc_vjp<T>(T(g.gamma), T(g.rho_floor), T(g.p_floor), w, bn, gl, gr, (T(*)[7])gw, gbn);
+    ppmc_vjp<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), w, bn, gl, gr, (T(*)[7])gw, gbn);
   }
 #pragma unroll
   for (int m = 0; m < NS; ++m)
@@ -446,9 +446,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __res
   prim_vjp(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
 #pragma unroll
   for (int f = 0; f < 5; ++f) g5[f * N + c] = o5[f];
-  gBcc[c] = T(gb[0]);
-  gBcc[N + c] = T(gb[1]);
-  gBcc[2 * N + c] = T(gb[2]);
+  gBcc[c] = from_d<T>(gb[0]);
+  gBcc[N + c] = from_d<T>(gb[1]);
+  gBcc[2 * N + c] = from_d<T>(gb[2]);
 }
 
 // R11: predictor faces: gU faces += gBf_a(p) + (1/2)(gBcc_a(p) + gBcc_a(p + e_a)); gU hydro += g5
