@@ -1142,4 +1142,36 @@ __device__ __forceinline__ void prim_vjp(const Grid& g, double r, double m0, dou
   g5[4] = ge;
 }
 
+// The same reverse for the FP32-bulk mode: the floor decisions from the
+// double pressure recovery as the FP32-bulk forward forms it
+// (P = (gamma - 1)(E - (|m|^2 / rho' + |B_cc|^2) / 2)), the derivative
+// arithmetic in float; gb[3] is written, not accumulated.
+__device__ __forceinline__ void prim_vjp_f32(const Grid& g, double r, double m0, double m1, double m2, double e,
+                                             const double* b, const float* gW, float* g5, float* gb) {
+  const bool rfl = !(r >= g.rho_floor);
+  const double rho = fmax(r, g.rho_floor);
+  const double ir = __drcp_rn(rho);
+  const double kem = 0.5 * ((m0 * m0 + m1 * m1 + m2 * m2) * ir + (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
+  const bool pfl = !(g.gm1 * (e - kem) >= g.p_floor);
+  const float irf = d2f_bits(ir), gm1 = d2f_bits(g.gm1);
+  const float m[3] = {d2f_bits(m0), d2f_bits(m1), d2f_bits(m2)};
+  const float bf[3] = {d2f_bits(b[0]), d2f_bits(b[1]), d2f_bits(b[2])};
+  const float ge = pfl ? 0.0f : gm1 * gW[4];
+  // ke = |m|^2 / (2 rho'), me = |B_cc|^2 / 2, both entering P with -ge
+  float gir = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float v = m[a] * irf;
+    gb[a] = gW[5 + a] - ge * bf[a];
+    // v = m ir: gm += gv ir, gir += gv m; ke: gm += -ge v
+    g5[1 + a] = gW[1 + a] * irf - ge * v;
+    gir += gW[1 + a] * m[a];
+  }
+  // d ke / d ir = |m|^2 / 2: gir += -ge |m|^2 / 2
+  gir += -0.5f * ge * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  const float grho = gW[0] - gir * irf * irf;
+  g5[0] = rfl ? 0.0f : grho;
+  g5[4] = ge;
+}
+
 }  // namespace mhd

@@ -439,16 +439,29 @@ __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __res
     b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
     b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
   }
-  double gw8[8];
+  if constexpr (std::is_same<T, float>::value) {
+    float gw8[8];
 #pragma unroll
-  for (int f = 0; f < 8; ++f) gw8[f] = to_d<T>(gW[f * N + c]);
-  double o5[5], gb[3] = {0.0, 0.0, 0.0};
-  prim_vjp(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
+    for (int f = 0; f < 8; ++f) gw8[f] = gW[f * N + c];
+    float o5[5], gb[3];
+    prim_vjp_f32(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
 #pragma unroll
-  for (int f = 0; f < 5; ++f) g5[f * N + c] = o5[f];
-  gBcc[c] = from_d<T>(gb[0]);
-  gBcc[N + c] = from_d<T>(gb[1]);
-  gBcc[2 * N + c] = from_d<T>(gb[2]);
+    for (int f = 0; f < 5; ++f) g5[f * N + c] = f2d_bits(o5[f]);
+    gBcc[c] = gb[0];
+    gBcc[N + c] = gb[1];
+    gBcc[2 * N + c] = gb[2];
+  } else {
+    double gw8[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) gw8[f] = to_d<T>(gW[f * N + c]);
+    double o5[5], gb[3] = {0.0, 0.0, 0.0};
+    prim_vjp(g, h5[0], h5[1], h5[2], h5[3], h5[4], b, gw8, o5, gb);
+#pragma unroll
+    for (int f = 0; f < 5; ++f) g5[f * N + c] = o5[f];
+    gBcc[c] = from_d<T>(gb[0]);
+    gBcc[N + c] = from_d<T>(gb[1]);
+    gBcc[2 * N + c] = from_d<T>(gb[2]);
+  }
 }
 
 // R11: predictor faces: gU faces += gBf_a(p) + (1/2)(gBcc_a(p) + gBcc_a(p + e_a)); gU hydro += g5
