@@ -52,16 +52,28 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   double gb[3] = {0.0, 0.0, 0.0};
   const bool rfl = u5[0] < g.rho_floor;
   const double r = rfl ? g.rho_floor : u5[0];
-  const double ke = 0.5 * (u5[1] * (u5[1] / r) + u5[2] * (u5[2] / r) + u5[3] * (u5[3] / r));
-  const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  const bool pfl = g.gm1 * (u5[4] - ke - me) < g.p_floor;
+  const double ir = __drcp_rn(r);
+  // kinetic + magnetic energy and the pressure-floor test with the forward's
+  // arithmetic (k_prim; its FP32-bulk form in prim_store_f32)
+  double ke, me;
+  if constexpr (std::is_same<T, float>::value) {
+    ke = 0.5 * ((u5[1] * u5[1] + u5[2] * u5[2] + u5[3] * u5[3]) * ir);
+    me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  } else {
+    ke = 0.5 * (u5[1] * (u5[1] * ir) + u5[2] * (u5[2] * ir) + u5[3] * (u5[3] * ir));
+    me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  }
+  const bool pfl = std::is_same<T, float>::value
+                       ? g.gm1 * (u5[4] - 0.5 * ((u5[1] * u5[1] + u5[2] * u5[2] + u5[3] * u5[3]) * ir +
+                                                 (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]))) < g.p_floor
+                       : g.gm1 * (u5[4] - ke - me) < g.p_floor;
   if (pfl) {  // E = p_floor/(gamma-1) + |m|^2/(2 r) + |B_cc|^2/2
     const double gE = g5[4];
     g5[4] = 0.0;
-    g5[1] += gE * u5[1] / r;
-    g5[2] += gE * u5[2] / r;
-    g5[3] += gE * u5[3] / r;
-    if (!rfl) g5[0] += -gE * ke / r;
+    g5[1] += gE * u5[1] * ir;
+    g5[2] += gE * u5[2] * ir;
+    g5[3] += gE * u5[3] * ir;
+    if (!rfl) g5[0] += -gE * ke * ir;
     gb[0] = gE * b[0];
     gb[1] = gE * b[1];
     gb[2] = gE * b[2];
