@@ -73,17 +73,19 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # as profiled; a kernel changed since has no entry.
 COUNTERS = {
     "fp64": {
-        "prim": (121.0, 171.0, 954 / 32, 105.1),
+        "prim": (121.0, 171.0, 959 / 32, 105.9),
         "flux_pcm": (236.5, 361.0, 1584 / 32, 100.9),
-        "emf": (96.0, 111.0, 1028 / 32, 139.5),
+        "emf": (96.0, 111.0, 1028 / 32, 139.7),
         "update_half": (88.0, 126.0, 826 / 32, 282.9),
-        "recon": (295.9, 379.9, 2234 / 32, 150.2),
-        "flux_hlld": (235.6, 359.6, 1578 / 32, 162.1),
-        "update_full": (50.0, 71.0, 524 / 32, 260.8),
+        "recon": (295.9, 379.9, 2234 / 32, 150.3),
+        "flux_hlld": (235.6, 359.6, 1578 / 32, 162.2),
+        "update_full": (50.0, 71.0, 524 / 32, 261.0),
     },
     "fp32_bulk": {
+        "prim": (19.0, 29.0, 744 / 32, 82.1),
         "flux_pcm": (0.0, 0.0, 554 / 32, 45.9),
         "emf": (0.0, 0.0, 570 / 32, 66.8),
+        "update_half": (33.0, 50.0, 1593 / 32, 171.7),
         "recon": (0.0, 0.0, 774 / 32, 62.7),
         "flux_hlld": (0.0, 0.0, 530 / 32, 74.2),
         "update_full": (19.0, 22.0, 1433 / 32, 180.5),
