@@ -70,5 +70,12 @@ def test_null_arguments_rejected(lib):
     lib.mhd_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
     lib.mhd_step.restype = ctypes.c_int
     assert lib.mhd_step(None, None, 0.1, None) == -1
+    vp = ctypes.c_void_p
+    lib.mhd_adjoint_step.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.mhd_adjoint_step.restype = ctypes.c_int
+    assert lib.mhd_adjoint_step(None, None, 1e-3, None, None) == -1
+    lib.mhd_adjoint_step_cfl.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.mhd_adjoint_step_cfl.restype = ctypes.c_int
+    assert lib.mhd_adjoint_step_cfl(None, None, None, None, None, None) == -1
     lib.mhd_strerror.restype = ctypes.c_char_p
     assert lib.mhd_strerror(-4).startswith(b"non-finite")
