@@ -249,11 +249,13 @@ template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* 
 }
 
 // blocks of 128 threads per SM requested from the register allocator (4:
-// at most 128 registers per thread, 3: at most 168).  The double and
-// double-float PPMC and the double PLMC kernels fit 128 registers without
-// spilling; the double-float PLMC kernel would spill there.
+// at most 128 registers per thread).  The double and double-float PPMC and
+// the double PLMC kernels fit 128 registers without spilling; the
+// double-float PLMC kernel spills 40 bytes there and still runs 9 % faster
+// than at 3 blocks (168 registers, no spill): its dependent float-pair
+// chains need the extra warps.  (The double-float flux kernels, 112-119
+// registers, lose 2 % at 5 blocks with 40-68 bytes of spill.)
 template <class T, int RECON> struct ReconMinBlocks { static constexpr int v = 4; };
-template <> struct ReconMinBlocks<df, 1> { static constexpr int v = 3; };
 
 template <class T, int RECON, int A>
 __global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
