@@ -254,7 +254,8 @@ template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* 
 // double-float PLMC kernel spills 40 bytes there and still runs 9 % faster
 // than at 3 blocks (168 registers, no spill): its dependent float-pair
 // chains need the extra warps.  (The double-float flux kernels, 112-119
-// registers, lose 2 % at 5 blocks with 40-68 bytes of spill.)
+// registers, lose 2 % at 5 blocks with 40-68 bytes of spill; the double PLMC
+// kernel, 108 registers, loses 5 % at 5 blocks, 96 registers.)
 template <class T, int RECON> struct ReconMinBlocks { static constexpr int v = 4; };
 
 template <class T, int RECON, int A>
