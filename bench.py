@@ -91,13 +91,13 @@ COUNTERS = {
         "update_full": (19.0, 22.0, 1433 / 32, 180.5),
     },
     "fp64_df": {
-        "prim": (37.0, 53.0, 1485 / 32, 105.1),
+        "prim": (37.0, 53.0, 1476 / 32, 105.2),
         "flux_pcm": (0.0, 0.0, 3034 / 32, 101.1),
         "emf": (0.0, 0.0, 1515 / 32, 140.0),
-        "update_half": (49.0, 66.0, 2591 / 32, 282.5),
-        "recon": (0.0, 0.0, 3810 / 32, 150.7),
+        "update_half": (49.0, 66.0, 2591 / 32, 282.6),
+        "recon": (0.0, 0.0, 3832 / 32, 151.8),
         "flux_hlld": (0.0, 0.0, 3000 / 32, 162.5),
-        "update_full": (19.0, 22.0, 1520 / 32, 260.1),
+        "update_full": (19.0, 22.0, 1520 / 32, 260.0),
     },
 }
 
