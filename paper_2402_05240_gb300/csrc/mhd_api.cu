@@ -432,8 +432,8 @@ int adjoint_step(mhd_ctx* c, const double* Un, double dt, const double* gUp, dou
   }
   double* part0 = cfl ? b.part : nullptr;
   double* part1 = cfl ? b.part + b.nparts : nullptr;
-  // forward recompute (Steps 1-8)
-  Launch<T>::prim(g, U, b.Wn, nullptr, c->flags, nullptr, s);
+  // forward recompute (Steps 1-8; W^n is already in place after the dt reduction)
+  if (!cfl) Launch<T>::prim(g, U, b.Wn, nullptr, c->flags, nullptr, s);
   for (int a = 0; a < 3; ++a) Launch<T>::flux_pcm(g, a, b.Wn, U, b.Fn, s);
   Launch<T>::emf(g, b.Wn, b.Fn, b.Eh, s);
   mhd::AdjLaunch<T>::fwd_half_keep(g, U, b.Fn, b.Eh, dt, b.Wh, b.Bh, b.Uh, s);
