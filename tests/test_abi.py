@@ -54,6 +54,10 @@ def test_config_validation_without_gpu():
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 0.0, 1e-20),  # floor
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(0, 3, 0)),  # bc
         mhd.mhd_config(8, 8, 8, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20, (ctypes.c_int * 3)(1, 2, 0)),  # outflow+halo
+        mhd.mhd_config(4, 4, 65536, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # nz above the launch grid's z limit
+        mhd.mhd_config(65536, 32769, 4, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # nx ny above 2^31
+        mhd.mhd_config(4, 4, 65530, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20,
+                       (ctypes.c_int * 3)(0, 0, 1)),  # padded nz above the z limit
     ]
     for cfg in bad:
         with pytest.raises(mhd.MHDError) as e:

@@ -280,3 +280,35 @@ def test_floors_trigger_and_count(mhd):
     assert counts[1] > 0
     assert counts[1] == orc.floor_counts[1] and counts[0] == orc.floor_counts[0]
     assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-12)
+
+
+# ------------------------------------------------------------- edge sizes --
+@pytest.mark.parametrize("n", [(4, 4, 4), (5, 4, 7), (4, 6, 5)])
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_smallest_grids(mhd, n, recon):
+    """Grids at the 4-cell minimum per axis: one step's stencil (5 cells with
+    PPMC) wraps around the periodic box more than once."""
+    U0 = turb(n, seed=17, kmax=1)
+    sim = mhd.Sim(*n, cfl=0.3, recon=recon)
+    U = cuda(U0)
+    dts = torch.zeros(5, dtype=torch.float64, device="cuda")
+    sim.run(U, 5, dts)
+    torch.cuda.synchronize()
+    sim.status()
+    ref, _ = O.Oracle(*n, recon=recon).run(U0, 5, dts=list(dts.cpu().numpy()))
+    assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-12)
+
+
+def test_longest_z_axis(mhd):
+    """nz = 65535, the largest extent the launch grid's z dimension takes,
+    with 4 x 4 cells per plane."""
+    n = (4, 4, 65535)
+    U0 = turb(n, seed=19, kmax=2)
+    sim = mhd.Sim(*n, cfl=0.3, recon="plmc")
+    U = cuda(U0)
+    dts = torch.zeros(2, dtype=torch.float64, device="cuda")
+    sim.run(U, 2, dts)
+    torch.cuda.synchronize()
+    sim.status()
+    ref, _ = O.Oracle(*n, recon="plmc").run(U0, 2, dts=list(dts.cpu().numpy()))
+    assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-12)
