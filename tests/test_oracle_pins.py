@@ -371,8 +371,9 @@ def test_ppmc_keeps_smooth_extrema_at_fourth_order():
     assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8, errs
 
 
+@pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 @pytest.mark.parametrize("profile", ["step", "tanh"])
-def test_ppmc_creates_no_new_extrema(profile):
+def test_recon_creates_no_new_extrema(profile, recon):
     """At a discontinuity and across a steep monotone front the limited
     interface values stay inside the range of the two cells they separate."""
     n = 32
@@ -383,7 +384,7 @@ def test_ppmc_creates_no_new_extrema(profile):
     else:
         rho = 1.5 + 0.5 * np.tanh((x - 0.5) / 0.03)
     U = _wave_state(box, lambda _x: rho)
-    WL, WR = O.Oracle(n, 4, 4, recon="ppmc").recon(U, 0)
+    WL, WR = O.Oracle(n, 4, 4, recon=recon).recon(U, 0)
     r = U[0, 0, 0]
     for i in range(n):
         lo, hi = min(r[i], r[(i + 1) % n]), max(r[i], r[(i + 1) % n])
