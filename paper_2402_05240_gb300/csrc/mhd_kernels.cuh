@@ -318,6 +318,13 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
 template <class T> __device__ __forceinline__ T upwind(T m, T lo, T hi) {
   return m > T(0) ? lo : (m < T(0) ? hi : T(0.5) * (lo + hi));
 }
+// double: the sign test on the bit pattern (integer pipes), the mean only
+// for an exactly zero mass flux
+template <> __device__ __forceinline__ double upwind<double>(double m, double lo, double hi) {
+  const long long b = dbits(m);
+  if (__builtin_expect((b & kAbsBits) == 0, 0)) return 0.5 * (lo + hi);
+  return b > 0 ? lo : hi;
+}
 
 template <class T, int A>
 __device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, const T* __restrict__ F, int i,
