@@ -51,6 +51,64 @@ template <> __device__ __forceinline__ df tsqrt<df>(df x) { return df_sqrt(x); }
 template <> __device__ __forceinline__ df trcp<df>(df x) { return df(1.0f, 0.0f) / x; }
 template <> __device__ __forceinline__ df trsqrt<df>(df x) { return df_rsqrt(x); }
 
+// Comparisons of the step's branch decisions.  The generic forms use
+// floating-point compares; for double they test the bit pattern on the
+// integer pipes (the FP64 pipe bounds the FP64 step), with the same result
+// for every non-NaN operand.  Positive doubles order like their bit
+// patterns as signed 64-bit integers; -0 is the most negative pattern.
+constexpr long long kAbsBits = 0x7fffffffffffffffLL;
+constexpr long long kNegZero = (long long)0x8000000000000000ULL;
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+template <class T> __device__ __forceinline__ bool ge0(T x) { return x >= T(0); }
+template <class T> __device__ __forceinline__ bool gt0(T x) { return x > T(0); }
+template <class T> __device__ __forceinline__ bool lt0(T x) { return x < T(0); }
+template <class T> __device__ __forceinline__ bool le0(T x) { return x <= T(0); }
+template <class T> __device__ __forceinline__ bool is0(T x) { return x == T(0); }
+// |x| < t for t >= 0
+template <class T> __device__ __forceinline__ bool abs_lt(T x, T t) { return fabs(x) < t; }
+// x < t for x, t >= 0
+template <class T> __device__ __forceinline__ bool nonneg_lt(T x, T t) { return x < t; }
+// max(x, t) for t > 0 (x of any sign)
+template <class T> __device__ __forceinline__ T max_pos(T x, T t) { return fmax(x, t); }
+// max(x, y) for x, y >= 0
+template <class T> __device__ __forceinline__ T max_nonneg(T x, T y) { return fmax(x, y); }
+// min and max of two values of any sign
+template <class T> __device__ __forceinline__ T min_s(T x, T y) { return fmin(x, y); }
+template <class T> __device__ __forceinline__ T max_s(T x, T y) { return fmax(x, y); }
+
+template <> __device__ __forceinline__ bool ge0<double>(double x) {
+  const long long b = dbits(x);
+  return (b >= 0) | (b == kNegZero);
+}
+template <> __device__ __forceinline__ bool gt0<double>(double x) { return dbits(x) > 0; }
+template <> __device__ __forceinline__ bool lt0<double>(double x) {
+  const long long b = dbits(x);
+  return (b < 0) & (b != kNegZero);
+}
+template <> __device__ __forceinline__ bool le0<double>(double x) { return dbits(x) <= 0; }
+template <> __device__ __forceinline__ bool is0<double>(double x) { return (dbits(x) & kAbsBits) == 0; }
+template <> __device__ __forceinline__ bool abs_lt<double>(double x, double t) {
+  return (dbits(x) & kAbsBits) < dbits(t);
+}
+template <> __device__ __forceinline__ bool nonneg_lt<double>(double x, double t) { return dbits(x) < dbits(t); }
+template <> __device__ __forceinline__ double max_pos<double>(double x, double t) {
+  return dbits(x) > dbits(t) ? x : t;
+}
+template <> __device__ __forceinline__ double max_nonneg<double>(double x, double y) {
+  return dbits(x) >= dbits(y) ? x : y;
+}
+// order key: sign-magnitude patterns mapped to a monotone signed integer
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & kAbsBits);
+}
+template <> __device__ __forceinline__ double min_s<double>(double x, double y) {
+  return dkey(y) < dkey(x) ? y : x;
+}
+template <> __device__ __forceinline__ double max_s<double>(double x, double y) {
+  return dkey(x) < dkey(y) ? y : x;
+}
+
 // Conversions between the compute type and double without the conversion
 // instructions, which issue at the FP64 rate on this GPU (mhd_df.cuh).
 template <class T> __device__ __forceinline__ double to_d(T x);
@@ -117,10 +175,10 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     return w[4] * gm1i + T(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) + T(0.5) * bb;
   };
   // max(c_f,L, c_f,R) as the root of the larger square (the root is monotone)
-  const T cmax = tsqrt<T>(fmax(fast_speed_sq<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
-                               fast_speed_sq<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6])));
-  const T SL = fmin(wl[1], wr[1]) - cmax;
-  const T SR = fmax(wl[1], wr[1]) + cmax;
+  const T cmax = tsqrt<T>(max_nonneg<T>(fast_speed_sq<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
+                                        fast_speed_sq<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6])));
+  const T SL = min_s<T>(wl[1], wr[1]) - cmax;
+  const T SR = max_s<T>(wl[1], wr[1]) + cmax;
 
   auto phys = [&](const T* w, T e, T pt, T* F) {
     const T mu = w[0] * w[1];
@@ -132,11 +190,11 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     F[5] = w[5] * w[1] - bn * w[2];
     F[6] = w[6] * w[1] - bn * w[3];
   };
-  if (SL >= T(0)) {
+  if (ge0<T>(SL)) {
     phys(wl, energy(wl, bbL), ptL, f);
     return;
   }
-  if (SR <= T(0)) {
+  if (le0<T>(SR)) {
     phys(wr, energy(wr, bbR), ptR, f);
     return;
   }
@@ -156,7 +214,7 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     s.iSM = trcp<T>(S - SM);
     s.r = rd * s.iSM;
     const T D = rd * (S - SM) - bn2;
-    if (fabs(D) < Eps<T>::hlld * pts) {
+    if (abs_lt<T>(D, Eps<T>::hlld * pts)) {
       s.v = w[2];
       s.w = w[3];
       s.by = w[5];
@@ -178,7 +236,7 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
   const Star sR = star(wr, SR, dR, rdR);
 
   // the region containing x/t = 0 lies on the side of S_M (ties to the left)
-  const bool left = SM >= T(0);
+  const bool left = ge0<T>(SM);
   const T* w = left ? wl : wr;
   const Star& s = left ? sL : sR;
   const T S = left ? SL : SR;
@@ -193,9 +251,9 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
   // double-star (rotational) states
   T SsL = SM, SsR = SM;
   T vss, wss, byss, bzss, ess;
-  const bool dbl = !(T(0.5) * bn2 < Eps<T>::hlld * pts);
+  const bool dbl = !nonneg_lt<T>(T(0.5) * bn2, Eps<T>::hlld * pts);
   if (dbl) {
-    const T sg = bn > T(0) ? T(1) : T(-1);
+    const T sg = gt0<T>(bn) ? T(1) : T(-1);
     const T abn = fabs(bn);
     SsL = SM - abn * sL.rsq;
     SsR = SM + abn * sR.rsq;
@@ -218,7 +276,7 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
   // F* = F + S (U* - U)
   for (int q = 0; q < 7; ++q) f[q] = F[q] + S * (Us[q] - U0[q]);
   const T Ss = left ? SsL : SsR;
-  const bool inner = left ? (SsL < T(0)) : (SsR >= T(0));
+  const bool inner = left ? lt0<T>(SsL) : ge0<T>(SsR);
   if (dbl && inner) {
     const T Uss[7] = {s.r, s.r * SM, s.r * vss, s.r * wss, ess, byss, bzss};
     for (int q = 0; q < 7; ++q) f[q] = f[q] + Ss * (Uss[q] - Us[q]);
@@ -259,12 +317,12 @@ template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w
   const T rcf = trsqrt<T>(cf2);
   E.cf = cf2 * rcf;
   E.cs = E.a * fabs(bn) * E.isr * rcf;
-  const T ibt = bt2r > T(0) ? trsqrt<T>(bt2r) : T(0);
+  const T ibt = gt0<T>(bt2r) ? trsqrt<T>(bt2r) : T(0);
   const T btn = bt2r * ibt * E.isr;  // |B_t| / sqrt(rho)
-  if (sd == T(0)) {
+  if (is0<T>(sd)) {
     E.af = T(1);
     E.as = T(0);
-  } else if (D >= T(0)) {
+  } else if (ge0<T>(D)) {
     const T q = trsqrt<T>(T(2) * sd * (sd + D));
     E.af = (sd + D) * q;
     E.as = T(2) * E.a * btn * q;
@@ -273,14 +331,14 @@ template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w
     E.af = T(2) * E.a * btn * q;
     E.as = (sd - D) * q;
   }
-  if (bt2r == T(0)) {
+  if (is0<T>(bt2r)) {
     E.b1 = T(0.70710678118654752440);
     E.b2 = T(0.70710678118654752440);
   } else {
     E.b1 = w[5] * ibt;
     E.b2 = w[6] * ibt;
   }
-  E.sg = bn >= T(0) ? T(1) : T(-1);
+  E.sg = ge0<T>(bn) ? T(1) : T(-1);
   const T a = E.a;
   E.Qf = E.cf * E.af * E.sg;
   E.Qs = E.cs * E.as * E.sg;
@@ -343,8 +401,6 @@ template <class T> __device__ __forceinline__ bool abs_ge_twice(T a, T b) { retu
 template <class T> __device__ __forceinline__ T twice(T x) { return T(2) * x; }
 template <> __device__ __forceinline__ df twice<df>(df x) { return df(2.0f * x.hi, 2.0f * x.lo); }
 
-constexpr long long kAbsBits = 0x7fffffffffffffffLL;
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 template <> __device__ __forceinline__ bool pos_prod<double>(double a, double b) {
   const long long x = dbits(a), y = dbits(b);
   return ((x ^ y) >= 0) & ((x & kAbsBits) != 0) & ((y & kAbsBits) != 0);

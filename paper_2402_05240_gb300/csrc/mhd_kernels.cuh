@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, const T* __restrict
 
 // ------------------------------------------------------------------ Step 6 --
 template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* w) {
-  w[0] = fmax(w[0], from_d<T>(g.rho_floor));
-  w[4] = fmax(w[4], from_d<T>(g.p_floor));
+  w[0] = max_pos<T>(w[0], from_d<T>(g.rho_floor));
+  w[4] = max_pos<T>(w[4], from_d<T>(g.p_floor));
 }
 
 // blocks of 128 threads per SM requested from the register allocator (4:
