@@ -73,21 +73,21 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # as profiled; a kernel changed since has no entry.
 COUNTERS = {
     "fp64": {
-        "prim": (121.0, 171.0, 959 / 32, 105.9),
-        "flux_pcm": (236.5, 361.0, 1584 / 32, 100.9),
-        "emf": (96.0, 111.0, 1028 / 32, 139.7),
-        "update_half": (88.0, 126.0, 826 / 32, 282.9),
-        "recon": (295.9, 379.9, 2234 / 32, 150.3),
-        "flux_hlld": (235.6, 359.6, 1578 / 32, 162.2),
-        "update_full": (50.0, 71.0, 524 / 32, 261.0),
+        "prim": (121.0, 171.0, 918 / 32, 106.0),
+        "flux_pcm": (235.3, 358.6, 1525 / 32, 101.2),
+        "emf": (72.0, 87.0, 977 / 32, 139.9),
+        "update_half": (88.0, 126.0, 809 / 32, 283.1),
+        "recon": (295.9, 379.9, 2183 / 32, 150.3),
+        "flux_hlld": (234.5, 357.3, 1516 / 32, 162.4),
+        "update_full": (50.0, 71.0, 524 / 32, 260.9),
     },
     "fp32_bulk": {
-        "prim": (19.0, 29.0, 744 / 32, 82.1),
+        "prim": (19.0, 29.0, 730 / 32, 82.0),
         "flux_pcm": (0.0, 0.0, 554 / 32, 45.9),
         "emf": (0.0, 0.0, 570 / 32, 66.8),
-        "update_half": (33.0, 50.0, 1593 / 32, 171.7),
+        "update_half": (33.0, 50.0, 1575 / 32, 171.6),
         "recon": (0.0, 0.0, 774 / 32, 62.7),
-        "flux_hlld": (0.0, 0.0, 530 / 32, 74.2),
+        "flux_hlld": (0.0, 0.0, 530 / 32, 74.3),
         "update_full": (19.0, 22.0, 1433 / 32, 180.5),
     },
     "fp64_df": {

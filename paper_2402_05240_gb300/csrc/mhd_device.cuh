@@ -68,6 +68,8 @@ template <class T> __device__ __forceinline__ bool is0(T x) { return x == T(0); 
 template <class T> __device__ __forceinline__ bool abs_lt(T x, T t) { return fabs(x) < t; }
 // x < t for x, t >= 0
 template <class T> __device__ __forceinline__ bool nonneg_lt(T x, T t) { return x < t; }
+// x < t for t > 0 (x of any sign)
+template <class T> __device__ __forceinline__ bool lt_pos(T x, T t) { return x < t; }
 // max(x, t) for t > 0 (x of any sign)
 template <class T> __device__ __forceinline__ T max_pos(T x, T t) { return fmax(x, t); }
 // max(x, y) for x, y >= 0
@@ -91,6 +93,7 @@ template <> __device__ __forceinline__ bool abs_lt<double>(double x, double t) {
   return (dbits(x) & kAbsBits) < dbits(t);
 }
 template <> __device__ __forceinline__ bool nonneg_lt<double>(double x, double t) { return dbits(x) < dbits(t); }
+template <> __device__ __forceinline__ bool lt_pos<double>(double x, double t) { return dbits(x) < dbits(t); }
 template <> __device__ __forceinline__ double max_pos<double>(double x, double t) {
   return dbits(x) > dbits(t) ? x : t;
 }
@@ -578,7 +581,7 @@ template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T&
     T r = T(0);
     // (|d2lim4 / d2f| <= 1: a reciprocal where d2f is far from the
     // underflow range, else the division)
-    if (d2f != T(0)) r = ratio_le1<T>(d2lim4<T>(d2f, d2m1, d20, d2p1), d2f);
+    if (!is0<T>(d2f)) r = ratio_le1<T>(d2lim4<T>(d2f, d2m1, d20, d2p1), d2f);
     qm = q[2] - r * dqm;
     qp = q[2] + r * dqp;
   } else {

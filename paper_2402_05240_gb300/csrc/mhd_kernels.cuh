@@ -78,7 +78,7 @@ template <class T> __device__ __forceinline__ T cell_inv_crossing(const Grid& g,
     const T b2 = sq[l] * ir + t2;
     const T dd = a2 - b2;
     const T cf = tsqrt<T>(T(0.5) * (a2 + b2 + tsqrt<T>(dd * dd + T(4) * a2 * t2)));
-    best = fmax(best, (fabs(w8[1 + l]) + cf) * from_d<T>(g.id[l]));
+    best = max_nonneg<T>(best, (fabs(w8[1 + l]) + cf) * from_d<T>(g.id[l]));
   }
   return best;
 }
@@ -97,13 +97,13 @@ __device__ __forceinline__ PrimD prim_core_ir(const Grid& g, double rho, double 
   w.v[2] = m2 * ir;
   const double ke = 0.5 * (m0 * w.v[0] + m1 * w.v[1] + m2 * w.v[2]);
   const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  w.p = fmax(g.gm1 * (e - ke - me), g.p_floor);
+  w.p = max_pos<double>(g.gm1 * (e - ke - me), g.p_floor);
   return w;
 }
 
 __device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, double m1, double m2, double e,
                                            const double* b) {
-  const double rho = fmax(r, g.rho_floor);
+  const double rho = max_pos<double>(r, g.rho_floor);
   return prim_core_ir(g, rho, __drcp_rn(rho), m0, m1, m2, e, b);
 }
 
@@ -132,7 +132,7 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
   const double mm = m0 * m0 + m1 * m1 + m2 * m2;
   const double bb = bsum[0] * bsum[0] + bsum[1] * bsum[1] + bsum[2] * bsum[2];
   const double kem = 0.5 * (mm * ir + 0.25 * bb);  // ke + me
-  const double p = fmax(g.gm1 * (e - kem), g.p_floor);
+  const double p = max_pos<double>(g.gm1 * (e - kem), g.p_floor);
   const float irf = d2f_bits(ir);
   w8[0] = d2f_bits(rho);
   w8[1] = d2f_bits(m0) * irf;
@@ -166,12 +166,12 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     double r = U[c], e = U[4 * N + c];
     const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
     if ((!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) && in) atomicOr(flags, 1u);
-    if (floors && r < g.rho_floor) {
+    if (floors && lt_pos<double>(r, g.rho_floor)) {
       r = g.rho_floor;
       U[c] = r;
       if (in) atomicAdd(&floors[0], 1ull);
     }
-    const double rho = fmax(r, g.rho_floor);
+    const double rho = max_pos<double>(r, g.rho_floor);
     const double ir = __drcp_rn(rho);
     T w8[8];
     if constexpr (std::is_same<T, float>::value) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
                             U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c],
                             U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]};
       const double kem = prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8);
-      if (floors && g.gm1 * (e - kem) < g.p_floor) {
+      if (floors && lt_pos<double>(g.gm1 * (e - kem), g.p_floor)) {
         U[4 * N + c] = g.p_floor * g.igm1 + kem;
         if (in) atomicAdd(&floors[1], 1ull);
       }
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
       if (floors) {
         const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
         const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-        if (g.gm1 * (e - ke - me) < g.p_floor) {
+        if (lt_pos<double>(g.gm1 * (e - ke - me), g.p_floor)) {
           e = g.p_floor * g.igm1 + ke + me;
           U[4 * N + c] = e;
           if (in) atomicAdd(&floors[1], 1ull);
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   T w8[8];
   if constexpr (std::is_same<T, float>::value) {
     const double bs[3] = {bxm + bx, bym + by, bzm + bz};
-    const double rho = fmax(u5[0], g.rho_floor);
+    const double rho = max_pos<double>(u5[0], g.rho_floor);
     prim_store_f32(g, W, c, rho, __drcp_rn(rho), u5[1], u5[2], u5[3], u5[4], bs, w8);
   } else {
     const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
