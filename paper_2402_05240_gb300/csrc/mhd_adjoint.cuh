@@ -174,42 +174,33 @@ __device__ __forceinline__ void eig_right_vjp(const Eig<T>& E, const T* q, const
 // a = sqrt(a2).  A root that is zero, and beta where |B_t|^2 < 1e-12 (B_n^2 +
 // gamma P) (reading D-23), carry no derivative.
 template <class T>
-__device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const EigG<T>& gE, T* gw0, T& gbn) {
+__device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const Eig<T>& E, const EigG<T>& gE,
+                                               T* gw0, T& gbn) {
   const T rho = w0[0], p = w0[4], by = w0[5], bz = w0[6];
-  // forward values
-  const T ir = trcp<T>(rho);
-  const T a2 = gamma * p * ir;
-  const T ia2 = trcp<T>(a2);
+  // forward values: the roots and reciprocals come from the forward
+  // eigensystem E of the same state (eig_build), the rest is recomputed
+  const T ir = E.ir, a2 = E.a2, ia2 = E.ia2, cf = E.cf, cs = E.cs, sr = E.sr, isr = E.isr, a = E.a;
   const T ca2 = bn * bn * ir;
   const T bt2r = by * by + bz * bz;
   const T bt2 = bt2r * ir;
   const T b2 = ca2 + bt2;
   const T D = a2 - b2;
   const T sd = tsqrt<T>(D * D + T(4) * a2 * bt2);
-  const T cf2 = T(0.5) * (a2 + b2 + sd);
-  const T icf2 = trcp<T>(cf2);
+  const T icf2 = E.rcf * E.rcf;
   const T cs2 = a2 * ca2 * icf2;
-  const T cf = tsqrt<T>(cf2);
-  const T cs = tsqrt<T>(cs2);
-  const T sg = bn >= T(0) ? T(1) : T(-1);
-  const T sr = tsqrt<T>(rho);
-  const T isr = trcp<T>(sr);
-  const T a = tsqrt<T>(a2);
+  const T sg = E.sg;
   // magnetosonic normalisations: af = sqrt(uf), as = sqrt(us)
-  const int br = sd == T(0) ? 0 : (D >= T(0) ? 1 : 2);
-  T af = T(1), as = T(0), M = T(0), N = T(0), iM = T(0), r2s = T(0);
+  const int br = is0<T>(sd) ? 0 : (ge0<T>(D) ? 1 : 2);
+  const T af = E.af, as = E.as;
+  T M = T(0), N = T(0), iM = T(0), r2s = T(0);
   if (br != 0) {
     N = T(2) * a2 * bt2;
     M = br == 1 ? sd * (sd + D) : sd * (sd - D);
     iM = trcp<T>(M);
     r2s = trcp<T>(T(2) * sd);
-    const T big = (br == 1 ? sd + D : sd - D) * r2s;  // the root of the larger member
-    const T small = N * iM;
-    af = tsqrt<T>(br == 1 ? big : small);
-    as = tsqrt<T>(br == 1 ? small : big);
   }
-  const T bt = tsqrt<T>(bt2r);
-  const bool bfree = !(bt == T(0)) && !(bt2r < T(1e-12) * (bn * bn + gamma * p));
+  const T ibt = gt0<T>(bt2r) ? trsqrt<T>(bt2r) : T(0);
+  const bool bfree = gt0<T>(bt2r) && !(bt2r < T(1e-12) * (bn * bn + gamma * p));
 
   // reverse sweep
   T g_rho = gE.rho, g_ir = gE.ir, g_sr = gE.sr, g_isr = gE.isr, g_a = gE.a, g_a2 = gE.a2, g_ia2 = gE.ia2;
@@ -225,13 +216,12 @@ __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const
   g_as += gE.As * a * sr;
   g_sr += gE.Af * a * af + gE.As * a * as;
   // a = sqrt(a2), isr = 1/sr, sr = sqrt(rho)
-  if (a > T(0)) g_a2 += g_a * T(0.5) * trcp<T>(a);
+  if (a > T(0)) g_a2 += g_a * T(0.5) * (a * ia2);  // 1/a = a / a^2
   g_sr += -g_isr * isr * isr;
   if (sr > T(0)) g_rho += g_sr * T(0.5) * isr;
   // b1 = by / bt, b2 = bz / bt, bt = sqrt(bt2r)
   T g_bt2r = T(0);
   if (bfree) {
-    const T ibt = trcp<T>(bt);
     g_by += gE.b1 * ibt;
     g_bz += gE.b2 * ibt;
     const T g_bt = -(gE.b1 * by + gE.b2 * bz) * ibt * ibt;
@@ -259,7 +249,7 @@ __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const
   }
   // cs = sqrt(cs2), cf = sqrt(cf2), cs2 = a2 ca2 / cf2, cf2 = (a2 + b2 + sd)/2
   T g_cs2 = cs > T(0) ? g_cs * T(0.5) * trcp<T>(cs) : T(0);
-  T g_cf2 = cf > T(0) ? g_cf * T(0.5) * trcp<T>(cf) : T(0);
+  T g_cf2 = cf > T(0) ? g_cf * T(0.5) * E.rcf : T(0);
   g_a2 += g_cs2 * ca2 * icf2;
   T g_ca2 = g_cs2 * a2 * icf2;
   g_cf2 += -g_cs2 * cs2 * icf2;
@@ -268,7 +258,7 @@ __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const
   g_sd += T(0.5) * g_cf2;
   // sd = sqrt(D^2 + 4 a2 bt2)
   if (sd > T(0)) {
-    const T g_X = g_sd * T(0.5) * trcp<T>(sd);
+    const T g_X = g_sd * r2s;  // (sd > 0: r2s = 1/(2 sd))
     g_D += g_X * T(2) * D;
     g_a2 += g_X * T(4) * bt2;
     g_bt2 += g_X * T(4) * a2;
@@ -324,15 +314,17 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
   for (int q = 0; q < 7; ++q) {
     sel[q] = -1;
     am[q] = T(0);
-    if (aL[q] * aR[q] > T(0)) {
-      // same selection order as fmin(fmin(2|aL|, 2|aR|), fmin(|aC|, |aG|))
-      const T c0 = T(2) * fabs(aL[q]), c1 = T(2) * fabs(aR[q]), c2 = fabs(aC[q]), c3 = fabs(aG[q]);
-      const int s01 = (c1 < c0) ? 1 : 0;
-      const T m01 = fmin(c0, c1);
-      const int s23 = (c3 < c2) ? 3 : 2;
-      const T m23 = fmin(c2, c3);
-      sel[q] = (m23 < m01) ? s23 : s01;
-      am[q] = sgn0<T>(aC[q]) * fmin(m01, m23);
+    if (pos_prod<T>(aL[q], aR[q])) {
+      // the selections of the forward min_abs(min_abs(2 aL, 2 aR), min_abs(aC, aG)),
+      // ties to the second operand
+      const T c0 = fabs(twice<T>(aL[q])), c1 = fabs(twice<T>(aR[q])), c2 = fabs(aC[q]), c3 = fabs(aG[q]);
+      const int s01 = nonneg_lt<T>(c0, c1) ? 0 : 1;
+      const T m01 = s01 == 0 ? c0 : c1;
+      const int s23 = nonneg_lt<T>(c2, c3) ? 2 : 3;
+      const T m23 = s23 == 2 ? c2 : c3;
+      const bool first = nonneg_lt<T>(m01, m23);
+      sel[q] = first ? s01 : s23;
+      am[q] = with_sign<T>(aC[q], first ? m01 : m23);
     }
   }
   eig_right<T>(E, am, dW);
@@ -396,7 +388,7 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
     gwm[q] += -gdL[q];
     gw0[q] += gdL[q] - gdR[q];
   }
-  eig_fields_vjp<T>(gamma, w0, bn, gE, gw0, gbn);
+  eig_fields_vjp<T>(gamma, w0, bn, E, gE, gw0, gbn);
 }
 
 // ------------------------------------------------------------- PPMC VJP --
@@ -630,7 +622,7 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, const T (*w)[7], T bn,
       gw[2][c] -= gd[c];
     }
   }
-  eig_fields_vjp<T>(gamma, w[2], bn, gE, gw[2], gbn);
+  eig_fields_vjp<T>(gamma, w[2], bn, E, gE, gw[2], gbn);
 }
 
 

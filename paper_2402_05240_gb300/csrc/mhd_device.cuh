@@ -295,6 +295,7 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
 // magnetosonic waves, 1/2 for the Alfven waves).
 template <class T> struct Eig {
   T rho, ir, sr, isr, a, a2, ia2, af, as, cf, cs, Qf, Qs, Af, As, b1, b2, sg;
+  T rcf;  // 1/c_f (for the reverse sweep)
 };
 
 // Square roots and divisions are folded into five reciprocal square roots
@@ -318,6 +319,7 @@ template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w
   const T sd = tsqrt<T>(D * D + T(4) * E.a2 * bt2);
   const T cf2 = T(0.5) * (E.a2 + b2 + sd);
   const T rcf = trsqrt<T>(cf2);
+  E.rcf = rcf;
   E.cf = cf2 * rcf;
   E.cs = E.a * fabs(bn) * E.isr * rcf;
   const T ibt = gt0<T>(bt2r) ? trsqrt<T>(bt2r) : T(0);
