@@ -116,7 +116,7 @@ Layout layout_of(const mhd_config& c) {
   L.flags = off;
   off += up(sizeof(unsigned));
   L.red = off;
-  off += up((9 + 9 * red_blocks((long long)Ni)) * sizeof(double));
+  off += up((9 + 17 * red_blocks((long long)Ni)) * sizeof(double));  // totals, partials, compensations
   L.Up = off;
   if (padded(c)) off += up(8 * N * sizeof(double));
   L.total = off;

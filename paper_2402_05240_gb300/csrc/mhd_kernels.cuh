@@ -614,15 +614,31 @@ __global__ void k_fill_ghosts(Grid gp, double* Up) {
 // ------------------------------------------------------------ diagnostics --
 // Per-block partial sums of the 8 fields and max |div B| over 1024 cells, then
 // one block combines the partials in a fixed order: deterministic results.
+// The sums are compensated: every partial carries the rounding error of its
+// additions (TwoSum, Knuth) beside its value and the two are added at the end
+// (pairwise summation with Neumaier-style error carrying), so the totals are
+// accurate to about one rounding of the result whatever the cell count.
 constexpr int DIAG_T = 1024;
 
+__device__ __forceinline__ void diag_add(double& s, double& c, double s2, double c2) {
+  const double t = s + s2;
+  const double v = t - s;
+  c += (s - (t - v)) + (s2 - v) + c2;
+  s = t;
+}
+
+// red layout: [9][nblk] partial values (sums of fields 0-7, max |div B|), then
+// [8][nblk] the compensations of the 8 sums
 __global__ void __launch_bounds__(DIAG_T) k_diag_partial(Grid g, const double* __restrict__ U, double* red, int nblk) {
   __shared__ double sh[DIAG_T / 32][9];
+  __shared__ double shc[DIAG_T / 32][8];
   const long long N = g.N;
   const long long c = (long long)blockIdx.x * DIAG_T + threadIdx.x;
-  double v[9];
+  double v[9], e[8];
 #pragma unroll
   for (int f = 0; f < 9; ++f) v[f] = 0.0;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) e[f] = 0.0;
   if (c < N) {
     const int i = (int)(c % g.n[0]);
     const int j = (int)((c / g.n[0]) % g.n[1]);
@@ -641,37 +657,62 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_partial(Grid g, const double* _
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int f = 0; f < 8; ++f) v[f] += __shfl_xor_sync(0xffffffffu, v[f], o);
+    for (int f = 0; f < 8; ++f) {
+      const double s2 = __shfl_xor_sync(0xffffffffu, v[f], o), c2 = __shfl_xor_sync(0xffffffffu, e[f], o);
+      diag_add(v[f], e[f], s2, c2);
+    }
     v[8] = fmax(v[8], __shfl_xor_sync(0xffffffffu, v[8], o));
   }
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
+  if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int f = 0; f < 9; ++f) sh[w][f] = v[f];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) shc[w][f] = e[f];
+  }
   __syncthreads();
   if (threadIdx.x < 9) {
     const int f = threadIdx.x;
-    double a = sh[0][f];
-    for (int q = 1; q < DIAG_T / 32; ++q) a = (f == 8) ? fmax(a, sh[q][f]) : a + sh[q][f];
+    double a = sh[0][f], ac = f < 8 ? shc[0][f] : 0.0;
+    for (int q = 1; q < DIAG_T / 32; ++q) {
+      if (f == 8)
+        a = fmax(a, sh[q][f]);
+      else
+        diag_add(a, ac, sh[q][f], shc[q][f]);
+    }
     red[(long long)f * nblk + blockIdx.x] = a;
+    if (f < 8) red[(long long)(9 + f) * nblk + blockIdx.x] = ac;
   }
 }
 
 __global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, double* out, int nblk) {
-  __shared__ double sh[DIAG_T];
+  __shared__ double sh[DIAG_T], shc[DIAG_T];
   for (int f = 0; f < 9; ++f) {
-    double a = 0.0;
+    double a = 0.0, ac = 0.0;
     for (int q = threadIdx.x; q < nblk; q += DIAG_T) {
       const double x = red_in[(long long)f * nblk + q];
-      a = (f == 8) ? fmax(a, x) : a + x;
+      if (f == 8)
+        a = fmax(a, x);
+      else
+        diag_add(a, ac, x, red_in[(long long)(9 + f) * nblk + q]);
     }
     sh[threadIdx.x] = a;
+    shc[threadIdx.x] = ac;
     __syncthreads();
     for (int o = DIAG_T / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] = (f == 8) ? fmax(sh[threadIdx.x], sh[threadIdx.x + o]) : sh[threadIdx.x] + sh[threadIdx.x + o];
+      if (threadIdx.x < o) {
+        if (f == 8) {
+          sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        } else {
+          double s1 = sh[threadIdx.x], c1 = shc[threadIdx.x];
+          diag_add(s1, c1, sh[threadIdx.x + o], shc[threadIdx.x + o]);
+          sh[threadIdx.x] = s1;
+          shc[threadIdx.x] = c1;
+        }
+      }
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[f] = sh[0];
+    if (threadIdx.x == 0) out[f] = f == 8 ? sh[0] : sh[0] + shc[0];
     __syncthreads();
   }
 }

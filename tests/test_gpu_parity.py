@@ -352,3 +352,25 @@ def test_zero_field(mhd, recon, precision, tol):
     sim.status()
     got = U.cpu().numpy()
     assert np.all(got[5:] == 0.0) and np.all(np.isfinite(got))
+
+
+def test_diagnostics_totals_are_compensated(mhd):
+    """The totals of the conservation diagnostics carry the rounding errors of
+    their additions: a field of +-2^52-sized values that cancel to ~1e5 is
+    summed to the exactly rounded total (math.fsum) within 1e-6, where plain
+    pairwise summation is off by ~100."""
+    n = (64, 32, 32)
+    N = n[0] * n[1] * n[2]
+    rng = np.random.default_rng(31)
+    b = rng.integers(-2 ** 52, 2 ** 52, size=N // 2).astype(np.float64)
+    x = np.concatenate([b, -b + rng.uniform(-1, 1, size=N // 2) * 1e3])
+    rng.shuffle(x)
+    U = turb(n, seed=3)
+    U[1] = x.reshape(U[1].shape)
+    sim = mhd.Sim(*n)
+    _, tot = sim.diagnostics(cuda(U))
+    ref = math.fsum(x)
+    assert abs(float(np.sum(x)) - ref) > 10.0  # the case defeats plain summation
+    assert abs(tot[1] - ref) <= 1e-6, (tot[1], ref)
+    for f in (0, 4, 5, 6, 7):
+        assert abs(tot[f] - math.fsum(U[f].ravel())) <= 1e-12 * math.fsum(np.abs(U[f]).ravel())
