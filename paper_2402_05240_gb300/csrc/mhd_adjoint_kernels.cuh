@@ -1,5 +1,8 @@
 // mhd_adjoint_kernels.cuh -- the reverse sweep of one VL+CT step (not in the
-// paper): gU^n = (dU^{n+1}/dU^n)^T gU^{n+1} at fixed dt.
+// paper): gU^n = (dU^{n+1}/dU^n)^T gU^{n+1} at fixed dt, and the terms that
+// make it the derivative of the step at the CFL dt of U^n (the dt cotangent
+// from the two update reverses, the derivative of Eq. dt at its maximising
+// cell).
 //
 // The forward intermediates are recomputed first (primitives W^n, predictor
 // fluxes F^n, half-step state, interface states and corrector fluxes F^{n+1/2},
