@@ -374,3 +374,25 @@ def test_diagnostics_totals_are_compensated(mhd):
     assert abs(tot[1] - ref) <= 1e-6, (tot[1], ref)
     for f in (0, 4, 5, 6, 7):
         assert abs(tot[f] - math.fsum(U[f].ravel())) <= 1e-12 * math.fsum(np.abs(U[f]).ravel())
+
+
+def test_full_size_512_ppmc_sampled(mhd):
+    """512^3 turbulent box with PPMC (the precision comparison's workload):
+    one GPU step checked against the oracle at sampled cells."""
+    n = (512, 512, 512)
+    U0 = I.turbulent_box(I.Box(*n), seed_v=1, seed_b=2)
+    sim = mhd.Sim(*n, cfl=0.3, recon="ppmc")
+    U = cuda(U0)
+    dt = sim.dt(U)
+    sim.step(U, dt)
+    torch.cuda.synchronize()
+    sim.status()
+    rng = np.random.default_rng(7)
+    cells = [tuple(int(x) for x in rng.integers(0, 512, 3)) for _ in range(12)] + [(0, 0, 0), (511, 511, 511)]
+    idx = tuple(torch.tensor(v, device="cuda") for v in zip(*cells))
+    got = U[:, idx[0], idx[1], idx[2]].cpu().numpy()
+    del U, sim
+    for m, c in enumerate(cells):
+        ref = _subbox_step(U0, c, dt, "ppmc")
+        scale = np.abs(ref) + np.array([1, 1, 1, 1, 1, 0.5, 0.5, 0.5])
+        assert np.all(np.abs(got[:, m] - ref) <= 1e-12 * scale), (c, got[:, m] - ref)
