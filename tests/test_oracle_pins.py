@@ -600,3 +600,29 @@ def test_step_cfl_jvp_matches_central_difference():
     assert np.max(np.abs(fd - JV)) / scale < 1e-6
     _, J0 = orc.step_jvp(U, d, dt)
     assert np.max(np.abs(JV - J0)) / scale > 1e-3
+
+
+def test_floors_raise_density_and_reset_energy():
+    """End-of-step floors (reading D-12): a cell whose density is below
+    rho_floor after the update holds rho_floor exactly; a cell whose
+    recovered pressure is below p_floor has its energy reset so that the
+    pressure is p_floor; each is counted once.  (A vanishing dt leaves every
+    other cell as it was.)"""
+    n = 8
+    box = I.Box(n, n, n)
+    rf, pf = 1e-3, 1e-4
+    rho = np.full(box.shape, 1.0)
+    pres = np.full(box.shape, 1.0)
+    rho[2, 3, 4] = 1e-6
+    pres[5, 6, 1] = 1e-7
+    U = I.assemble(box, rho, (0.1, -0.2, 0.05), pres, (0.3, 0.2, -0.1))
+    orc = O.Oracle(n, n, n, rho_floor=rf, p_floor=pf)
+    orc.floor_counts[0] = orc.floor_counts[1] = 0
+    V = orc.step(U, 1e-14)
+    assert V[0, 2, 3, 4] == rf
+    assert list(orc.floor_counts) == [1, 1]
+    W = O.Oracle(n, n, n, rho_floor=1e-30, p_floor=-1e30).primitives(V)
+    assert abs(W[4, 5, 6, 1] - pf) <= 1e-12 * pf + 1e-14
+    mask = np.ones(box.shape, bool)
+    mask[2, 3, 4] = mask[5, 6, 1] = False
+    assert np.max(np.abs(V[:, mask] - U[:, mask])) < 1e-9
