@@ -626,3 +626,19 @@ def test_floors_raise_density_and_reset_energy():
     mask = np.ones(box.shape, bool)
     mask[2, 3, 4] = mask[5, 6, 1] = False
     assert np.max(np.abs(V[:, mask] - U[:, mask])) < 1e-9
+
+
+def test_diagnostics_divergence_and_totals():
+    """max |div B| of a face field with a known discrete divergence (B_x
+    growing linearly in x: a everywhere but at the periodic seam, where the
+    jump gives a (1 - n)), and the field totals against math.fsum."""
+    nx, ny, nz = 12, 5, 7
+    box = I.Box(nx, ny, nz)
+    a = 0.37
+    bx = np.broadcast_to(a * (np.arange(nx) + 1) / nx, box.shape).copy()
+    U = I.assemble(box, np.full(box.shape, 1.0), (0.1, 0.2, 0.3), np.full(box.shape, 1.0),
+                   (bx, np.zeros(box.shape), np.zeros(box.shape)))
+    dmax, tot = O.Oracle(nx, ny, nz).diagnostics(U)
+    assert abs(dmax - a * (nx - 1)) <= 1e-12 * a * nx
+    for f in range(8):
+        assert abs(tot[f] - math.fsum(U[f].ravel())) <= 1e-13 * max(math.fsum(np.abs(U[f]).ravel()), 1.0)
