@@ -14,7 +14,8 @@ timed region.  One process per GPU; ranks run independent replicas (weak
 scaling, no data-path collective).
 
 --impl reference times the CPU oracle (the plain FP64 reference) on the
-host cores on a bounded sample of the same recipe (128^3 per step).
+host cores on a bounded sample of the same recipe (--ref-n, 96^3 per step by
+default).
 """
 from __future__ import annotations
 

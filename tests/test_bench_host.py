@@ -1,0 +1,60 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic bytes per cell of
+each stage and the roofline arithmetic of the reported JSON line."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+LAUNCHES = {"prim": 1, "flux_pcm": 3, "emf": 2, "update_half": 1, "recon": 3, "flux_hlld": 3, "update_full": 1}
+
+
+def test_counted_bytes_per_step(bench):
+    """2400 B/cell per FP64 (or double-float) step, 1340 B/cell FP32-bulk."""
+    for T, total in ((8, 2400), (4, 1340)):
+        sb = bench.stage_bytes(T)
+        assert sum(sb[k] * n for k, n in LAUNCHES.items()) == total
+
+
+def _prof(ms_per_launch, steps):
+    return {k: (ms_per_launch[k] * n * steps, n * steps) for k, n in LAUNCHES.items()} | {"dt": (0.01, steps)}
+
+
+def test_roofline_of_a_counted_stage(bench):
+    """The dominant stage with ncu counters: FP64-pipe operations per launch
+    over the live launch time against 601.3 G op/s; traffic = ncu DRAM bytes
+    per cell x cells; the HBM views of the stage and of the step."""
+    n3 = 256 ** 3
+    ms = {"prim": 3.5, "flux_pcm": 7.7, "emf": 3.0, "update_half": 2.8, "recon": 10.9, "flux_hlld": 7.7,
+          "update_full": 1.5}
+    r = bench.roofline_of(_prof(ms, 10), "fp64", n3, 6791.4, "measured", "plmc")
+    assert r["kernel"] == "recon" and r["bound"] == "alu"
+    ops, flop, winst, dram = bench.COUNTERS["fp64"]["recon"]
+    assert r["fp64_pipe"]["achieved"] == pytest.approx(ops * n3 / 10.9e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(max(r["fp64_pipe"]["frac"], r["issue"]["frac"]), rel=1e-9)
+    assert r["traffic"] == round(dram * n3)
+    assert r["hbm"]["achieved"] == pytest.approx(176 * n3 / 10.9e-3 / 1e9, rel=1e-3)
+    step_s = sum(ms[k] * n for k, n in LAUNCHES.items()) * 1e-3 + 0.001e-3
+    assert r["step_hbm"]["frac_counted"] == pytest.approx(n3 / step_s * 2400 / 1e9 / 6791.4, rel=1e-3)
+    assert sum(r["stage_share"].values()) == pytest.approx(1.0, abs=1e-3)
+
+
+def test_roofline_without_counters_is_hbm_bound(bench):
+    """PPMC has no counters: the dominant stage is reported against HBM with
+    no traffic figure."""
+    n3 = 128 ** 3
+    ms = {"prim": 0.5, "flux_pcm": 1.0, "emf": 0.4, "update_half": 0.4, "recon": 2.4, "flux_hlld": 1.0,
+          "update_full": 0.2}
+    r = bench.roofline_of(_prof(ms, 2), "fp64", n3, 6791.4, "measured", "ppmc")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+    assert r["frac"] == pytest.approx(176 * n3 / 2.4e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
