@@ -91,14 +91,26 @@ typedef struct mhd_config {
 
 typedef struct mhd_ctx mhd_ctx; /* opaque; owns the workspace */
 
-/* Bytes of device workspace mhd_init will allocate for cfg. */
+/* Library infrastructure, not in the paper.  *bytes receives the device
+ * workspace mhd_init allocates for cfg (primitives, fluxes, edge fields,
+ * reconstructed states, scratch of the reductions; sized for the compute
+ * type of cfg->precision).  No device work.  Errors: MHD_ERR_ARG (cfg or
+ * bytes NULL, or cfg invalid). */
 int mhd_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
-/* Create a context for cfg on the current CUDA device; stream is a
- * cudaStream_t (NULL = default stream).  Allocates the workspace. */
+/* Library infrastructure, not in the paper.  Creates a context for cfg on
+ * the current CUDA device; stream is a cudaStream_t (NULL = default stream)
+ * that every later call on the context uses.  Allocates and zeroes the
+ * workspace (mhd_workspace_bytes) and synchronises the stream.  *out
+ * receives the context (owned by the caller, freed by mhd_destroy), or NULL
+ * on error.  Errors: MHD_ERR_ARG (out or cfg NULL, cfg invalid),
+ * MHD_ERR_OOM (host or device allocation failed), MHD_ERR_CUDA. */
 int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream);
 
-/* Free the workspace and the context (NULL is ignored). */
+/* Library infrastructure, not in the paper.  Synchronises the context's
+ * stream, then frees the workspace, the adjoint workspace, the device copy
+ * used by mhd_run_host, the profiling events and the context itself; the
+ * stream is the caller's and is not destroyed.  NULL is ignored. */
 void mhd_destroy(mhd_ctx* ctx);
 
 /* Step 1, Eq. dt: dt = C_CFL * min over cells and directions l of
@@ -149,9 +161,15 @@ int mhd_dt_sub(mhd_ctx* ctx, const double* Ug_dev, const int gn[3], const int of
  * state then holds the step that raised them. */
 int mhd_evolve(mhd_ctx* ctx, double* U_dev, double t_end, int max_steps, double* t_host, int* steps_host);
 
-/* As mhd_run on a HOST state: copies U_host to a device buffer owned by the
- * context, runs nsteps, copies the result back and synchronises.  *t_host
- * (may be NULL) receives the simulated time advanced. */
+/* Steps 1-9 (Sec. 2.2) as in mhd_run, on a HOST state (not in the paper:
+ * the end-to-end form that includes the host<->device copies).  U_host
+ * (8 x N doubles, layout as U_dev; pinned memory for full copy bandwidth):
+ * copied to a device buffer the context allocates on the first call and
+ * keeps, stepped nsteps times in place, copied back; synchronous.  *t_host
+ * (may be NULL) receives the simulated time advanced (the sum of the dt
+ * values).  Errors: MHD_ERR_ARG (ctx or U_host NULL, nsteps < 0, a
+ * subdomain context), MHD_ERR_OOM, MHD_ERR_CUDA, then the device flags as
+ * mhd_status returns them. */
 int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
 
 /* Vector-Jacobian product of one mhd_step at fixed dt (not in the paper):
@@ -177,10 +195,13 @@ int mhd_adjoint_step(mhd_ctx* ctx, const double* U_n_dev, double dt, const doubl
 int mhd_adjoint_step_cfl(mhd_ctx* ctx, const double* U_n_dev, const double* gU_np1_dev, double* gU_n_dev,
                          double* dt_host, double* g_dt_host);
 
-/* Bytes of device memory the first mhd_adjoint_step call allocates (once per
- * context, freed by mhd_destroy): forward intermediates of one step plus
- * cotangent buffers, 197 words of the compute type (a float pair for
- * MHD_FP64_DF) + 10 doubles per cell. */
+/* Library infrastructure of the adjoint (not in the paper).  *bytes
+ * receives the device memory the first mhd_adjoint_step or
+ * mhd_adjoint_step_cfl call allocates (once per context, freed by
+ * mhd_destroy): forward intermediates of one step plus cotangent buffers,
+ * 197 words of the compute type (a float pair for MHD_FP64_DF) + 10
+ * doubles per cell, plus the partials of the CFL reduction.  No device
+ * work.  Errors: MHD_ERR_ARG (cfg or bytes NULL, or cfg invalid). */
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
 /* Diagnostics of a state (Sec. 3, div B at round-off): max over cells of
@@ -208,18 +229,28 @@ int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, do
 int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev, void* stream, double* divb_max_host,
                            double totals_host[8]);
 
-/* Synchronise and read the device flags raised since the last call;
- * counts_host[0..1] (may be NULL) receive the density / pressure floor
- * triggers of the full updates since the last call.  Returns MHD_OK or
- * MHD_ERR_NONFINITE. */
+/* Library infrastructure, not in the paper.  Synchronises the context's
+ * stream and reads the device flags raised since the last call, then clears
+ * them; counts_host[0..1] (may be NULL) receive the density / pressure
+ * floor triggers (Sec. 2.2 floors, reading D-12) of the full updates since
+ * the last call, then reset.  Returns MHD_ERR_NONFINITE (a non-finite value
+ * or a non-positive density was seen), else MHD_ERR_DT (a device dt that
+ * was not positive and finite), else MHD_OK; MHD_ERR_ARG for a NULL ctx,
+ * MHD_ERR_CUDA if the stream failed. */
 int mhd_status(mhd_ctx* ctx, long long counts_host[2]);
 
-/* Synchronise and read the density / pressure floor triggers (D-12) since
- * the last call of this function or of mhd_status, then reset them; the
- * error flags are left for mhd_status. */
+/* The density / pressure floors of the full update (Sec. 2.2, reading
+ * D-12: cells whose density or pressure fell below cfg.rho_floor /
+ * cfg.p_floor and were reset).  Synchronises the context's stream;
+ * *n_rho_host and *n_p_host (each may be NULL) receive the triggers since
+ * the last call of this function or of mhd_status, which are then reset;
+ * the error flags are left for mhd_status.  Errors: MHD_ERR_ARG (NULL
+ * ctx), MHD_ERR_CUDA. */
 int mhd_floor_count(mhd_ctx* ctx, long long* n_rho_host, long long* n_p_host);
 
-/* Static message for a status code. */
+/* Library infrastructure, not in the paper.  A static, NUL-terminated
+ * English message for a status code ("unknown status" for codes the library
+ * does not return); never NULL, never to be freed. */
 const char* mhd_strerror(int code);
 
 /* ---- tracing: per-stage CUDA-event timing -----------------------------
@@ -237,8 +268,20 @@ const char* mhd_strerror(int code);
 #define MHD_STAGE_DT 7          /* dt finalisation                            */
 #define MHD_NUM_STAGES 8
 
+/* Library infrastructure, not in the paper.  Synchronises the context's
+ * stream, turns the per-stage timing on (on != 0) or off and clears what
+ * was recorded.  Errors: MHD_ERR_ARG (NULL ctx), MHD_ERR_CUDA. */
 int mhd_profile_enable(mhd_ctx* ctx, int on);
+
+/* Library infrastructure, not in the paper.  Synchronises the context's
+ * stream; ms_host[s] receives the summed device milliseconds and
+ * launches_host[s] the launch count of stage s since the last enable or
+ * read (both zero with profiling off); the record is then cleared.
+ * Errors: MHD_ERR_ARG (a NULL argument), MHD_ERR_CUDA. */
 int mhd_profile_read(mhd_ctx* ctx, double ms_host[MHD_NUM_STAGES], long long launches_host[MHD_NUM_STAGES]);
+
+/* Library infrastructure, not in the paper.  A static short name of a stage
+ * id ("prim", "flux_pcm", ...; "unknown" out of range); never NULL. */
 const char* mhd_stage_name(int stage);
 
 /* ---- per-stage entry points (for stage-by-stage parity checks) ---------
