@@ -371,6 +371,53 @@ def test_ppmc_keeps_smooth_extrema_at_fourth_order():
     assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8, errs
 
 
+@pytest.mark.parametrize("case", ["interface_C", "extremum_C", "sign_and_overshoot"])
+def test_ppmc_limiter_worked_examples(case):
+    """Hand-worked values of the PPMC limiters (Sec. 2.2.6; Colella & Sekora
+    2008 interface limiter with C = 1.25, McCorquodale & Colella 2011 cell
+    limiter, as read in D-11) on an entropy mode: only rho varies, so the
+    one characteristic field with a density entry carries q = rho - 3 and the
+    limiter acts on q itself.  Five cells q_{i-2..i+2} decide cell i's faces;
+    the values were derived by hand, exact in binary where stated.
+
+    interface_C: q = (-1, 0, 1, 1.25, 0).  Upper interface: 7/12 (1 + 1.25) =
+    1.3125 lies above 1.25, so it is limited with d2c = (0 - 1 - 1.25 + 0)/2 =
+    -1.125, neighbour curvatures -0.75 and -1.5: min(1.125, 1.25*0.75,
+    1.25*1.5) = 0.9375, value 1.125 + 0.9375/6 = 1.28125 (C = 1 would give
+    1.25, C = 2 leaves 1.3125).  Lower interface 7/12 - 0.25/12 = 0.5625 is
+    inside [0, 1].  The cell is monotone and neither deviation (0.4375,
+    0.28125) reaches twice the other, so the faces stay 0.5625 / 1.28125.
+
+    extremum_C: q = (0.625, 0.875, 1, 0.875, 0.625), a maximum.  Both
+    interfaces 7/12 * 1.875 - 1.5/12 = 0.96875 (inside their cells' range);
+    d2f = 6 (2 * 0.96875 - 2) = -0.375, curvatures -0.125, -0.25, -0.125:
+    r = min(0.375, 1.25 * 0.125, ...) / 0.375 = 5/12, so both faces are
+    1 - (5/12) * 0.03125 = 379/384 (C = 1: 1 - 1/96, C = 2: 1 - 1/48).
+
+    sign_and_overshoot: q = (0, 0.125, 0.25, 1.5, 1.625).  Lower interface
+    7/12 * 0.375 - 1.5/12 = 0.09375 falls below 0.125; its left curvature
+    0 - 0.25 + 0.25 is exactly 0, so the limited curvature is 0 and the value
+    is the mean 0.1875.  Upper interface 6/12 * 1.75 = 0.875.  The cell is
+    monotone and 0.625 >= 2 * 0.0625, so the upper face is clipped to
+    0.25 + 2 * 0.0625 = 0.375."""
+    pattern, wr_q, wl_q = {
+        "interface_C": ((-1.0, 0.0, 1.0, 1.25, 0.0), 0.5625, 1.28125),
+        "extremum_C": ((0.625, 0.875, 1.0, 0.875, 0.625), 379 / 384, 379 / 384),
+        "sign_and_overshoot": ((0.0, 0.125, 0.25, 1.5, 1.625), 0.1875, 0.375),
+    }[case]
+    n, i = 16, 7
+    q = np.zeros(n)
+    q[i - 2:i + 3] = pattern
+    box = I.Box(n, 4, 4)
+    U = _wave_state(box, lambda _x: 3.0 + q)
+    WL, WR = O.Oracle(n, 4, 4, recon="ppmc").recon(U, 0)
+    assert abs(WR[0, 0, 0, i] - (3.0 + wr_q)) < 1e-13, (WR[0, 0, 0, i], 3.0 + wr_q)
+    assert abs(WL[0, 0, 0, i] - (3.0 + wl_q)) < 1e-13, (WL[0, 0, 0, i], 3.0 + wl_q)
+    # the other fields carry no deviation (P, v, B uniform)
+    np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(WR[1:, 0, 0, i], WR[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
+
+
 @pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 @pytest.mark.parametrize("profile", ["step", "tanh"])
 def test_recon_creates_no_new_extrema(profile, recon):
