@@ -288,6 +288,29 @@ def test_plmc_linear_entropy_profile_gives_centred_slope():
         np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("recon", ["plmc", "plm_prim"])
+@pytest.mark.parametrize("cells", [(3.0, 4.0, 4.25), (5.0, 4.5, 2.5)])
+def test_plm_single_field_slope_is_van_leer(recon, cells):
+    """Sec. 2.2.6, Eq. limiter: the slope is sgn(d_C) min(2|d_L|, 2|d_R|,
+    |d_C|, |d_G|) with d_G the van Leer difference 2 d_L d_R / (d_L + d_R).
+    For data in one characteristic field (rho only) the harmonic mean d_G is
+    never above 2 min(|d_L|, |d_R|) nor above |d_C|, so the slope is d_G
+    itself.  (3, 4, 4.25): d_L = 1, d_R = 0.25, slope 0.5/1.25 = 0.4, faces
+    4 -+ 0.2 (minmod would give 0.25, MC 0.5, centred 0.625).
+    (5, 4.5, 2.5): d_L = -0.5, d_R = -2, slope 2/(-2.5) = -0.8, faces
+    4.5 -+ (-0.4)."""
+    n, i = 16, 7
+    rho = np.full(n, cells[1])
+    rho[i - 1:i + 2] = cells
+    box = I.Box(n, 4, 4)
+    U = _wave_state(box, lambda _x: rho)
+    WL, WR = O.Oracle(n, 4, 4, recon=recon).recon(U, 0)
+    slope = {(3.0, 4.0, 4.25): 0.4, (5.0, 4.5, 2.5): -0.8}[cells]  # worked above
+    assert abs(WL[0, 0, 0, i] - (cells[1] + 0.5 * slope)) < 1e-14
+    assert abs(WR[0, 0, 0, i] - (cells[1] - 0.5 * slope)) < 1e-14
+    np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
+
+
 @pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 def test_recon_flat_at_extremum(recon):
     """A local extremum of the cell averages gets no slope (Eq. limiter; MC11)."""
