@@ -32,6 +32,25 @@ def test_header_declares_the_step_api():
         assert required in names
 
 
+def test_every_entry_point_is_documented():
+    """Each declaration in include/*.h has its own comment directly above it
+    that either cites the passage it computes (Sec., Eq., Step or a reading
+    D-n) or states that the paper has no counterpart."""
+    cite = re.compile(r"Sec\.|Eq\.|Steps? \d|D-\d+|not in the paper|paper has no counterpart")
+    seen = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        for m in re.finditer(r"^(?:int|void|const char\*)\s+\**(mhd_\w+)\s*\(", txt, flags=re.M):
+            before = txt[:m.start()].rstrip()
+            assert before.endswith("*/"), f"{h}: {m.group(1)} has no comment directly above it"
+            comment = re.sub(r"\s*\n\s*\*?\s*", " ", before[before.rfind("/*"):])
+            assert cite.search(comment), f"{h}: {m.group(1)} cites no passage: {comment[:120]}"
+            seen.add(m.group(1))
+    assert seen == set(declared_functions())
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
