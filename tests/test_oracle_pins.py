@@ -180,6 +180,51 @@ def test_hlld_reduces_to_hllc_without_field():
         np.testing.assert_allclose(O.hlld(G, wl, wr, 0.0), hllc_toro(wl, wr), rtol=1e-13, atol=1e-13)
 
 
+def hllc_total_pressure(wl, wr, gamma=G):
+    """B_n = 0: the magnetic field only adds the pressure B_t^2/2 and is carried
+    with the gas (B_t / rho is advected), so the Riemann fan is two fast waves
+    around a contact.  Toro's HLLC (Sec. 10.4) with the total pressure
+    p + B_t^2/2, the fast speed sqrt((gamma p + B_t^2)/rho) in the outer
+    estimates, and B_t scaled like rho across each outer wave."""
+    def fast(w):
+        return math.sqrt((gamma * w[4] + w[5] ** 2 + w[6] ** 2) / w[0])
+    SL = min(wl[1], wr[1]) - max(fast(wl), fast(wr))
+    SR = max(wl[1], wr[1]) + max(fast(wl), fast(wr))
+    FL, FR = physical_flux(wl, 0.0), physical_flux(wr, 0.0)
+    UL, UR = cons(wl, 0.0), cons(wr, 0.0)
+    if SL >= 0:
+        return FL
+    if SR <= 0:
+        return FR
+
+    def ptot(w):
+        return w[4] + 0.5 * (w[5] ** 2 + w[6] ** 2)
+    rl, ul, rr, ur = wl[0], wl[1], wr[0], wr[1]
+    Ss = (ptot(wr) - ptot(wl) + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur))
+
+    def ustar(w, U, S):
+        r, u = w[0], w[1]
+        fac = r * (S - u) / (S - Ss)
+        e = U[4] / r + (Ss - u) * (Ss + ptot(w) / (r * (S - u)))
+        return fac * np.array([1.0, Ss, w[2], w[3], e, w[5] / r, w[6] / r])
+
+    if Ss >= 0:
+        return FL + SL * (ustar(wl, UL, SL) - UL)
+    return FR + SR * (ustar(wr, UR, SR) - UR)
+
+
+def test_hlld_reduces_to_hllc_with_total_pressure_when_bn_is_zero():
+    """Miyoshi & Kusano's HLLD with B_n = 0: the Alfven waves S*_{L,R} =
+    S_M -+ |B_n| / sqrt(rho*) fall onto the contact, the double-star states
+    vanish, and the flux is the total-pressure HLLC above (transverse fields
+    nonzero, unlike the B = 0 case)."""
+    rng = np.random.default_rng(15)
+    for _ in range(200):
+        wl, _ = rand_state(rng)
+        wr, _ = rand_state(rng)
+        np.testing.assert_allclose(O.hlld(G, wl, wr, 0.0), hllc_total_pressure(wl, wr), rtol=1e-12, atol=1e-12)
+
+
 def test_hlld_stationary_contact_exact():
     """An isolated stationary contact (u = 0, equal P and B, density jump) has zero mass flux."""
     wl = np.array([2.0, 0.0, 0.3, -0.2, 1.0, 0.4, 0.7])
