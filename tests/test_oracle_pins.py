@@ -245,6 +245,28 @@ def test_hlld_rotational_discontinuity_exact():
     np.testing.assert_allclose(O.hlld(G, wl, wr, 1.0), physical_flux(wl, 1.0), atol=1e-14)
 
 
+@pytest.mark.parametrize("V", [0.5, -0.5, 0.9, -0.9])
+@pytest.mark.parametrize("family", ["right", "left"])
+def test_hlld_moving_rotational_discontinuity_exact(family, V):
+    """Miyoshi & Kusano: HLLD resolves an isolated rotational discontinuity
+    exactly.  The stationary one above, boosted by V along x (the equations
+    are Galilean invariant; B is unchanged), moves at V: the states satisfy
+    F(U_L) - F(U_R) = V (U_L - U_R), and the exact flux at x/t = 0 is F(U_L)
+    for V > 0 and F(U_R) for V < 0.  "right" is the wave S*_R (u = -1, B_n =
+    1); "left" its mirror image, the wave S*_L (u = 1, B_n = -1)."""
+    if family == "right":
+        wl = np.array([1.0, -1.0 + V, 0.0, 0.0, 1.0, 1.0, 0.0])
+        wr = np.array([1.0, -1.0 + V, 1.0, -1.0, 1.0, 0.0, 1.0])
+        bn = 1.0
+    else:
+        wl = np.array([1.0, 1.0 + V, 1.0, -1.0, 1.0, 0.0, 1.0])
+        wr = np.array([1.0, 1.0 + V, 0.0, 0.0, 1.0, 1.0, 0.0])
+        bn = -1.0
+    fl, fr = physical_flux(wl, bn), physical_flux(wr, bn)
+    np.testing.assert_allclose(fl - fr, V * (cons(wl, bn) - cons(wr, bn)), atol=1e-15)
+    np.testing.assert_allclose(O.hlld(G, wl, wr, bn), fl if V > 0 else fr, atol=1e-14)
+
+
 def test_hlld_mirror_symmetry():
     """x -> -x maps (u, B_n) -> (-u, -B_n) and swaps the states; the flux
     components odd under the reflection change sign."""
