@@ -235,6 +235,19 @@ def test_hlld_stationary_contact_exact():
         np.testing.assert_allclose(f, physical_flux(wr, bn), atol=1e-15)
 
 
+@pytest.mark.parametrize("V", [0.3, -0.3, 0.05, -0.05])
+def test_hlld_moving_contact_exact(V):
+    """The stationary contact boosted by V along x moves at V (F(U_L) - F(U_R)
+    = V (U_L - U_R)); HLLD resolves it exactly, with or without a normal
+    field: the flux at x/t = 0 is F(U_L) for V > 0 and F(U_R) for V < 0."""
+    wl = np.array([2.0, V, 0.3, -0.2, 1.0, 0.4, 0.7])
+    wr = np.array([0.5, V, 0.3, -0.2, 1.0, 0.4, 0.7])
+    for bn in (0.0, 0.9, -1.3):
+        fl, fr = physical_flux(wl, bn), physical_flux(wr, bn)
+        np.testing.assert_allclose(fl - fr, V * (cons(wl, bn) - cons(wr, bn)), atol=1e-15)
+        np.testing.assert_allclose(O.hlld(G, wl, wr, bn), fl if V > 0 else fr, atol=1e-14)
+
+
 def test_hlld_rotational_discontinuity_exact():
     """An isolated stationary rotational discontinuity: rho = P = B_n = 1, u = -1,
     B_t (1,0) -> (0,1), v_t (0,0) -> (1,-1) satisfies the jump conditions, so
