@@ -95,9 +95,42 @@ def _check(code, where):
         raise MHDError(code, where)
 
 
-def _ptr(t: torch.Tensor):
-    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous(), "float64 contiguous CUDA tensor expected"
+# Cells and device of every live context (recorded by mhd_init, dropped by
+# mhd_destroy).  The library takes raw pointers and cannot see buffer sizes,
+# so the binding checks each buffer against its context before the call.
+_CTX = {}
+
+
+def _ptr(t: torch.Tensor, numel: int | None = None, name: str = "tensor", cuda: bool = True,
+         device: int | None = None):
+    """Address of a float64 contiguous tensor with at least ``numel``
+    elements, on the GPU ``device`` (any GPU if None) or, with cuda=False, in
+    host memory.  Raises TypeError / ValueError otherwise."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: torch.Tensor expected, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name}: float64 expected, got {t.dtype}")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{name}: {'CUDA' if cuda else 'host'} tensor expected, got one on {t.device}")
+    if cuda and device is not None and t.device.index != device:
+        raise ValueError(f"{name}: on {t.device}, the context lives on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: contiguous tensor expected")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {numel} needed")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _cells(ctx):
+    """(cells, device) of a context made by mhd_init, else (None, None)."""
+    v = ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx
+    return _CTX.get(v, (None, None))
+
+
+def _field(ctx, t, fields: int, name: str):
+    """_ptr for a [fields][N] array of the context's grid."""
+    n, dev = _cells(ctx)
+    return _ptr(t, None if n is None else fields * n, name, device=dev)
 
 
 # ---- C ABI, same names --------------------------------------------------
@@ -111,26 +144,28 @@ def mhd_init(cfg: mhd_config, stream=None):
     ctx = ctypes.c_void_p(0)
     s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
     _check(LIB.mhd_init(ctypes.byref(ctx), ctypes.byref(cfg), s), "mhd_init")
+    _CTX[ctx.value] = (cfg.nx * cfg.ny * cfg.nz, torch.cuda.current_device())
     return ctx
 
 
 def mhd_destroy(ctx):
+    _CTX.pop(ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx, None)
     LIB.mhd_destroy(ctx)
 
 
 def mhd_dt(ctx, U: torch.Tensor) -> float:
     v = ctypes.c_double(0)
-    _check(LIB.mhd_dt(ctx, _ptr(U), ctypes.byref(v)), "mhd_dt")
+    _check(LIB.mhd_dt(ctx, _field(ctx, U, 8, "U"), ctypes.byref(v)), "mhd_dt")
     return v.value
 
 
 def mhd_step(ctx, U: torch.Tensor, dt: float, want_next_dt: bool = False):
     """One step at dt in place; with want_next_dt, returns the CFL dt of the new state (synchronises)."""
     if not want_next_dt:
-        _check(LIB.mhd_step(ctx, _ptr(U), float(dt), None), "mhd_step")
+        _check(LIB.mhd_step(ctx, _field(ctx, U, 8, "U"), float(dt), None), "mhd_step")
         return None
     v = ctypes.c_double(0)
-    _check(LIB.mhd_step(ctx, _ptr(U), float(dt), ctypes.byref(v)), "mhd_step")
+    _check(LIB.mhd_step(ctx, _field(ctx, U, 8, "U"), float(dt), ctypes.byref(v)), "mhd_step")
     return v.value
 
 
@@ -142,49 +177,65 @@ def mhd_floor_count(ctx):
 
 
 def mhd_run(ctx, U: torch.Tensor, nsteps: int, dt_log: torch.Tensor | None = None):
-    p = _ptr(dt_log) if dt_log is not None else ctypes.c_void_p(0)
-    _check(LIB.mhd_run(ctx, _ptr(U), int(nsteps), p), "mhd_run")
+    p = ctypes.c_void_p(0)
+    if dt_log is not None:
+        p = _ptr(dt_log, max(int(nsteps), 0), "dt_log", device=_cells(ctx)[1])
+    _check(LIB.mhd_run(ctx, _field(ctx, U, 8, "U"), int(nsteps), p), "mhd_run")
 
 
 def mhd_evolve(ctx, U: torch.Tensor, t_end: float, max_steps: int = 1 << 30):
     """Advance U in place to t_end; returns (time reached, steps taken)."""
     t = ctypes.c_double(0)
     n = ctypes.c_int(0)
-    _check(LIB.mhd_evolve(ctx, _ptr(U), float(t_end), int(max_steps), ctypes.byref(t), ctypes.byref(n)), "mhd_evolve")
+    _check(LIB.mhd_evolve(ctx, _field(ctx, U, 8, "U"), float(t_end), int(max_steps), ctypes.byref(t), ctypes.byref(n)), "mhd_evolve")
     return t.value, n.value
+
+
+def _sub_dims(Ug):
+    """gn = (gnx, gny, gnz) of a [8, gnz, gny, gnx] state."""
+    if not isinstance(Ug, torch.Tensor) or Ug.dim() != 4 or Ug.shape[0] != 8:
+        raise ValueError("Ug: a [8, gnz, gny, gnx] tensor expected")
+    return (ctypes.c_int * 3)(Ug.shape[3], Ug.shape[2], Ug.shape[1])
 
 
 def mhd_step_sub(ctx, Ug: torch.Tensor, offset, dt: float, Ug_out: torch.Tensor):
     """One step of a subdomain: Ug is [8, gnz, gny, gnx] holding it at
     offset (ox, oy, oz) with its halo; its new interior goes to Ug_out."""
-    gn = (ctypes.c_int * 3)(Ug.shape[3], Ug.shape[2], Ug.shape[1])
+    gn = _sub_dims(Ug)
+    if not isinstance(Ug_out, torch.Tensor) or Ug_out.shape != Ug.shape:
+        raise ValueError("Ug_out: same shape as Ug expected")
     off = (ctypes.c_int * 3)(*[int(o) for o in offset])
-    _check(LIB.mhd_step_sub(ctx, _ptr(Ug), gn, off, float(dt), _ptr(Ug_out)), "mhd_step_sub")
+    dev = _cells(ctx)[1]
+    _check(LIB.mhd_step_sub(ctx, _ptr(Ug, name="Ug", device=dev), gn, off, float(dt),
+                            _ptr(Ug_out, name="Ug_out", device=dev)), "mhd_step_sub")
 
 
 def mhd_dt_sub(ctx, Ug: torch.Tensor, offset) -> float:
-    gn = (ctypes.c_int * 3)(Ug.shape[3], Ug.shape[2], Ug.shape[1])
+    gn = _sub_dims(Ug)
     off = (ctypes.c_int * 3)(*[int(o) for o in offset])
     v = ctypes.c_double(0)
-    _check(LIB.mhd_dt_sub(ctx, _ptr(Ug), gn, off, ctypes.byref(v)), "mhd_dt_sub")
+    _check(LIB.mhd_dt_sub(ctx, _ptr(Ug, name="Ug", device=_cells(ctx)[1]), gn, off, ctypes.byref(v)), "mhd_dt_sub")
     return v.value
 
 
 def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:
-    assert U_host.dtype == torch.float64 and not U_host.is_cuda and U_host.is_contiguous()
+    n = _cells(ctx)[0]
+    p = _ptr(U_host, None if n is None else 8 * n, "U_host", cuda=False)
     t = ctypes.c_double(0)
-    _check(LIB.mhd_run_host(ctx, ctypes.c_void_p(U_host.data_ptr()), int(nsteps), ctypes.byref(t)), "mhd_run_host")
+    _check(LIB.mhd_run_host(ctx, p, int(nsteps), ctypes.byref(t)), "mhd_run_host")
     return t.value
 
 
 def mhd_adjoint_step(ctx, U_n: torch.Tensor, dt: float, gU_np1: torch.Tensor, gU_n: torch.Tensor):
-    _check(LIB.mhd_adjoint_step(ctx, _ptr(U_n), float(dt), _ptr(gU_np1), _ptr(gU_n)), "mhd_adjoint_step")
+    _check(LIB.mhd_adjoint_step(ctx, _field(ctx, U_n, 8, "U_n"), float(dt), _field(ctx, gU_np1, 8, "gU_np1"),
+                                _field(ctx, gU_n, 8, "gU_n")), "mhd_adjoint_step")
 
 
 def mhd_adjoint_step_cfl(ctx, U_n: torch.Tensor, gU_np1: torch.Tensor, gU_n: torch.Tensor):
     """Returns (dt, g_dt)."""
     dt, gdt = ctypes.c_double(0), ctypes.c_double(0)
-    _check(LIB.mhd_adjoint_step_cfl(ctx, _ptr(U_n), _ptr(gU_np1), _ptr(gU_n), ctypes.byref(dt), ctypes.byref(gdt)),
+    _check(LIB.mhd_adjoint_step_cfl(ctx, _field(ctx, U_n, 8, "U_n"), _field(ctx, gU_np1, 8, "gU_np1"),
+                                    _field(ctx, gU_n, 8, "gU_n"), ctypes.byref(dt), ctypes.byref(gdt)),
            "mhd_adjoint_step_cfl")
     return dt.value, gdt.value
 
@@ -192,7 +243,7 @@ def mhd_adjoint_step_cfl(ctx, U_n: torch.Tensor, gU_np1: torch.Tensor, gU_n: tor
 def mhd_diagnostics(ctx, U: torch.Tensor):
     m = ctypes.c_double(0)
     tot = (ctypes.c_double * 8)()
-    _check(LIB.mhd_diagnostics(ctx, _ptr(U), ctypes.byref(m), tot), "mhd_diagnostics")
+    _check(LIB.mhd_diagnostics(ctx, _field(ctx, U, 8, "U"), ctypes.byref(m), tot), "mhd_diagnostics")
     return m.value, list(tot)
 
 
@@ -202,7 +253,8 @@ def mhd_diagnostics_static(cfg: mhd_config, U: torch.Tensor, stream=None):
     m = ctypes.c_double(0)
     tot = (ctypes.c_double * 8)()
     s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
-    _check(LIB.mhd_diagnostics_static(ctypes.byref(cfg), _ptr(U), s, ctypes.byref(m), tot), "mhd_diagnostics_static")
+    p = _ptr(U, 8 * cfg.nx * cfg.ny * cfg.nz, "U")
+    _check(LIB.mhd_diagnostics_static(ctypes.byref(cfg), p, s, ctypes.byref(m), tot), "mhd_diagnostics_static")
     return m.value, list(tot)
 
 
@@ -214,19 +266,22 @@ def mhd_status(ctx):
 
 
 def mhd_stage_primitives(ctx, U, W):
-    _check(LIB.mhd_stage_primitives(ctx, _ptr(U), _ptr(W)), "mhd_stage_primitives")
+    _check(LIB.mhd_stage_primitives(ctx, _field(ctx, U, 8, "U"), _field(ctx, W, 8, "W")), "mhd_stage_primitives")
 
 
 def mhd_stage_fluxes(ctx, U, recon: int, F):
-    _check(LIB.mhd_stage_fluxes(ctx, _ptr(U), int(recon), _ptr(F)), "mhd_stage_fluxes")
+    _check(LIB.mhd_stage_fluxes(ctx, _field(ctx, U, 8, "U"), int(recon), _field(ctx, F, 21, "F")),
+           "mhd_stage_fluxes")
 
 
 def mhd_stage_edges(ctx, U, F, E):
-    _check(LIB.mhd_stage_edges(ctx, _ptr(U), _ptr(F), _ptr(E)), "mhd_stage_edges")
+    _check(LIB.mhd_stage_edges(ctx, _field(ctx, U, 8, "U"), _field(ctx, F, 21, "F"), _field(ctx, E, 3, "E")),
+           "mhd_stage_edges")
 
 
 def mhd_stage_recon(ctx, U, axis: int, recon: int, WL, WR):
-    _check(LIB.mhd_stage_recon(ctx, _ptr(U), int(axis), int(recon), _ptr(WL), _ptr(WR)), "mhd_stage_recon")
+    _check(LIB.mhd_stage_recon(ctx, _field(ctx, U, 8, "U"), int(axis), int(recon), _field(ctx, WL, 7, "WL"),
+                               _field(ctx, WR, 7, "WR")), "mhd_stage_recon")
 
 
 def mhd_adjoint_workspace_bytes(cfg: mhd_config) -> int:
@@ -236,15 +291,18 @@ def mhd_adjoint_workspace_bytes(cfg: mhd_config) -> int:
 
 
 def mhd_stage_recon_vjp(ctx, U, axis: int, recon: int, gWL, gWR, gU):
-    _check(LIB.mhd_stage_recon_vjp(ctx, _ptr(U), int(axis), int(recon), _ptr(gWL), _ptr(gWR), _ptr(gU)),
-           "mhd_stage_recon_vjp")
+    _check(LIB.mhd_stage_recon_vjp(ctx, _field(ctx, U, 8, "U"), int(axis), int(recon), _field(ctx, gWL, 7, "gWL"),
+                                   _field(ctx, gWR, 7, "gWR"), _field(ctx, gU, 8, "gU")), "mhd_stage_recon_vjp")
 
 
 def mhd_stage_hlld_vjp(gamma, precision: int, wl, wr, bn, gf, gwl, gwr, gbn, f, stream=None):
     s = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
     n = bn.numel()
-    _check(LIB.mhd_stage_hlld_vjp(int(n), float(gamma), int(precision), _ptr(wl), _ptr(wr), _ptr(bn), _ptr(gf),
-                                  _ptr(gwl), _ptr(gwr), _ptr(gbn), _ptr(f), s), "mhd_stage_hlld_vjp")
+    faces = {k: _ptr(t, 7 * n, k) for k, t in (("wl", wl), ("wr", wr), ("gf", gf), ("gwl", gwl), ("gwr", gwr),
+                                                ("f", f))}
+    _check(LIB.mhd_stage_hlld_vjp(int(n), float(gamma), int(precision), faces["wl"], faces["wr"], _ptr(bn, n, "bn"),
+                                  faces["gf"], faces["gwl"], faces["gwr"], _ptr(gbn, n, "gbn"), faces["f"], s),
+           "mhd_stage_hlld_vjp")
 
 
 MHD_NUM_STAGES = 8

@@ -102,3 +102,39 @@ def test_null_arguments_rejected(lib):
     assert lib.mhd_adjoint_step_cfl(None, None, None, None, None, None) == -1
     lib.mhd_strerror.restype = ctypes.c_char_p
     assert lib.mhd_strerror(-4).startswith(b"non-finite")
+
+
+def test_binding_checks_buffers_before_the_library_sees_them():
+    """The library takes raw pointers and cannot see sizes; the binding
+    refuses a wrong dtype, device, layout or size with an exception (not an
+    assert, which python -O would strip) before any call."""
+    import torch
+    from paper_2402_05240_gb300 import mhd
+    f64 = torch.float64
+    with pytest.raises(TypeError):
+        mhd._ptr([1.0, 2.0], name="U")
+    with pytest.raises(TypeError):
+        mhd._ptr(torch.zeros(8, dtype=torch.float32), name="U")
+    with pytest.raises(ValueError):
+        mhd._ptr(torch.zeros(8, dtype=f64), name="U")  # host tensor where a CUDA one is needed
+    with pytest.raises(ValueError):
+        mhd._ptr(torch.zeros(4, 4, dtype=f64).t(), name="U_host", cuda=False)  # not contiguous
+    with pytest.raises(ValueError):
+        mhd._ptr(torch.zeros(8, dtype=f64), 9, "U_host", cuda=False)
+    assert mhd._ptr(torch.zeros(9, dtype=f64), 9, "U_host", cuda=False).value is not None
+    # a context's cells come from its registration (made by mhd_init); a fake
+    # registration stands in for one here and no library call is reached
+    fake = ctypes.c_void_p(0x1000)
+    mhd._CTX[fake.value] = (4 * 5 * 6, 0)
+    try:
+        assert mhd._cells(fake) == (120, 0)
+        with pytest.raises(ValueError):
+            mhd.mhd_run_host(fake, torch.zeros(8 * 120 - 1, dtype=f64), 1)
+        with pytest.raises(ValueError):
+            mhd.mhd_step_sub(fake, torch.zeros(8, 6, 5, 4, dtype=f64), (0, 0, 0), 1e-3,
+                             torch.zeros(8, 6, 5, 5, dtype=f64))
+        with pytest.raises(ValueError):
+            mhd.mhd_dt_sub(fake, torch.zeros(7, 6, 5, 4, dtype=f64), (0, 0, 0))
+    finally:
+        del mhd._CTX[fake.value]
+    assert mhd._cells(fake) == (None, None)
