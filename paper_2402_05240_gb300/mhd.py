@@ -187,7 +187,8 @@ def mhd_evolve(ctx, U: torch.Tensor, t_end: float, max_steps: int = 1 << 30):
     """Advance U in place to t_end; returns (time reached, steps taken)."""
     t = ctypes.c_double(0)
     n = ctypes.c_int(0)
-    _check(LIB.mhd_evolve(ctx, _field(ctx, U, 8, "U"), float(t_end), int(max_steps), ctypes.byref(t), ctypes.byref(n)), "mhd_evolve")
+    _check(LIB.mhd_evolve(ctx, _field(ctx, U, 8, "U"), float(t_end), int(max_steps), ctypes.byref(t),
+                          ctypes.byref(n)), "mhd_evolve")
     return t.value, n.value
 
 
