@@ -4,9 +4,10 @@ Each test names the passage it checks.  None of them compares the oracle with
 itself: they use closed forms, textbook special cases (HLLC for B = 0 and,
 with the total pressure, for B_n = 0; the van Leer slope for one field),
 hand-worked limiter values, invariants of the exact equations (conservation,
-div B, symmetry), exact discrete solutions (isolated contacts and rotational
-discontinuities, stationary and moving) and the convergence order the paper
-reports.
+div B; the symmetries: axis relabelling, x-y transposition, mirror, field
+reversal, density scaling), exact discrete solutions (isolated contacts and
+rotational discontinuities, stationary and moving) and the convergence order
+the paper reports.
 """
 import json
 import math
