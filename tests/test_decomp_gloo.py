@@ -1,7 +1,7 @@
 """Domain decomposition over ranks on the CPU (gloo): the halo exchange and
 the dt all-reduce of paper_2402_05240_gb300.decomp, with the oracle's step on
 each rank's halo-extended block, reproduce the monolithic oracle run bit for
-bit (2 and 4 ranks, every decomposed axis, edges and corners included)."""
+bit (2, 3 and 4 ranks, every decomposed axis, edges and corners included)."""
 import os
 import socket
 
@@ -66,8 +66,10 @@ def _worker(rank, world, port, parts, recon, outdir):
     dist.destroy_process_group()
 
 
+# with 2 parts on an axis both neighbours are the same rank; 3 parts make
+# a ring with distinct lower and upper neighbours
 @pytest.mark.parametrize("parts,recon", [((2, 1, 1), "plmc"), ((1, 2, 1), "ppmc"), ((1, 1, 2), "plmc"),
-                                         ((2, 2, 1), "ppmc")])
+                                         ((2, 2, 1), "ppmc"), ((3, 1, 1), "plmc"), ((3, 1, 1), "ppmc")])
 def test_decomposed_run_equals_monolithic(tmp_path, parts, recon):
     import torch.multiprocessing as mp
 
