@@ -5,24 +5,29 @@
  * (Eq. dt), PCM predictor fluxes from the HLLD Riemann solver (Steps 2-3),
  * edge electric fields (Eq. emf-edge, Steps 4 and 8), half-step update
  * (Step 5), PLMC/PPMC characteristic reconstruction (Step 6, Sec. 2.2.6),
- * corrector fluxes (Step 7) and full-step update (Step 9), on a periodic 3-D
- * Cartesian mesh.
+ * corrector fluxes (Step 7) and full-step update (Step 9), on a 3-D Cartesian
+ * mesh, periodic by default (outflow boundaries and halo-fed subdomains are
+ * options of mhd_config).
  *
  * State layout (all entry points): one contiguous float64 array
  *   U[8][nz][ny][nx], x fastest, fields rho, mx, my, mz, E, Bx, By, Bz
  * (the conserved vector U of Sec. 2.1).  Bx[k][j][i] is the face-centred
  * field at x_{i+1/2} (the upper x-face of cell i; Sec. 2.2 "staggered grid");
- * By at y_{j+1/2}, Bz at z_{k+1/2}.  There are no ghost cells: periodic
- * neighbours are found by wrap-around indexing inside the kernels.
+ * By at y_{j+1/2}, Bz at z_{k+1/2}.  The caller's arrays hold no ghost
+ * cells: periodic neighbours are found by wrap-around indexing inside the
+ * kernels, and outflow axes are padded inside the library's workspace.
  *
  * Pointers: arguments named *_dev are device pointers (cudaMalloc / torch
  * CUDA tensors), *_host host pointers.  The caller owns every state and
- * gradient buffer; the library owns only the workspace it allocates in
- * mhd_init and frees in mhd_destroy.  All device work is issued on the
- * stream given to mhd_init (NULL = legacy default stream).
+ * gradient buffer.  The library owns the workspace it allocates in
+ * mhd_init, the adjoint workspace and the device copy of mhd_run_host that
+ * it allocates on first use, all freed by mhd_destroy, and the static
+ * scratch of mhd_diagnostics_static.  All device work of a context is
+ * issued on the stream given to mhd_init (NULL = legacy default stream).
  *
- * Errors: every call returns an int status (MHD_OK = 0, negative on error);
- * the library never exits, aborts or traps.  Device kernels raise flags
+ * Errors: every call except mhd_destroy, mhd_strerror and mhd_stage_name
+ * returns an int status (MHD_OK = 0, negative on error); the library never
+ * exits, aborts or traps.  Device kernels raise flags
  * (non-finite value, non-positive density) that the synchronising calls
  * (mhd_dt, mhd_status, mhd_diagnostics, mhd_run_host) report.
  */
