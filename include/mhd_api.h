@@ -24,6 +24,9 @@
  * it allocates on first use, all freed by mhd_destroy, and the static
  * scratch of mhd_diagnostics_static.  All device work of a context is
  * issued on the stream given to mhd_init (NULL = legacy default stream).
+ * A context holds mutable host state (profiling records, the lazily
+ * allocated buffers): calls on one context from several host threads must
+ * be serialised by the caller; separate contexts are independent.
  *
  * Errors: every call except mhd_destroy, mhd_strerror and mhd_stage_name
  * returns an int status (MHD_OK = 0, negative on error); the library never
