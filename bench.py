@@ -71,7 +71,10 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # one 128^3 turbulent-box step (per-kernel SASS op counters and DRAM bytes):
 # (FP64 pipe ops DFMA + DADD + DMUL, FP64 flop 2 DFMA + DADD + DMUL,
 #  warp instructions, DRAM bytes read + written).  They hold for the kernels
-# as profiled; a kernel changed since has no entry.
+# as profiled; a kernel changed since has no entry.  The double-float entries
+# predate the comparison helpers whose double specialisations decide branches
+# on bit patterns; for the float-pair type those helpers are the comparisons
+# they replaced, so its kernels compute and access memory as profiled.
 COUNTERS = {
     "fp64": {
         "prim": (121.0, 171.0, 918 / 32, 106.0),
