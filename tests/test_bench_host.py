@@ -58,3 +58,16 @@ def test_roofline_without_counters_is_hbm_bound(bench):
     r = bench.roofline_of(_prof(ms, 2), "fp64", n3, 6791.4, "measured", "ppmc")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
     assert r["frac"] == pytest.approx(176 * n3 / 2.4e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
+
+
+def test_partial_counters_give_no_step_dram_figure(bench):
+    """Double-float: the dominant stage has counters, the primitive and update
+    stages (changed after the capture) do not, so the stage's own figures
+    are reported and the step-level ncu DRAM figure is left out."""
+    n3 = 256 ** 3
+    ms = {"prim": 0.9, "flux_pcm": 3.0, "emf": 0.9, "update_half": 0.6, "recon": 6.2, "flux_hlld": 3.9,
+          "update_full": 0.4}
+    assert "prim" not in bench.COUNTERS["fp64_df"] and "recon" in bench.COUNTERS["fp64_df"]
+    r = bench.roofline_of(_prof(ms, 10), "fp64_df", n3, 6791.4, "measured", "plmc")
+    assert r["kernel"] == "recon" and r["bound"] == "alu" and r["traffic"] is not None
+    assert "ncu_dram_bytes_per_cell" not in r["step_hbm"]
