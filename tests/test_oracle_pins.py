@@ -394,6 +394,39 @@ def test_plm_single_field_slope_is_van_leer(recon, cells):
     np.testing.assert_allclose(WL[1:, 0, 0, i], WL[1:, 0, 0, 0], rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("col", [0, 1, 2, 4, 5, 6])
+@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+def test_single_wave_profile_reconstructs_along_its_eigenvector(recon, col):
+    """Sec. 2.2.6 (characteristic projection, limiting, back-projection): a
+    profile W_s = W_0 + eps a_s r_k along one right eigenvector r_k (fast,
+    Alfven or slow, from the eigensystem pinned above) has amplitude a in
+    field k and O(eps^2) in the others, so the faces are W_i + eps (limited
+    deviation of a) r_k + O(eps^2).  The deviations are the hand-worked ones
+    of the single-field pins: PLMC a = (0, 1, 1.25) gives the van Leer slope
+    0.4, faces -+0.2; PPMC a = (-1, 0, 1, 1.25, 0) gives -0.4375 / 0.28125.
+    A field mixed up between L and R, a projection with the wrong cell's
+    eigenvectors or a dropped back-projection shows here."""
+    w0 = np.array([1.2, 0.1, -0.2, 0.15, 0.9, 0.6, -0.45])
+    bn = 0.8
+    r = O.eigen(G, w0, bn)[1][:, col]
+    pattern, wr_q, wl_q = {"plmc": ((0.0, 1.0, 1.25), -0.2, 0.2),
+                           "ppmc": ((-1.0, 0.0, 1.0, 1.25, 0.0), -0.4375, 0.28125)}[recon]
+    n, i, eps = 16, 7, 1e-6
+    a = np.zeros(n)
+    h = len(pattern) // 2
+    a[i - h:i + h + 1] = pattern
+    W = w0[:, None] + eps * a[None, :] * r[:, None]  # solver frame along x
+    box = I.Box(n, 4, 4)
+
+    def b(x):
+        return np.broadcast_to(x, box.shape)
+    U = I.assemble(box, b(W[0]), (b(W[1]), b(W[2]), b(W[3])), b(W[4]), (b(np.full(n, bn)), b(W[5]), b(W[6])))
+    WL, WR = O.Oracle(n, 4, 4, recon=recon).recon(U, 0)
+    tol = 1e-7 * np.max(np.abs(r))
+    np.testing.assert_allclose((WL[:, 0, 0, i] - W[:, i]) / eps, wl_q * r, rtol=0, atol=tol)
+    np.testing.assert_allclose((WR[:, 0, 0, i] - W[:, i]) / eps, wr_q * r, rtol=0, atol=tol)
+
+
 @pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 def test_recon_flat_at_extremum(recon):
     """A local extremum of the cell averages gets no slope (Eq. limiter; MC11)."""
