@@ -825,6 +825,31 @@ def test_jvp_matches_central_difference(recon):
     assert err < 1e-6
 
 
+@pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc"])
+def test_jvp_matches_central_difference_in_field_directions(recon):
+    """As above along directions that move the face field too: a random
+    divergence-free face-field direction (the discrete curl of random edge
+    potentials), alone and together with random hydro directions.  This
+    checks the dual-number derivatives through B_n, the transverse fields,
+    the cell-centred averages and the edge fields."""
+    n = 8
+    box = I.Box(n, n, n)
+    U = I.turbulent_box(box, seed_v=33, seed_b=34, kmax=2)
+    orc = O.Oracle(n, n, n, recon=recon)
+    dt = orc.dt(U, 0.3)
+    rng = np.random.default_rng(9)
+    for hydro in (False, True):
+        d = np.zeros(U.shape)
+        if hydro:
+            d[:5] = rng.normal(size=(5,) + box.shape)
+        d[5:8] = np.array(I.faces_from_potential(box, *(rng.normal(size=box.shape) / n for _ in range(3))))
+        V, JV = orc.step_jvp(U, d, dt)
+        eps = 1e-8
+        fd = (orc.step(U + eps * d, dt) - orc.step(U - eps * d, dt)) / (2 * eps)
+        err = np.max(np.abs(fd - JV)) / np.max(np.abs(JV))
+        assert err < 1e-6, (hydro, err)
+
+
 def _cfl_argmin(U, orc, d):
     """(cell, axis) of the smallest d_l / (|v_l| + c_f,l), from the oracle's
     primitives and the textbook fast speed written out here."""
