@@ -395,7 +395,7 @@ def test_plm_single_field_slope_is_van_leer(recon, cells):
 
 
 @pytest.mark.parametrize("col", [0, 1, 2, 4, 5, 6])
-@pytest.mark.parametrize("recon", ["plmc", "ppmc"])
+@pytest.mark.parametrize("recon", ["plmc", "ppmc", "plm_prim"])
 def test_single_wave_profile_reconstructs_along_its_eigenvector(recon, col):
     """Sec. 2.2.6 (characteristic projection, limiting, back-projection): a
     profile W_s = W_0 + eps a_s r_k along one right eigenvector r_k (fast,
@@ -405,11 +405,14 @@ def test_single_wave_profile_reconstructs_along_its_eigenvector(recon, col):
     of the single-field pins: PLMC a = (0, 1, 1.25) gives the van Leer slope
     0.4, faces -+0.2; PPMC a = (-1, 0, 1, 1.25, 0) gives -0.4375 / 0.28125.
     A field mixed up between L and R, a projection with the wrong cell's
-    eigenvectors or a dropped back-projection shows here."""
+    eigenvectors or a dropped back-projection shows here.  The primitive-
+    limited PLM gives the same faces: each primitive's differences are the
+    amplitude differences times one component of r_k, and the van Leer
+    slope is homogeneous of degree one."""
     w0 = np.array([1.2, 0.1, -0.2, 0.15, 0.9, 0.6, -0.45])
     bn = 0.8
     r = O.eigen(G, w0, bn)[1][:, col]
-    pattern, wr_q, wl_q = {"plmc": ((0.0, 1.0, 1.25), -0.2, 0.2),
+    pattern, wr_q, wl_q = {"plmc": ((0.0, 1.0, 1.25), -0.2, 0.2), "plm_prim": ((0.0, 1.0, 1.25), -0.2, 0.2),
                            "ppmc": ((-1.0, 0.0, 1.0, 1.25, 0.0), -0.4375, 0.28125)}[recon]
     n, i, eps = 16, 7, 1e-6
     a = np.zeros(n)
