@@ -226,11 +226,15 @@ int mhd_diagnostics(mhd_ctx* ctx, const double* U_dev, double* divb_max_host, do
  * U_dev is a state in the usual layout; the work runs on `stream` (a
  * cudaStream_t, NULL = default stream) and the call synchronises it before
  * writing the max |div B| and the 8 field sums to host memory.
- * Scratch: a file-scope device array of 9.4 MB (grids up to 512^3 =
- * 134,217,728 cells) that every GPU loading the library holds until the
- * process exits.  Larger grids return MHD_ERR_TOO_LARGE.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * Scratch: a file-scope device array of 17.8 MB (9 results, then 9 partial
+ * values and 8 compensation terms per 1024-cell block: 9 + 17 * 131072
+ * doubles for grids up to 512^3 = 134,217,728 cells) that every GPU loading
+ * the library holds until the process exits.  Larger grids return
+ * MHD_ERR_TOO_LARGE.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The address is cached per device
+ * ordinal for the life of the process and is not looked up again after a
+ * cudaDeviceReset: do not call this after resetting a device.
  * All calls share the one array and it keeps the last call's contents:
  * calls whose work overlaps on the GPU (other streams, other host threads
  * on the same device) race and must be serialised by the caller. */

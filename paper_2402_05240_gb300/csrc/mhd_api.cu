@@ -82,10 +82,7 @@ void padded_dims(const mhd_config& c, int n[3], int lo[3]) {
   }
 }
 
-size_t red_blocks(long long N) {
-  long long b = (N + 1023) / 1024;
-  return (size_t)(b < 1 ? 1 : b);
-}
+size_t red_blocks(long long N) { return (size_t)mhd::diag_blocks(N); }
 
 Layout layout_of(const mhd_config& c) {
   int np[3], lo[3];
@@ -116,7 +113,7 @@ Layout layout_of(const mhd_config& c) {
   L.flags = off;
   off += up(sizeof(unsigned));
   L.red = off;
-  off += up((9 + 17 * red_blocks((long long)Ni)) * sizeof(double));  // totals, partials, compensations
+  off += up((size_t)mhd::diag_scratch_doubles((long long)red_blocks((long long)Ni)) * sizeof(double));
   L.Up = off;
   if (padded(c)) off += up(8 * N * sizeof(double));
   L.total = off;
@@ -836,7 +833,7 @@ const char* mhd_strerror(int code) {
     case MHD_ERR_OOM: return "out of device memory";
     case MHD_ERR_NONFINITE: return "non-finite value or non-positive density in the state";
     case MHD_ERR_DT: return "time step not positive or not finite";
-    case MHD_ERR_TOO_LARGE: return "grid larger than the static scratch of mhd_diagnostics_static (512^3 cells)";
+    case MHD_ERR_TOO_LARGE: return "grid larger than the 17.8 MB static scratch of mhd_diagnostics_static (512^3 cells)";
     default: return "unknown status";
   }
 }

@@ -619,6 +619,7 @@ __global__ void k_fill_ghosts(Grid gp, double* Up) {
 // (pairwise summation with Neumaier-style error carrying), so the totals are
 // accurate to about one rounding of the result whatever the cell count.
 constexpr int DIAG_T = 1024;
+static_assert(DIAG_T == kDiagCells, "one partial block of the diagnostics reduces kDiagCells cells");
 
 __device__ __forceinline__ void diag_add(double& s, double& c, double s2, double c2) {
   const double t = s + s2;

@@ -79,7 +79,16 @@ void launch_set_dt(double* dt_cur, double value, cudaStream_t s);
 void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
                       unsigned* flags, double t_end, cudaStream_t s);
 
-// max |div B| and field sums of a state into red[0..8] (red holds 9 + 9 nb doubles)
+// Diagnostics scratch layout (doubles): the 9 results (8 field sums, then
+// max |div B|), then per partial block 9 partials (field-major: red[9 + f nb
+// + b]), then per block the 8 compensation terms of the field sums
+// (red[9 + (9 + f) nb + b]).  One partial block reduces kDiagCells cells.
+constexpr long long kDiagCells = 1024;
+constexpr long long diag_blocks(long long N) { return N < 1 ? 1 : (N + kDiagCells - 1) / kDiagCells; }
+constexpr long long diag_scratch_doubles(long long nb) { return 9 + 17 * nb; }
+
+// max |div B| and field sums of a state into red[0..8]; red holds
+// diag_scratch_doubles(nb) doubles, nb = diag_blocks(g.N)
 void launch_diagnostics(const Grid& g, const double* U, double* red, int nb, cudaStream_t s);
 
 // outflow boundaries: copy the caller's state U (grid gi) into the interior

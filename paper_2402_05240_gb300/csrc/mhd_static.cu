@@ -17,13 +17,14 @@
 
 namespace {
 
-// Cells reduced per partial block (must match the partial kernel's block size).
-constexpr long long kCellsPerBlock = 1024;
 // Largest grid served: 512^3 cells -> 131072 partial blocks.
 constexpr long long kMaxCells = 134217728LL;
-constexpr long long kMaxBlocks = kMaxCells / kCellsPerBlock;
-// 9 final values + 9 partials per block (8 field sums and max |div B|): 9.4 MB.
-constexpr long long kScratchDoubles = 9 + 9 * kMaxBlocks;
+constexpr long long kMaxBlocks = mhd::diag_blocks(kMaxCells);
+// The layout the diagnostics kernels write (mhd_launch.h): 9 results, then 9
+// partials and 8 compensation terms per block -- 9 + 17 * 131072 doubles,
+// 17.8 MB.
+constexpr long long kScratchDoubles = mhd::diag_scratch_doubles(kMaxBlocks);
+static_assert(kScratchDoubles == 9 + 17 * 131072LL, "static scratch sized for 512^3 cells");
 
 __device__ __align__(256) double g_diag_scratch[kScratchDoubles];
 
@@ -85,11 +86,13 @@ extern "C" int mhd_diagnostics_static(const mhd_config* cfg, const double* U_dev
     g.hi[a] = g.n[a];
     g.bc[a] = cfg->bc[a];
   }
-  const int nblk = (int)((N + kCellsPerBlock - 1) / kCellsPerBlock);
+  const long long nblk = mhd::diag_blocks(N);
+  // the size check above bounds nblk; this one ties the launch to the array
+  if (mhd::diag_scratch_doubles(nblk) > kScratchDoubles) return MHD_ERR_TOO_LARGE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Every partial the final pass reads is written by the partial pass of this
   // call, so nothing in the scratch has to start at zero.
-  mhd::launch_diagnostics(g, U_dev, scratch, nblk, s);
+  mhd::launch_diagnostics(g, U_dev, scratch, (int)nblk, s);
   if (cudaGetLastError() != cudaSuccess) return MHD_ERR_CUDA;
   double out[9];
   if (cudaMemcpyAsync(out, scratch, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;

@@ -138,3 +138,22 @@ def test_binding_checks_buffers_before_the_library_sees_them():
     finally:
         del mhd._CTX[fake.value]
     assert mhd._cells(fake) == (None, None)
+
+
+def test_static_diagnostics_scratch_holds_the_layout_the_kernels_write(lib):
+    """The allocation-free diagnostics write 9 results, then 9 partials and 8
+    compensation terms per 1024-cell block; for its largest grid (512^3 cells,
+    131072 blocks) its file-scope device array must hold 9 + 17 * 131072
+    doubles.  The host shadow of a __device__ array has the array's size, so
+    the symbol table of the built library shows it without a GPU."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_2402_05240_gb300 import build
+    out = subprocess.run([nm, "-S", "-C", build.LIB], capture_output=True, text=True, check=True).stdout
+    sizes = [int(ln.split()[1], 16) for ln in out.splitlines() if ln.endswith("g_diag_scratch")]
+    assert len(sizes) == 1, out[:2000]
+    blocks = -(-512 ** 3 // 1024)
+    assert sizes[0] == 8 * (9 + 17 * blocks)

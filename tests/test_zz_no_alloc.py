@@ -44,6 +44,41 @@ def test_static_diagnostics_match_context_version_on_consecutive_calls(mhd):
     sim.close()
 
 
+def _static_call(mhd, cfg, U):
+    m = ctypes.c_double(0)
+    tot = (ctypes.c_double * 8)()
+    code = mhd.LIB.mhd_diagnostics_static(ctypes.byref(cfg), ctypes.c_void_p(U.data_ptr()),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          ctypes.byref(m), tot)
+    return code, m.value, list(tot)
+
+
+def test_static_diagnostics_at_its_largest_grid(mhd):
+    """512^3 cells (131072 partial blocks) fill the static scratch exactly;
+    two calls in a row on different states match the context version."""
+    n = 512
+    N = n ** 3
+    sim = mhd.Sim(n, n, n, precision="fp32_bulk")  # the smaller workspace; the diagnostics are FP64 either way
+    gen = torch.Generator(device="cuda")
+    U = torch.empty(8, n, n, n, dtype=torch.float64, device="cuda")
+    for seed in (11, 12):
+        gen.manual_seed(seed)
+        U.uniform_(0.5, 1.5, generator=gen)
+        U[1:4] -= 1.0  # momenta of both signs
+        U[5:8] -= 1.0  # face fields of both signs, div B of order 1 / dx
+        ref_div, ref_tot = sim.diagnostics(U)
+        code, div, tot = _static_call(mhd, sim.cfg, U)
+        assert code == mhd.MHD_OK
+        assert abs(div - ref_div) <= 1e-12 * abs(ref_div)
+        np.testing.assert_allclose(tot, ref_tot, rtol=1e-12, atol=1e-12 * np.max(np.abs(ref_tot)))
+        # the sums also agree with torch's own FP64 sums of the fields
+        np.testing.assert_allclose(tot, U.reshape(8, N).sum(dim=1).cpu().numpy(), rtol=1e-10,
+                                   atol=1e-10 * N)
+    sim.close()
+    del U
+    torch.cuda.empty_cache()
+
+
 def test_static_diagnostics_rejects_grids_beyond_its_scratch(mhd):
     big = mhd.mhd_config(1024, 1024, 1024, 1e-3, 1e-3, 1e-3, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20)
     U = torch.zeros(8, dtype=torch.float64, device="cuda")  # never read: the size check comes first
