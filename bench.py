@@ -1,14 +1,17 @@
 """Benchmark of the VL+CT ideal-MHD step on GB300 (cell-updates/s).
 
-Workload (default): the 256^3 periodic turbulent box (rho = 1, P = 1, k^-2
+Workload (default): the 512^3 periodic turbulent box (rho = 1, P = 1, k^-2
 velocity at rms Mach 1 over k = 1..16, B = (0.5, 0, 0) + divergence-free
-perturbation of rms 0.1), PLMC + HLLD, CFL 0.3, dt from the CFL reduction on
+perturbation of rms 0.1), PPMC + HLLD, CFL 0.3, dt from the CFL reduction on
 the device every step.  The headline line is the FP64 step; the FP32-bulk
-step on the same workload is reported under "variants".
+and double-float steps on the same workload are reported under "variants",
+each with its per-field relative L1 and max error against the FP64 state
+after 10 steps on the FP64 run's dt sequence, and the adjoint steps where
+their workspace fits beside the state (else at 256^3, said so).
 
 Timing: W warm-up steps, then K steps bracketed by a barrier and a device
 synchronisation, CUDA events on the library's stream, max over ranks.  The
-state (1.07 GB) and workspace are far larger than L2, so no flush is needed.
+state (8.6 GB) and workspace are far larger than L2, so no flush is needed.
 Per-stage device times come from the library's event tracing over the same
 timed region.  One process per GPU; ranks run independent replicas (weak
 scaling, no data-path collective).
@@ -67,16 +70,17 @@ FP64_PEAK_GFLOPS = 2 * FP64_PIPE_GINST
 # Warp-instruction issue limit: 4 schedulers per SM, 152 SMs, 2.07 GHz.
 ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 
-# Per-cell counters of one launch of each stage (PLMC runs only), from an ncu capture of
-# one 128^3 turbulent-box step (per-kernel SASS op counters and DRAM bytes):
-# (FP64 pipe ops DFMA + DADD + DMUL, FP64 flop 2 DFMA + DADD + DMUL,
-#  warp instructions, DRAM bytes read + written).  They hold for the kernels
-# as profiled; a kernel changed since has no entry.  The double-float entries
-# predate the comparison helpers whose double specialisations decide branches
-# on bit patterns; for the float-pair type those helpers are the comparisons
-# they replaced, so the float-pair kernels listed compute and access memory as
-# profiled.
-COUNTERS = {
+# Per-cell counters of one launch of each stage, from ncu captures at 128^3 of
+# the turbulent box (per-kernel SASS op counters and DRAM bytes), keyed by
+# reconstruction and precision: (FP64 pipe ops DFMA + DADD + DMUL, FP64 flop
+# 2 DFMA + DADD + DMUL, warp instructions, DRAM bytes read + written).  They
+# hold for the kernels as profiled; a kernel changed since has no entry.  The
+# double-float entries predate the comparison helpers whose double
+# specialisations decide branches on bit patterns; for the float-pair type
+# those helpers are the comparisons they replaced, so the float-pair kernels
+# listed compute and access memory as profiled.  The PCM predictor, edge
+# fields and updates do not depend on the reconstruction.
+_PLMC = {
     "fp64": {
         "prim": (121.0, 171.0, 918 / 32, 106.0),
         "flux_pcm": (235.3, 358.6, 1525 / 32, 101.2),
@@ -104,8 +108,10 @@ COUNTERS = {
         "flux_hlld": (0.0, 0.0, 3000 / 32, 162.5),
     },
 }
-
-
+# PPMC: the stages that do not depend on the reconstruction carry over; the
+# reconstruction and corrector Riemann kernels need captures of their own
+_PPMC = {prec: {k: v for k, v in tab.items() if k not in ("recon", "flux_hlld")} for prec, tab in _PLMC.items()}
+COUNTERS = {"plmc": _PLMC, "ppmc": _PPMC}
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -231,16 +237,32 @@ def time_adjoint(mhd, torch, U0, n, steps, warmup, recon, precision, barrier, fw
     ws = mhd.mhd_adjoint_workspace_bytes(sim.cfg)
     code, _ = mhd.mhd_status(sim.ctx)
     sim.close()
-    return {"value": n ** 3 / (ms * 1e-3), "ms_per_step": ms, "ratio_to_forward": ms / fwd_ms,
-            "dtype": {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)", "fp64_df": "df64 (float pairs, FP64 state)"}[
-                precision], "adjoint_workspace_gb": ws / 1e9,
-            "status": code}
+    del U, g, gout
+    torch.cuda.empty_cache()
+    return {"n": n, "value": n ** 3 / (ms * 1e-3), "ms_per_step": ms,
+            "ratio_to_forward": ms / fwd_ms if fwd_ms else None,
+            "dtype": DTYPES[precision], "adjoint_workspace_gb": ws / 1e9, "status": code}
+
+
+DTYPES = {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)", "fp64_df": "df64 (float pairs, FP64 state)"}
+MODE_NAMES = {"fp64": "FP64", "fp32_bulk": "FP32-bulk", "fp64_df": "double-float"}
+
+
+def adjoint_fits(mhd, torch, n, recon, precision):
+    """Whether the forward and adjoint workspaces of an n^3 context plus the
+    three states of time_adjoint (state, cotangent in and out) fit in the
+    device memory that is free now (5 % kept back)."""
+    cfg = mhd.mhd_config(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, 5.0 / 3.0, 0.3, mhd.RECON[recon],
+                         mhd.PRECISION[precision], 1e-20, 1e-20)
+    need = mhd.mhd_workspace_bytes(cfg) + mhd.mhd_adjoint_workspace_bytes(cfg) + 3 * 64 * n ** 3
+    free, _ = torch.cuda.mem_get_info()
+    return need <= 0.95 * free, need
 
 
 def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     """Roofline of the dominant stage (largest share of the timed region).
 
-    With per-cell counters of the stage (PLMC runs; ncu capture at 128^3):
+    With per-cell counters of the stage (ncu capture at 128^3):
     the stage is bound by the FP64 pipe or by instruction issue, whichever
     runs closer to its peak -- achieved = counted FP64-pipe operations
     (DFMA + DADD + DMUL) per launch / live launch time against the measured
@@ -270,13 +292,13 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     cells_per_s = n3 / step_s
     step_hbm = {"cells_per_s": round(cells_per_s), "frac_counted": round(cells_per_s * counted / 1e9 / hbm_peak, 4),
                 "frac_min_128B": round(cells_per_s * 128 / 1e9 / hbm_peak, 4)}
-    table = COUNTERS.get(precision, {}) if recon == "plmc" else {}
+    table = COUNTERS.get(recon, {}).get(precision, {})
     if table and all(k in table for k in prof if k != "dt" and prof[k][1]):
         ncu_b = sum(table[k][3] * v[1] for k, v in prof.items() if k != "dt") / steps
         step_hbm.update({"ncu_dram_bytes_per_cell": round(ncu_b, 1),
                          "frac_ncu": round(cells_per_s * ncu_b / 1e9 / hbm_peak, 4)})
     out["step_hbm"] = step_hbm
-    cnt = COUNTERS.get(precision, {}).get(name) if recon == "plmc" else None
+    cnt = COUNTERS.get(recon, {}).get(precision, {}).get(name)
     if cnt:
         gi = cnt[0] * n3 / per_launch_s / 1e9
         gw = cnt[2] * n3 / per_launch_s / 1e9
@@ -299,12 +321,12 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     return out
 
 
-def cpu_baseline_sample(n_sample=128, steps=1):
+def cpu_baseline_sample(recon, n_sample=128, steps=1):
     """The oracle as it stands on the host cores: one step of the same recipe
-    at n_sample^3 (a bounded sample of the 256^3 workload)."""
+    at n_sample^3 (a bounded sample of the workload)."""
     import oracle
     U = make_state(n_sample)
-    orc = oracle.Oracle(n_sample, n_sample, n_sample, recon="plmc")
+    orc = oracle.Oracle(n_sample, n_sample, n_sample, recon=recon)
     dt = orc.dt(U, 0.3)
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -312,7 +334,7 @@ def cpu_baseline_sample(n_sample=128, steps=1):
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": n_sample ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} FP64 PLMC step(s) of the turbulent-box recipe at {n_sample}^3 "
+            "sample": f"{steps} FP64 {recon.upper()} step(s) of the turbulent-box recipe at {n_sample}^3 "
                       f"({el:.1f} s wall)"}
 
 
@@ -337,8 +359,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"turbulent box {n}^3 sample of the 256^3 recipe, "
-                                                   f"{args.recon.upper()} + HLLD, FP64, CPU oracle",
+        "data": "synthetic", "config": {"workload": f"turbulent box {args.n or 512}^3, {args.recon.upper()} + HLLD, "
+                                                   f"FP64 step, CFL 0.3: CPU oracle on a {n}^3 sample of the "
+                                                   "recipe per step",
                                         "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n}^3 per step, {args.steps} steps"},
@@ -379,16 +402,16 @@ def run_workload(args, mhd, torch, rank):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     if args.workload == "precision512":
-        r = Wk.precision_compare(mhd, torch, n=args.n if args.n != 256 else 512, steps=args.steps,
+        r = Wk.precision_compare(mhd, torch, n=args.n or 512, steps=args.steps,
                                  warmup=args.warmup, recon="ppmc")
         value, ms, dtype = r["fp64"]["value"], r["fp64"]["ms_per_step"], "f64"
         wl = f"turbulent box {r['n']}^3, PPMC + HLLD, FP64 vs FP32-bulk vs double-float, {r['steps']} steps"
     elif args.workload == "adjoint_rollout":
-        r = Wk.adjoint_rollout(mhd, torch, n=args.n, steps=100, every=10)
+        r = Wk.adjoint_rollout(mhd, torch, n=args.n or 256, steps=100, every=10)
         value, ms, dtype = r["backward_cell_updates_per_s"], r["backward_s"] / r["steps"] * 1e3, "f32 (FP64 state)"
         wl = f"blast beta=0.1 {r['n']}^3, PPMC + HLLD, FP32-bulk, 100-step adjoint rollout, checkpoints every 10"
     else:
-        n = args.n if args.n != 256 else 459
+        n = args.n or 459
         r = Wk.slow_wave(mhd, torch, n=n, steps=args.steps, warmup=args.warmup, precision=args.precision)
         value, ms = r["value"], r["ms_per_step"]
         dtype = {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)", "fp64_df": "df64 (float pairs, FP64 state)"}[
@@ -409,8 +432,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--recon", default="plmc", choices=["plmc", "ppmc"])
+    ap.add_argument("--n", type=int, default=None,
+                    help="cells per axis (default 512; 256 for adjoint_rollout, 459 for slow_wave)")
+    ap.add_argument("--recon", default="ppmc", choices=["plmc", "ppmc"])
+    ap.add_argument("--compare-steps", type=int, default=10,
+                    help="steps after which each variant's state is compared with the headline mode's")
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--ref-sweep", action="store_true",
                     help="with --impl reference: also time the oracle at 32^3-256^3, all cores and one thread")
@@ -451,9 +477,11 @@ def main():
     if args.workload != "turbulent":
         return run_workload(args, mhd, torch, rank)
 
-    n = args.n
+    n = args.n or 512
     n3 = n ** 3
+    t0 = time.perf_counter()
     U0 = torch.from_numpy(make_state(n)).cuda()
+    gen_s = time.perf_counter() - t0
     hbm_peak, peak_kind = load_peaks()
 
     clocks = ClockSampler(local)
@@ -467,6 +495,7 @@ def main():
         ms64 = float(t.item())
     value = world * n3 / (ms64 * 1e-3)
     roof = roofline_of(prof64, args.precision, n3, hbm_peak, peak_kind, args.recon)
+    del U
 
     # end to end through the public host-buffer entry point (copies inside)
     e2e_s = None
@@ -478,44 +507,78 @@ def main():
         for _ in range(args.e2e_steps):
             mhd.mhd_run_host(sim.ctx, host, 1)
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        del host
     sim.close()
-    del U, sim
+    del sim
+    torch.cuda.empty_cache()
 
     variants = {}
     if not args.no_variants:
-        ms32, prof32, launches32, sim32, U32 = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
-                                                        "fp32_bulk", barrier)
-        variants["fp32_bulk"] = {
-            "value": world * n3 / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32 (FP64 state)",
-            "roofline": roofline_of(prof32, "fp32_bulk", n3, hbm_peak, peak_kind, args.recon), "gpu_launches": launches32}
-        sim32.close()
-        del U32, sim32
-        msdf, profdf, launchesdf, simdf, Udf = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon,
-                                                        "fp64_df", barrier)
-        variants["fp64_df"] = {
-            "value": world * n3 / (msdf * 1e-3), "ms_per_step": msdf,
-            "dtype": "double-float (float pairs) on FP32 pipes, FP64 state",
-            "roofline": roofline_of(profdf, "fp64_df", n3, hbm_peak, peak_kind, args.recon), "gpu_launches": launchesdf,
-            "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in profdf.items()}}
-        simdf.close()
-        del Udf, simdf
-        adj_steps = max(2, args.steps // 2)
-        variants["adjoint_fp64"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64", barrier, ms64)
-        variants["adjoint_fp32_bulk"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp32_bulk",
-                                                     barrier, ms32)
-        variants["adjoint_fp64_df"] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, "fp64_df",
-                                                   barrier, msdf)
+        from paper_2402_05240_gb300 import workloads as Wk
+        modes = [m for m in ("fp64", "fp32_bulk", "fp64_df") if m != args.precision]
+        # the headline mode's state after --compare-steps steps and its dts,
+        # against which each variant's state is compared on the same dts
+        ref = U0.clone()
+        dts = torch.zeros(args.compare_steps, dtype=torch.float64, device="cuda")
+        sim = mhd.Sim(n, n, n, cfl=0.3, recon=args.recon, precision=args.precision,
+                      stream=torch.cuda.current_stream().cuda_stream)
+        sim.run(ref, args.compare_steps, dts)
+        sim.status()
+        sim.close()
+        del sim
+        dts_host = dts.cpu().numpy().tolist()
+        for m in modes:
+            msm, profm, launchesm, simm, Um = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon, m,
+                                                       barrier)
+            Um.copy_(U0)
+            for dt in dts_host:
+                simm.step(Um, dt)
+            torch.cuda.synchronize()
+            simm.status()
+            simm.close()
+            variants[m] = {
+                "value": world * n3 / (msm * 1e-3), "ms_per_step": msm, "dtype": DTYPES[m],
+                "speedup_over_headline": ms64 / msm,
+                "roofline": roofline_of(profm, m, n3, hbm_peak, peak_kind, args.recon), "gpu_launches": launchesm,
+                "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in profm.items()},
+                f"vs_{args.precision}_after_{args.compare_steps}_steps": Wk.field_errors(torch, Um, ref)}
+            del Um, simm
+            torch.cuda.empty_cache()
+        del ref
+        torch.cuda.empty_cache()
+        fwd = {args.precision: ms64, **{m: variants[m]["ms_per_step"] for m in modes}}
+        U_small = None
+        for m in ("fp32_bulk", "fp64", "fp64_df"):
+            adj_steps = max(2, args.steps // 2)
+            fits, need = adjoint_fits(mhd, torch, n, args.recon, m)
+            if fits:
+                variants["adjoint_" + m] = time_adjoint(mhd, torch, U0, n, adj_steps, 1, args.recon, m, barrier,
+                                                        fwd[m])
+                continue
+            # does not fit beside the state at this size: time it at n/2 (and its forward step there)
+            nh = n // 2
+            if U_small is None:
+                U_small = torch.from_numpy(make_state(nh)).cuda()
+            msf, _, _, simf, Uf = time_gpu(mhd, torch, U_small, nh, adj_steps, 1, args.recon, m, barrier)
+            simf.close()
+            del Uf, simf
+            entry = time_adjoint(mhd, torch, U_small, nh, adj_steps, 1, args.recon, m, barrier, msf)
+            entry["note"] = (f"at {n}^3 the forward and adjoint workspaces and three states need "
+                             f"{need / 1e9:.0f} GB, more than the free device memory; timed at {nh}^3")
+            variants["adjoint_" + m] = entry
+        del U_small
+        torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_bulk": "f32 (FP64 state)",
-                                       "fp64_df": "df64 (float pairs, FP64 state)"}[args.precision],
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": f"turbulent box {n}^3, {args.recon.upper()} + HLLD, "
-                               f"{ {'fp64': 'FP64', 'fp32_bulk': 'FP32-bulk', 'fp64_df': 'double-float'}[args.precision]} "
-                               "step, CFL 0.3, device dt",
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (state 1.07 GB)"},
+                               f"{MODE_NAMES[args.precision]} step, CFL 0.3, device dt",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 (state {64 * n3 / 1e9:.2f} GB)",
+                   "input_generation_s": round(gen_s, 1)},
         "roofline": roof,
         "e2e": ({"value": world * n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3,
                  "d2h_bytes_per_step": 64 * n3} if e2e_s else None),
@@ -525,7 +588,7 @@ def main():
         "variants": variants,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_sample(args.recon)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

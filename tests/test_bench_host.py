@@ -39,7 +39,7 @@ def test_roofline_of_a_counted_stage(bench):
           "update_full": 1.5}
     r = bench.roofline_of(_prof(ms, 10), "fp64", n3, 6791.4, "measured", "plmc")
     assert r["kernel"] == "recon" and r["bound"] == "alu"
-    ops, flop, winst, dram = bench.COUNTERS["fp64"]["recon"]
+    ops, flop, winst, dram = bench.COUNTERS["plmc"]["fp64"]["recon"]
     assert r["fp64_pipe"]["achieved"] == pytest.approx(ops * n3 / 10.9e-3 / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(max(r["fp64_pipe"]["frac"], r["issue"]["frac"]), rel=1e-9)
     assert r["traffic"] == round(dram * n3)
@@ -50,8 +50,8 @@ def test_roofline_of_a_counted_stage(bench):
 
 
 def test_roofline_without_counters_is_hbm_bound(bench):
-    """PPMC has no counters: the dominant stage is reported against HBM with
-    no traffic figure."""
+    """A dominant stage without counters (here the PPMC reconstruction before
+    its capture) is reported against HBM with no traffic figure."""
     n3 = 128 ** 3
     ms = {"prim": 0.5, "flux_pcm": 1.0, "emf": 0.4, "update_half": 0.4, "recon": 2.4, "flux_hlld": 1.0,
           "update_full": 0.2}
@@ -67,7 +67,7 @@ def test_partial_counters_give_no_step_dram_figure(bench):
     n3 = 256 ** 3
     ms = {"prim": 0.9, "flux_pcm": 3.0, "emf": 0.9, "update_half": 0.6, "recon": 6.2, "flux_hlld": 3.9,
           "update_full": 0.4}
-    assert "prim" not in bench.COUNTERS["fp64_df"] and "recon" in bench.COUNTERS["fp64_df"]
+    assert "prim" not in bench.COUNTERS["plmc"]["fp64_df"] and "recon" in bench.COUNTERS["plmc"]["fp64_df"]
     r = bench.roofline_of(_prof(ms, 10), "fp64_df", n3, 6791.4, "measured", "plmc")
     assert r["kernel"] == "recon" and r["bound"] == "alu" and r["traffic"] is not None
     assert "ncu_dram_bytes_per_cell" not in r["step_hbm"]

@@ -338,6 +338,95 @@ def test_eigensystem(case):
         assert np.max(np.abs(L @ R - np.eye(7))) < 1e-12 * (1 + np.max(np.abs(L)) * np.max(np.abs(R)))
 
 
+def closed_form_left_eigenvectors(w, bn, gamma=G):
+    """Rows of L = R^-1 for the primitive variables (rho, v_n, v_t1, v_t2, P,
+    B_t1, B_t2), in the normalisation of Stone et al. (2008, App. A), rows
+    ordered u - c_f, u - c_a, u - c_s, u, u + c_s, u + c_a, u + c_f.
+
+    Derived here from the right eigenvectors by splitting the transverse
+    components along beta = B_t/|B_t| and its normal: the Alfven pair lives
+    on (v_perp, B_perp); the entropy row is d rho - dP/a^2; the fast and slow
+    pairs solve two 2x2 systems, one on the odd part (v_n, v_par), one on the
+    even part (P, B_par), which close with alpha_f^2 + alpha_s^2 = 1 and
+    A_f alpha_f + A_s alpha_s = a sqrt(rho).  With N = C_f^2 + C_s^2:
+      fast -/+: (0, -/+ C_f/2N, +/- Q_s beta/2N, alpha_f/(2 rho a^2), alpha_s beta/(2 a sqrt rho))
+      slow -/+: (0, -/+ C_s/2N, -/+ Q_f beta/2N, alpha_s/(2 rho a^2), -alpha_f beta/(2 a sqrt rho))
+      Alfven -/+: (0, 0, beta_perp/2, 0, +/- S beta_perp/(2 sqrt rho)), beta_perp = (-beta_2, beta_1)
+      entropy: (1, 0, 0, 0, -1/a^2, 0, 0)."""
+    rho, _, _, _, p, by, bz = (float(x) for x in w)
+    a2 = gamma * p / rho
+    ca2 = bn * bn / rho
+    bt2 = (by * by + bz * bz) / rho
+    disc = math.sqrt((a2 + ca2 + bt2) ** 2 - 4 * a2 * ca2)
+    cf2 = 0.5 * (a2 + ca2 + bt2 + disc)
+    cs2 = 0.5 * (a2 + ca2 + bt2 - disc) if ca2 > 0 else 0.0
+    if cf2 - cs2 == 0:
+        af, as_ = 1.0, 0.0
+    else:
+        af = math.sqrt(min(max((a2 - cs2) / (cf2 - cs2), 0.0), 1.0))
+        as_ = math.sqrt(min(max((cf2 - a2) / (cf2 - cs2), 0.0), 1.0))
+    bt = math.hypot(by, bz)
+    b1, b2 = (by / bt, bz / bt) if bt > 0 else (1 / math.sqrt(2), 1 / math.sqrt(2))
+    S = 1.0 if bn >= 0 else -1.0
+    a, sr = math.sqrt(a2), math.sqrt(rho)
+    Cf, Cs = math.sqrt(cf2) * af, math.sqrt(cs2) * as_
+    Qf, Qs = S * Cf, S * Cs
+    N = Cf * Cf + Cs * Cs
+    L = np.zeros((7, 7))
+    for row, sg in ((0, 1.0), (6, -1.0)):  # fast, u - c_f then u + c_f
+        L[row] = [0, -sg * Cf / (2 * N), sg * Qs * b1 / (2 * N), sg * Qs * b2 / (2 * N), af / (2 * rho * a2),
+                  as_ * b1 / (2 * a * sr), as_ * b2 / (2 * a * sr)]
+    for row, sg in ((2, 1.0), (4, -1.0)):  # slow
+        L[row] = [0, -sg * Cs / (2 * N), -sg * Qf * b1 / (2 * N), -sg * Qf * b2 / (2 * N), as_ / (2 * rho * a2),
+                  -af * b1 / (2 * a * sr), -af * b2 / (2 * a * sr)]
+    for row, sg in ((1, 1.0), (5, -1.0)):  # Alfven
+        L[row] = [0, 0, -b2 / 2, b1 / 2, 0, -sg * S * b2 / (2 * sr), sg * S * b1 / (2 * sr)]
+    L[3] = [1, 0, 0, 0, -1 / a2, 0, 0]
+    return L
+
+
+@pytest.mark.parametrize("case", ["generic", "bn0", "bt2_0", "bt2_tiny"])
+def test_left_eigenvectors_equal_the_closed_form(case):
+    """Stone et al. (2008, App. A): the oracle inverts R numerically and sets
+    to zero the entries of L below 32 eps of their row's largest entry
+    (reading D-29).  Against the closed-form L written out above:
+    every entry agrees to a few ulps of its row's scale; entries that are
+    zero in exact arithmetic (the v_n entries of the slow rows and the
+    v_t entries of the fast rows at B_n = 0, the beta_2 entries at B_t2 = 0)
+    are exactly zero, which fails without the zeroing; and beta_2 entries of
+    3e-14 of their row's scale (B_t2 / B_t1 = 3e-14) survive, which fails if
+    the threshold is raised tenfold."""
+    w = np.array([1.3, 0.2, -0.1, 0.3, 0.7, 0.8, -0.5])
+    bn = 0.6
+    if case == "bn0":
+        bn = 0.0
+    elif case == "bt2_0":
+        w[6] = 0.0
+    elif case == "bt2_tiny":
+        w[6] = 3e-14 * w[5]
+    _, R, L = O.eigen(G, w, bn)
+    Lc = closed_form_left_eigenvectors(w, bn)
+    assert np.max(np.abs(Lc @ R - np.eye(7))) < 1e-14  # the closed form inverts the oracle's R
+    for r in range(7):
+        scale = np.max(np.abs(Lc[r]))
+        assert np.max(np.abs(L[r] - Lc[r])) <= 8 * np.finfo(float).eps * scale, (r, L[r], Lc[r])
+        zero = Lc[r] == 0.0
+        assert np.all(L[r][zero] == 0.0), (r, L[r][zero])
+    if case == "bn0":
+        assert Lc[2, 1] == 0 and Lc[4, 1] == 0 and Lc[0, 2] == 0 and Lc[6, 3] == 0
+    # the beta_2 entries: v_t2 and B_t2 of the fast and slow rows, v_t1 and
+    # B_t1 of the Alfven rows
+    beta2 = [(r, c) for r in (0, 2, 4, 6) for c in (3, 6)] + [(r, c) for r in (1, 5) for c in (2, 5)]
+    if case == "bt2_0":
+        assert all(Lc[r, c] == 0 for r, c in beta2)
+    if case == "bt2_tiny":
+        eps = np.finfo(float).eps
+        for r, c in beta2:
+            scale = np.max(np.abs(Lc[r]))
+            assert 32 * eps < abs(Lc[r, c]) / scale < 320 * eps, (r, c, Lc[r, c] / scale)
+            assert L[r, c] != 0.0 and abs(L[r, c] - Lc[r, c]) <= 8 * eps * scale
+
+
 # --------------------------------------------------------- reconstruction --
 def _wave_state(box, f_rho):
     """rho varies along x; P, v, B uniform: a pure entropy (contact) mode."""
@@ -513,7 +602,7 @@ def test_ppmc_keeps_smooth_extrema_at_fourth_order():
     assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8, errs
 
 
-@pytest.mark.parametrize("case", ["interface_C", "extremum_C", "sign_and_overshoot"])
+@pytest.mark.parametrize("case", ["interface_C", "extremum_C", "sign_and_overshoot", "smooth_cubic_extremum"])
 def test_ppmc_limiter_worked_examples(case):
     """Hand-worked values of the PPMC limiters (Sec. 2.2.6; Colella & Sekora
     2008 interface limiter with C = 1.25, McCorquodale & Colella 2011 cell
@@ -541,11 +630,24 @@ def test_ppmc_limiter_worked_examples(case):
     0 - 0.25 + 0.25 is exactly 0, so the limited curvature is 0 and the value
     is the mean 0.1875.  Upper interface 6/12 * 1.75 = 0.875.  The cell is
     monotone and 0.625 >= 2 * 0.0625, so the upper face is clipped to
-    0.25 + 2 * 0.0625 = 0.375."""
+    0.25 + 2 * 0.0625 = 0.375.
+
+    smooth_cubic_extremum: where reading D-11 and the published cell limiter
+    differ.  q_j = 10 j^2 + j^3 (j = -2..2: 32, 9, 0, 11, 48) has a minimum
+    at cell i.  Both interfaces are 5/3 (7/12 * 9 - 43/12 and
+    7/12 * 11 - 57/12), inside their cells' range; curvatures 14, 20, 26,
+    d2f = 6 * 10/3 = 20, lim = min(20, 1.25 * 14, ...) = 17.5, r = 7/8, so
+    D-11 gives both faces 7/8 * 5/3 = 35/24.  McCorquodale & Colella's full
+    limiter first checks the third differences of the curvatures, here all
+    6 (a cubic): equal third differences (spread 0 < 0.1 * 6) mark a smooth
+    extremum, which that limiter leaves alone (faces 5/3).  That test needs
+    curvatures at i +- 2 (seven cells) while PPMC's stencil is five cells,
+    which is why D-11 leaves it out."""
     pattern, wr_q, wl_q = {
         "interface_C": ((-1.0, 0.0, 1.0, 1.25, 0.0), 0.5625, 1.28125),
         "extremum_C": ((0.625, 0.875, 1.0, 0.875, 0.625), 379 / 384, 379 / 384),
         "sign_and_overshoot": ((0.0, 0.125, 0.25, 1.5, 1.625), 0.1875, 0.375),
+        "smooth_cubic_extremum": ((32.0, 9.0, 0.0, 11.0, 48.0), 35 / 24, 35 / 24),
     }[case]
     n, i = 16, 7
     q = np.zeros(n)
