@@ -50,6 +50,7 @@ def stage_bytes(T: int) -> dict:
         "recon": 8 * T + 14 * T,             # W in; W_L, W_R out (one axis)
         "flux_hlld": 15 * T + 7 * T,         # W_L, W_R, face B in; 7 fluxes out (one axis)
         "update_full": 64 + 18 * T + 64,     # U, fluxes, edges in; U out
+        "recon_flux": 8 * T + T + 7 * T,     # W, face B in; 7 fluxes out (one axis; states stay on chip)
         "dt": 0,
     }
 

@@ -36,6 +36,11 @@ struct mhd_ctx {
   unsigned* flags;              // [0] error flags
   double* red;                  // diagnostics partials
   double* host_state;           // lazily allocated device copy for mhd_run_host
+  // mhd_run_host's copy pipeline (created on its first call): two copy
+  // streams and the events ordering slab copies against the slab primitives
+  cudaStream_t io_stream[2];
+  cudaEvent_t io_ev[2 * 16 + 3];
+  bool io_ready;
   size_t red_count;
   void* adj_ws;                 // adjoint workspace, allocated by the first adjoint call
   size_t adj_bytes;
@@ -184,11 +189,16 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
   prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 4
   prof(c, MHD_STAGE_UPDATE_HALF,
        [&] { Launch<T>::update_half(g, U, F, E, c->scal, W, as<T>(c->Bh), c->flags, s); });  // Step 5
+#ifdef MHD_AB_STAGED
   for (int a = 0; a < 3; ++a) {                                               // Steps 6-7
     prof(c, MHD_STAGE_RECON, [&] { Launch<T>::recon(g, recon, a, W, as<T>(c->WL), as<T>(c->WR), s); });
     prof(c, MHD_STAGE_FLUX_HLLD,
          [&] { Launch<T>::flux_hlld(g, a, as<T>(c->WL), as<T>(c->WR), as<T>(c->Bh), F, s); });
   }
+#else
+  for (int a = 0; a < 3; ++a)  // Steps 6-7, the interface states kept on chip
+    prof(c, MHD_STAGE_RECON_FLUX, [&] { Launch<T>::recon_flux(g, recon, a, W, as<T>(c->Bh), F, s); });
+#endif
   prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 8
   prof(c, MHD_STAGE_UPDATE_FULL, [&] { Launch<T>::update_full(g, U, F, E, c->scal, s); });  // Step 9
 }
@@ -236,6 +246,84 @@ template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_l
   run_begin<T>(c, S);
   for (int n = 0; n < nsteps; ++n) run_one<T>(c, S, dt_log, n, kNoEnd);
   leave(c, U);
+  return cuda_status();
+}
+
+// mhd_run_host on a periodic grid with the host copies in z slabs on two copy
+// streams: the primitives of Step 1 start on each slab as soon as it and the
+// slab below it (whose top plane holds the lower z faces) have arrived, and
+// the last step's floors and primitives release each slab for its copy back
+// while the next slab is processed.  Same kernels and order of arithmetic as
+// mhd_run: the result is bit for bit that of copy, mhd_run, copy.
+constexpr int kIoSlabs = 16;
+int io_setup(mhd_ctx* c) {
+  if (c->io_ready) return MHD_OK;
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamCreateWithFlags(&c->io_stream[i], cudaStreamNonBlocking) != cudaSuccess) return MHD_ERR_CUDA;
+  for (cudaEvent_t& e : c->io_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MHD_ERR_CUDA;
+  c->io_ready = true;
+  return MHD_OK;
+}
+
+template <class T> int run_host_slabs(mhd_ctx* c, double* U_host, int nsteps) {
+  const Grid& g = c->g;
+  cudaStream_t s = c->stream;
+  const int nz = g.n[2];
+  const int S = nz < kIoSlabs ? nz : kIoSlabs;
+  const size_t plane = (size_t)g.n[0] * g.n[1];
+  cudaEvent_t* evH = c->io_ev;
+  cudaEvent_t* evP = c->io_ev + kIoSlabs;
+  cudaEvent_t ev0 = c->io_ev[2 * kIoSlabs], evD0 = c->io_ev[2 * kIoSlabs + 1], evD1 = c->io_ev[2 * kIoSlabs + 2];
+  double* D = c->host_state;
+  auto zb = [&](int k) { return (int)((long long)k * nz / S); };
+  auto copy_slab = [&](int k, cudaMemcpyKind kind, cudaStream_t cs) {
+    const size_t off = (size_t)zb(k) * plane, n = (size_t)(zb(k + 1) - zb(k)) * plane * sizeof(double);
+    for (int f = 0; f < 8; ++f) {
+      const size_t o = (size_t)f * g.N + off;
+      const cudaError_t e = kind == cudaMemcpyHostToDevice ? cudaMemcpyAsync(D + o, U_host + o, n, kind, cs)
+                                                           : cudaMemcpyAsync(U_host + o, D + o, n, kind, cs);
+      if (e != cudaSuccess) return false;
+    }
+    return true;
+  };
+  // the device buffer may still be read by earlier work on the context's stream
+  cudaEventRecord(ev0, s);
+  for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(c->io_stream[i], ev0, 0);
+  for (int k = 0; k < S; ++k) {
+    if (!copy_slab(k, cudaMemcpyHostToDevice, c->io_stream[k & 1])) return MHD_ERR_CUDA;
+    cudaEventRecord(evH[k], c->io_stream[k & 1]);
+  }
+  // run_begin in slabs: slab k needs slabs k and k - 1; slab 0 the last one
+  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);
+  for (int q = 1; q <= S; ++q) {
+    const int k = q % S, below = (k + S - 1) % S;
+    cudaStreamWaitEvent(s, evH[k], 0);
+    cudaStreamWaitEvent(s, evH[below], 0);
+    Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, nullptr, n, c->flags, kNoEnd, s); });
+    step_body<T>(c, D, c->cfg.recon);
+    if (n + 1 < nsteps) {
+      prof(c, MHD_STAGE_PRIM, [&] { Launch<T>::prim(g, D, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });
+      continue;
+    }
+    // the last step's floors and primitives slab by slab, each slab copied back once done
+    for (int k = 0; k < S; ++k) {
+      prof(c, MHD_STAGE_PRIM, [&] {
+        Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, c->floors, s);
+      });
+      cudaEventRecord(evP[k], s);
+      cudaStreamWaitEvent(c->io_stream[k & 1], evP[k], 0);
+      if (!copy_slab(k, cudaMemcpyDeviceToHost, c->io_stream[k & 1])) return MHD_ERR_CUDA;
+    }
+  }
+  cudaEventRecord(evD0, c->io_stream[0]);
+  cudaEventRecord(evD1, c->io_stream[1]);
+  cudaStreamWaitEvent(s, evD0, 0);
+  cudaStreamWaitEvent(s, evD1, 0);
   return cuda_status();
 }
 
@@ -330,18 +418,22 @@ int check_sub(mhd_ctx* c, const int gn[3], const int off[3]) {
 }
 
 // ---- adjoint ----------------------------------------------------------------
-// Adjoint workspace (compute type T): forward intermediates W^n[8], F^n[21],
+// Adjoint buffers (compute type T): forward intermediates W^n[8], F^n[21],
 // W^{n+1/2}[8], B^{n+1/2}[3], W_L/W_R of the three axes [21+21], F^{n+1/2}[21],
 // E[3]; cotangents gF[21], gE[3], gW[8], gWL[7], gWR[7], recon slots[36],
 // gBf[3], gBcc[3], gBccF[3]; in double the half-step hydro state[5] and g5[5];
 // then the per-block partials of the dt cotangent (two per block) and a few
-// scalars for the reverse of the CFL dt.
+// scalars for the reverse of the CFL dt.  W^n, F^n, E, B^{n+1/2}, gWL and
+// gWR live in the context's step workspace (W, F, E, Bh, WL, WR, 49 words),
+// which holds nothing between calls (every step entry point recomputes W
+// first); the adjoint allocates the other 148 words and the doubles.
+constexpr size_t kAdjOwnWords = 197 - 49;
 size_t adj_part_count(const mhd_config& c) { return (size_t)mhd::cell_blocks(c.nx, c.ny, c.nz); }
 size_t adj_bytes_of(const mhd_config& c) {
   const size_t N = (size_t)c.nx * c.ny * c.nz;
   const size_t ts = c.precision == MHD_FP32_BULK ? 4 : 8;
-  return up(197 * N * ts) + up(10 * N * sizeof(double)) + up((2 * adj_part_count(c) + 8) * sizeof(double)) +
-         4 * kAlign;
+  return up(kAdjOwnWords * N * ts) + up(10 * N * sizeof(double)) +
+         up((2 * adj_part_count(c) + 8) * sizeof(double)) + 4 * kAlign;
 }
 
 template <class T> struct AdjView {
@@ -371,24 +463,25 @@ template <class T> int adj_view(mhd_ctx* c, AdjView<T>& v) {
     p += n * N;
     return q;
   };
-  v.Wn = take(8);
-  v.Fn = take(21);
+  v.Wn = as<T>(c->W);
+  v.Fn = as<T>(c->F);
+  v.Eh = as<T>(c->E);
+  v.Bh = as<T>(c->Bh);
+  v.gWL = as<T>(c->WL);
+  v.gWR = as<T>(c->WR);
   v.Wh = take(8);
-  v.Bh = take(3);
   v.WLa = take(21);
   v.WRa = take(21);
   v.Fh = take(21);
-  v.Eh = take(3);
   v.gF = take(21);
   v.gE = take(3);
   v.gW = take(8);
-  v.gWL = take(7);
-  v.gWR = take(7);
   v.gS = take(36);
   v.gBf = take(3);
   v.gBcc = take(3);
   v.gBccF = take(3);
-  char* d = reinterpret_cast<char*>(c->adj_ws) + up(197 * N * sizeof(T));
+  static_assert(8 + 21 * 4 + 3 + 8 + 36 + 3 * 3 == kAdjOwnWords, "adjoint buffers");
+  char* d = reinterpret_cast<char*>(c->adj_ws) + up(kAdjOwnWords * N * sizeof(T));
   v.Uh = reinterpret_cast<double*>(d);
   v.g5 = v.Uh + 5 * N;
   v.nparts = (long long)adj_part_count(c->cfg);
@@ -628,6 +721,13 @@ void mhd_destroy(mhd_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
   if (c->host_state) cudaFree(c->host_state);
+  if (c->io_ready) {
+    for (int i = 0; i < 2; ++i) {
+      cudaStreamSynchronize(c->io_stream[i]);
+      cudaStreamDestroy(c->io_stream[i]);
+    }
+    for (cudaEvent_t e : c->io_ev) cudaEventDestroy(e);
+  }
   if (c->adj_ws) cudaFree(c->adj_ws);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
@@ -662,7 +762,7 @@ int mhd_profile_read(mhd_ctx* c, double ms[MHD_NUM_STAGES], long long launches[M
 
 const char* mhd_stage_name(int stage) {
   static const char* names[MHD_NUM_STAGES] = {"prim", "flux_pcm", "emf", "update_half", "recon",
-                                              "flux_hlld", "update_full", "dt"};
+                                              "flux_hlld", "update_full", "dt", "recon_flux"};
   if (stage < 0 || stage >= MHD_NUM_STAGES) return "unknown";
   return names[stage];
 }
@@ -748,10 +848,17 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
     }
   }
   cudaStream_t s = c->stream;
-  if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
-  int st = mhd_run(c, c->host_state, nsteps, nullptr);
-  if (st != MHD_OK) return st;
-  if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  if (!c->Up && nsteps > 0) {
+    int st = io_setup(c);
+    if (st != MHD_OK) return st;
+    st = with_type(c->cfg.precision, [&](auto t) { return run_host_slabs<MHD_T>(c, U_host, nsteps); });
+    if (st != MHD_OK) return st;
+  } else {
+    if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
+    int st = mhd_run(c, c->host_state, nsteps, nullptr);
+    if (st != MHD_OK) return st;
+    if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  }
   double t = 0;
   if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;

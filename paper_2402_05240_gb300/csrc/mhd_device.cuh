@@ -100,6 +100,12 @@ template <> __device__ __forceinline__ double max_pos<double>(double x, double t
 template <> __device__ __forceinline__ double max_nonneg<double>(double x, double y) {
   return dbits(x) >= dbits(y) ? x : y;
 }
+// x finite (not +-inf, not NaN), and x > 0 and not NaN, on the bit pattern
+__device__ __forceinline__ bool finite_bits(double x) { return (dbits(x) & kAbsBits) < 0x7ff0000000000000LL; }
+__device__ __forceinline__ bool pos_bits(double x) {
+  const long long b = dbits(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
 // order key: sign-magnitude patterns mapped to a monotone signed integer
 __device__ __forceinline__ long long dkey(double x) {
   const long long b = dbits(x);

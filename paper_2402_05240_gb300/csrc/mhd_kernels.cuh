@@ -154,10 +154,12 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
 // rho and E are written, so this is race-free in place.  The CFL maximum and
 // the floor counters take interior cells only (ghost cells of a padded grid
 // are copies).
+// (z0: first z plane of the launch, which covers planes z0 .. z0 + gridDim.z - 1)
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
-                                                 unsigned* flags, unsigned long long* floors) {
-  const CellIdx ci = cell_of_thread(g);
+                                                 unsigned* flags, unsigned long long* floors, int z0) {
+  CellIdx ci = cell_of_thread(g);
+  ci.k += z0;
   T inv = T(0);
   if (ci.ok) {
     const int i = ci.i, j = ci.j, k = ci.k;
@@ -165,7 +167,9 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
     const bool in = interior(g, i, j, k);
     double r = U[c], e = U[4 * N + c];
     const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
-    if ((!(r > 0.0) || !isfinite(e) || !isfinite(m0) || !isfinite(m1) || !isfinite(m2)) && in) atomicOr(flags, 1u);
+    // (bit-pattern tests on the integer pipes: the FP64 pipe bounds this kernel)
+    if ((!pos_bits(r) || !finite_bits(e) || !finite_bits(m0) || !finite_bits(m1) || !finite_bits(m2)) && in)
+      atomicOr(flags, 1u);
     if (floors && lt_pos<double>(r, g.rho_floor)) {
       r = g.rho_floor;
       U[c] = r;
@@ -258,13 +262,12 @@ template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* 
 // kernel, 108 registers, loses 5 % at 5 blocks, 96 registers.)
 template <class T, int RECON> struct ReconMinBlocks { static constexpr int v = 4; };
 
+// interface states of cell (i, j, k) along A (Step 6): wl = W_{L,i+1/2} (the
+// cell's state at its upper face), wr = W_{R,i-1/2} (at its lower face), floored
 template <class T, int RECON, int A>
-__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
-                                                  T* __restrict__ WR) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
-  T wl[7], wr[7];
+__device__ __forceinline__ void recon_cell(const Grid& g, const T* __restrict__ W, int i, int j, int k, T* wl,
+                                           T* wr) {
+  const long long N = g.N, c = cidx(g, i, j, k);
   const T bn = W[(5 + A) * N + c];
   if (RECON == 0) {
     load_dir<A>(W, N, c, wl);
@@ -272,19 +275,29 @@ __global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(G
     for (int q = 0; q < 7; ++q) wr[q] = wl[q];
   } else if (RECON == 1 || RECON == 3) {
     T wm[7], w0[7], wp[7];
-    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
+    load_dir<A>(W, N, nb<A>(g, i, j, k, -1), wm);
     load_dir<A>(W, N, c, w0);
-    load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, 1), wp);
+    load_dir<A>(W, N, nb<A>(g, i, j, k, 1), wp);
     if (RECON == 1) plmc<T>(from_d<T>(g.gamma), wm, w0, wp, bn, wl, wr);
     else plm_prim<T>(wm, w0, wp, wl, wr);
   } else {
     T w[5][7];
 #pragma unroll
-    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
+    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, i, j, k, s), w[s + 2]);
     ppmc<T>(from_d<T>(g.gamma), w, bn, wl, wr);
   }
   floor_face<T>(g, wl);
   floor_face<T>(g, wr);
+}
+
+template <class T, int RECON, int A>
+__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
+                                                  T* __restrict__ WR) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T wl[7], wr[7];
+  recon_cell<T, RECON, A>(g, W, ci.i, ci.j, ci.k, wl, wr);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     WL[q * N + c] = wl[q];
@@ -308,6 +321,114 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
   hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, Bf[A * N + c], f);
 #pragma unroll
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+}
+
+// ------------------------------------------------------ Steps 6-7 fused --
+// Reconstruction and HLLD of one axis in one pass: the interface states stay
+// in registers (W_L, W_R never reach memory) and every cell is reconstructed
+// once, up to one cell per tile or segment.  Same arithmetic as k_recon
+// followed by k_flux_hlld, so the same fluxes bit for bit.
+template <class T> __device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <> __device__ __forceinline__ df shfl_up1<df>(df v) {
+  return df(__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1));
+}
+
+// Faces of x: each warp reconstructs 32 consecutive cells x0 - 1 .. x0 + 30
+// and solves the 31 faces between them (x0 = 31 * tile); the state at the
+// upper face of cell x - 1 comes from the neighbouring lane.  Face f + 1/2 is
+// stored at cell f; tile 0 computes f = -1, the periodic face of cell nx - 1.
+constexpr int kFacesPerWarp = BX - 1;
+template <class T, int RECON>
+__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v)
+    k_recon_flux_x(Grid g, const T* __restrict__ W, const T* __restrict__ Bf, T* __restrict__ F) {
+  const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (j >= g.n[1]) return;  // uniform over the warp (one warp per row)
+  const int nx = g.n[0];
+  const int lane = threadIdx.x;
+  const int f = blockIdx.x * kFacesPerWarp + lane - 2;  // face f + 1/2 of this lane
+  int x = (f + 1) % nx;                                 // cell reconstructed by this lane (f + 1 >= -1)
+  if (x < 0) x += nx;
+  T wl[7], wr[7], pl[7];
+  recon_cell<T, RECON, 0>(g, W, x, j, k, wl, wr);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) pl[q] = shfl_up1<T>(wl[q]);
+  if (lane == 0 || f > nx - 2) return;
+  const long long N = g.N, c = cidx(g, f < 0 ? f + nx : f, j, k);
+  T fl[7];
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), pl, wr, Bf[c], fl);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[(long long)q * N + c] = fl[q];
+}
+
+// Faces of y (A = 1) or z (A = 2): each thread owns one column along A and
+// marches through a segment [s0, s1) of it, carrying the upper-face state of
+// the previous cell in its own slot of shared memory (in registers it would
+// push the reconstruction past its register budget); the segment starts
+// with the reconstruction of cell s0 - 1.  Face c - 1/2 is stored at cell
+// c - 1.  Warps span consecutive x, so every load and store is a coalesced
+// row.
+// one step of the column march: reconstruct cell (i, j, k), solve the face
+// below it (stored at cell cprev) with the carried upper-face state of the
+// cell below, then carry this cell's upper-face state.  Not inlined: inlined
+// into the loop, the reconstruction's constants and addresses are hoisted
+// out of it and the kernel spills.
+#ifdef MHD_AB_INLINE_MARCH
+#define MHD_MARCH_INL __forceinline__
+#else
+#define MHD_MARCH_INL __noinline__
+#endif
+template <class T, int RECON, int A>
+__device__ MHD_MARCH_INL void march_face(const Grid& g, const T* __restrict__ W, const T* __restrict__ Bf,
+                                        T* __restrict__ F, int i, int j, int k, long long cprev, T* carry) {
+  T wl[7], wr[7], pl[7], fl[7];
+  recon_cell<T, RECON, A>(g, W, i, j, k, wl, wr);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) pl[q] = carry[q * BX * BY];
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), pl, wr, Bf[A * g.N + cprev], fl);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * g.N + cprev] = fl[q];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) carry[q * BX * BY] = wl[q];
+}
+
+// blocks per SM requested for the column march: its loop keeps the column's
+// indices live beside the reconstruction and the Riemann solver, which at
+// 128 registers spill for double and float pairs; float fits in 96
+template <class T, int RECON> struct MarchMinBlocks { static constexpr int v = 4; };
+template <int RECON> struct MarchMinBlocks<float, RECON> { static constexpr int v = 4; };
+
+template <class T, int RECON, int A>
+__global__ void __launch_bounds__(BX* BY, MarchMinBlocks<T, RECON>::v)
+    k_recon_flux_col(Grid g, const T* __restrict__ W, const T* __restrict__ Bf, T* __restrict__ F, int seg) {
+  static_assert(A == 1 || A == 2, "column march along y or z");
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int t = blockIdx.y * BY + threadIdx.y;  // z index (A = 1) or y index (A = 2)
+  constexpr int O = A == 1 ? 2 : 1;
+  if (i >= g.n[0] || t >= g.n[O]) return;
+  const int nA = g.n[A];
+  const int s0 = blockIdx.z * seg;
+  const int s1 = min(s0 + seg, nA);
+  auto at = [&](int c, int* ijk) {
+    ijk[0] = i;
+    ijk[A] = c;
+    ijk[O] = t;
+  };
+  __shared__ T carry[7][BX * BY];
+  const int slot = threadIdx.y * BX + threadIdx.x;
+  int p[3];
+  T wl[7], wr[7];
+  at(s0 == 0 ? nA - 1 : s0 - 1, p);
+  recon_cell<T, RECON, A>(g, W, p[0], p[1], p[2], wl, wr);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) carry[q][slot] = wl[q];
+  long long cprev = cidx(g, p[0], p[1], p[2]);
+#pragma unroll 1
+  for (int c = s0; c < s1; ++c) {
+    at(c, p);
+    const long long cc = cidx(g, p[0], p[1], p[2]);
+    march_face<T, RECON, A>(g, W, Bf, F, p[0], p[1], p[2], cprev, &carry[0][slot]);
+    cprev = cc;
+  }
 }
 
 // ------------------------------------------------------------ Steps 4, 8 --
@@ -472,7 +593,7 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
   Bh[N + c] = from_d<T>(by);
   Bh[2 * N + c] = from_d<T>(bz);
   // (the outer ghost layers of a padded grid see the wrap and carry no check)
-  if ((!(u5[0] > 0.0) || !isfinite(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);
+  if ((!pos_bits(u5[0]) || !finite_bits(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);
   T w8[8];
   if constexpr (std::is_same<T, float>::value) {
     const double bs[3] = {bxm + bx, bym + by, bzm + bz};
@@ -725,7 +846,14 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, dou
 template <class T>
 void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
                    unsigned long long* floors, cudaStream_t s) {
-    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors);
+    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, 0);
+  }
+template <class T>
+void Launch<T>::prim_slab(const Grid& g, int z0, int z1, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
+                          unsigned long long* floors, cudaStream_t s) {
+    dim3 gr = grid_of(g);
+    gr.z = z1 - z0;
+    k_prim<T><<<gr, dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, z0);
   }
 template <class T>
 void Launch<T>::flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s) {
@@ -762,6 +890,36 @@ void Launch<T>::flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const 
     if (a == 1) k_flux_hlld<T, 1><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
     if (a == 2) k_flux_hlld<T, 2><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
   }
+// segments per column of the y and z marches: enough threads to fill the GPU
+// (152 SMs x 2048 threads, twice over), segments of at least 16 cells
+inline int march_segments(const Grid& g, int a) {
+  const long long cols = (long long)g.n[0] * g.n[a == 1 ? 2 : 1];
+  const long long want = (2LL * 152 * 2048 + cols - 1) / cols;
+  long long most = g.n[a] / 16;
+  if (most < 1) most = 1;
+  return (int)(want < 1 ? 1 : (want > most ? most : want));
+}
+template <class T, int RC>
+void recon_flux_rc(const Grid& g, int a, const T* W, const T* Bf, T* F, cudaStream_t s) {
+  if (a == 0) {
+    const dim3 gr((g.n[0] + kFacesPerWarp - 1) / kFacesPerWarp, (g.n[1] + BY - 1) / BY, g.n[2]);
+    k_recon_flux_x<T, RC><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F);
+    return;
+  }
+  const int nseg = march_segments(g, a);
+  const int seg = (g.n[a] + nseg - 1) / nseg;
+  const int o = a == 1 ? 2 : 1;
+  const dim3 gr((g.n[0] + BX - 1) / BX, (g.n[o] + BY - 1) / BY, (g.n[a] + seg - 1) / seg);
+  if (a == 1) k_recon_flux_col<T, RC, 1><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F, seg);
+  else k_recon_flux_col<T, RC, 2><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F, seg);
+}
+template <class T>
+void Launch<T>::recon_flux(const Grid& g, int rc, int a, const T* W, const T* Bf, T* F, cudaStream_t s) {
+  if (rc == 0) recon_flux_rc<T, 0>(g, a, W, Bf, F, s);
+  else if (rc == 1) recon_flux_rc<T, 1>(g, a, W, Bf, F, s);
+  else if (rc == 2) recon_flux_rc<T, 2>(g, a, W, Bf, F, s);
+  else recon_flux_rc<T, 3>(g, a, W, Bf, F, s);
+}
 template <class T>
 void Launch<T>::emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s) {
     k_emf<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, E);

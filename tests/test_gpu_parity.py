@@ -166,6 +166,32 @@ def test_fixed_dt_step_matches_run(mhd):
     assert np.all(rel_l1(U.cpu().numpy(), ref) <= 1e-13)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk", "fp64_df"])
+@pytest.mark.parametrize("n,steps", [((40, 28, 21), 1), ((40, 28, 21), 3), ((20, 12, 5), 2)])
+def test_run_host_equals_copy_run_copy(mhd, precision, n, steps):
+    """mhd_run_host pipelines its host copies in z slabs against the slab
+    primitives of the first and last step (16 slabs; fewer than 16 planes
+    give one plane each): the state (floors included, set high enough to
+    fire) and the simulated time equal those of a copy, mhd_run and a copy
+    back, bit for bit, from pinned and from pageable host memory."""
+    U0 = turb(n, seed=11)
+    ref_sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision, rho_floor=0.9, p_floor=0.5)
+    ref = cuda(U0)
+    dts = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    ref_sim.run(ref, steps, dts)
+    ref_sim.status()
+    for pinned in (True, False):
+        sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision, rho_floor=0.9, p_floor=0.5)
+        host = torch.from_numpy(U0.copy())
+        if pinned:
+            host = host.pin_memory()
+        t = mhd.mhd_run_host(sim.ctx, host, steps)
+        assert torch.equal(host, ref.cpu()), (precision, n, steps, pinned)
+        assert t == float(dts.sum().item()) or abs(t - float(dts.sum().item())) <= 1e-15 * t
+        sim.close()
+    ref_sim.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
 @pytest.mark.parametrize("recon", ["plmc", "ppmc"])
 def test_uniform_state_bit_identical(mhd, precision, recon):
@@ -376,12 +402,15 @@ def test_diagnostics_totals_are_compensated(mhd):
         assert abs(tot[f] - math.fsum(U[f].ravel())) <= 1e-12 * math.fsum(np.abs(U[f]).ravel())
 
 
-def test_full_size_512_ppmc_sampled(mhd):
-    """512^3 turbulent box with PPMC (the precision comparison's workload):
-    one GPU step checked against the oracle at sampled cells."""
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_bulk", 2e-5)])
+def test_full_size_512_ppmc_sampled(mhd, precision, tol):
+    """512^3 turbulent box with PPMC (the benchmark workload): one GPU step
+    checked against the oracle at sampled cells, FP64 at 1e-12 and FP32-bulk
+    at 2e-5 of each value's scale (float reconstruction and Riemann solver,
+    one step)."""
     n = (512, 512, 512)
     U0 = I.turbulent_box(I.Box(*n), seed_v=1, seed_b=2)
-    sim = mhd.Sim(*n, cfl=0.3, recon="ppmc")
+    sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision)
     U = cuda(U0)
     dt = sim.dt(U)
     sim.step(U, dt)
@@ -395,4 +424,4 @@ def test_full_size_512_ppmc_sampled(mhd):
     for m, c in enumerate(cells):
         ref = _subbox_step(U0, c, dt, "ppmc")
         scale = np.abs(ref) + np.array([1, 1, 1, 1, 1, 0.5, 0.5, 0.5])
-        assert np.all(np.abs(got[:, m] - ref) <= 1e-12 * scale), (c, got[:, m] - ref)
+        assert np.all(np.abs(got[:, m] - ref) <= tol * scale), (c, got[:, m] - ref)
