@@ -50,7 +50,6 @@ def stage_bytes(T: int) -> dict:
         "recon": 8 * T + 14 * T,             # W in; W_L, W_R out (one axis)
         "flux_hlld": 15 * T + 7 * T,         # W_L, W_R, face B in; 7 fluxes out (one axis)
         "update_full": 64 + 18 * T + 64,     # U, fluxes, edges in; U out
-        "recon_flux": 8 * T + T + 7 * T,     # W, face B in; 7 fluxes out (one axis; states stay on chip)
         "dt": 0,
     }
 
@@ -109,9 +108,20 @@ _PLMC = {
         "flux_hlld": (0.0, 0.0, 3000 / 32, 162.5),
     },
 }
-# PPMC: the stages that do not depend on the reconstruction carry over; the
-# reconstruction and corrector Riemann kernels need captures of their own
+# PPMC: the reconstruction kernels captured on their own (-k regex:k_recon,
+# the three axes of one step at 128^3); the other stages do not depend on the
+# reconstruction and carry over where they are unchanged since their capture
 _PPMC = {prec: {k: v for k, v in tab.items() if k not in ("recon", "flux_hlld")} for prec, tab in _PLMC.items()}
+_PPMC["fp64"]["recon"] = (485.3, 599.0, 4356 / 32, 151.4)
+_PPMC["fp32_bulk"]["recon"] = (0.0, 0.0, 1565 / 32, 63.8)
+_PPMC["fp64_df"]["recon"] = (0.0, 0.0, 8646 / 32, 151.1)
+# the Riemann solver's fast-speed maximum, the edge fields and the kernels that
+# write W (which now also write the cells' reference fields) changed after
+# the captures above
+for _tab in (_PLMC, _PPMC):
+    for _prec in _tab:
+        for _k in ("flux_pcm", "flux_hlld", "emf", "prim", "update_half"):
+            _tab[_prec].pop(_k, None)
 COUNTERS = {"plmc": _PLMC, "ppmc": _PPMC}
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""

@@ -209,8 +209,8 @@ int mhd_adjoint_step_cfl(mhd_ctx* ctx, const double* U_n_dev, const double* gU_n
  * mhd_destroy): forward intermediates of one step plus cotangent buffers,
  * 148 words of the compute type (a float pair for MHD_FP64_DF) + 10
  * doubles per cell, plus the partials of the CFL reduction.  The adjoint
- * also uses the context's step workspace (mhd_workspace_bytes; 49 more
- * words per cell), whose contents no call relies on between calls.  No
+ * also uses 49 words per cell of the context's step workspace
+ * (mhd_workspace_bytes), whose contents no call relies on between calls.  No
  * device work.  Errors: MHD_ERR_ARG (cfg or bytes NULL, or cfg invalid). */
 int mhd_adjoint_workspace_bytes(const mhd_config* cfg, size_t* bytes);
 
@@ -280,8 +280,7 @@ const char* mhd_strerror(int code);
 #define MHD_STAGE_FLUX_HLLD 5   /* corrector HLLD fluxes (Step 7)             */
 #define MHD_STAGE_UPDATE_FULL 6 /* full-step update (Step 9)                  */
 #define MHD_STAGE_DT 7          /* dt finalisation                            */
-#define MHD_STAGE_RECON_FLUX 8  /* PLMC / PPMC states and corrector HLLD in one pass (Steps 6-7) */
-#define MHD_NUM_STAGES 9
+#define MHD_NUM_STAGES 8
 
 /* Library infrastructure, not in the paper.  Synchronises the context's
  * stream, turns the per-stage timing on (on != 0) or off and clears what

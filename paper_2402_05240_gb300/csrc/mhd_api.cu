@@ -30,6 +30,7 @@ struct mhd_ctx {
   size_t ws_bytes;
   // typed views into ws (element type = compute type)
   void *W, *F, *E, *WL, *WR, *Bh;
+  void* Er;                     // cell reference fields -(v x B_cc) written with W (step path)
   double* scal;                 // [0] dt_cur
   unsigned long long* dtbits;   // [0] dt reduction word
   unsigned long long* floors;   // [0..1] floor counters
@@ -67,7 +68,7 @@ constexpr size_t kAlign = 256;
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t W, F, E, WL, WR, Bh, scal, dtbits, floors, flags, red, Up, total;
+  size_t W, F, E, WL, WR, Bh, Er, scal, dtbits, floors, flags, red, Up, total;
 };
 
 bool padded(const mhd_config& c) {
@@ -108,6 +109,8 @@ Layout layout_of(const mhd_config& c) {
   L.WR = off;
   off += up(7 * N * ts);
   L.Bh = off;
+  off += up(3 * N * ts);
+  L.Er = off;
   off += up(3 * N * ts);
   L.scal = off;
   off += up(8 * sizeof(double));
@@ -186,20 +189,16 @@ template <class T> void step_body(mhd_ctx* c, double* U, int recon) {
   T* E = as<T>(c->E);
   for (int a = 0; a < 3; ++a)  // Steps 2-3
     prof(c, MHD_STAGE_FLUX_PCM, [&] { Launch<T>::flux_pcm(g, a, W, U, F, s); });
-  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 4
+  T* Er = as<T>(c->Er);
+  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s, Er); });        // Step 4
   prof(c, MHD_STAGE_UPDATE_HALF,
-       [&] { Launch<T>::update_half(g, U, F, E, c->scal, W, as<T>(c->Bh), c->flags, s); });  // Step 5
-#ifdef MHD_AB_STAGED
+       [&] { Launch<T>::update_half(g, U, F, E, c->scal, W, as<T>(c->Bh), c->flags, s, Er); });  // Step 5
   for (int a = 0; a < 3; ++a) {                                               // Steps 6-7
     prof(c, MHD_STAGE_RECON, [&] { Launch<T>::recon(g, recon, a, W, as<T>(c->WL), as<T>(c->WR), s); });
     prof(c, MHD_STAGE_FLUX_HLLD,
          [&] { Launch<T>::flux_hlld(g, a, as<T>(c->WL), as<T>(c->WR), as<T>(c->Bh), F, s); });
   }
-#else
-  for (int a = 0; a < 3; ++a)  // Steps 6-7, the interface states kept on chip
-    prof(c, MHD_STAGE_RECON_FLUX, [&] { Launch<T>::recon_flux(g, recon, a, W, as<T>(c->Bh), F, s); });
-#endif
-  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s); });            // Step 8
+  prof(c, MHD_STAGE_EMF, [&] { Launch<T>::emf(g, W, F, E, s, Er); });        // Step 8
   prof(c, MHD_STAGE_UPDATE_FULL, [&] { Launch<T>::update_full(g, U, F, E, c->scal, s); });  // Step 9
 }
 
@@ -227,7 +226,7 @@ template <class T> void run_begin(mhd_ctx* c, double* U) {
   cudaStream_t s = c->stream;
   cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);
-  Launch<T>::prim(c->g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+  Launch<T>::prim(c->g, U, as<T>(c->W), c->dtbits, c->flags, nullptr, s, as<T>(c->Er));
 }
 
 // one device-dt step: dt (Step 1), Steps 2-9, then floors, W^{n+1} and the
@@ -238,7 +237,8 @@ template <class T> void run_one(mhd_ctx* c, double* U, double* dt_log, int n, do
   prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, t_end, s); });
   step_body<T>(c, U, c->cfg.recon);
   refill(c, U);
-  prof(c, MHD_STAGE_PRIM, [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });
+  prof(c, MHD_STAGE_PRIM,
+       [&] { Launch<T>::prim(g, U, as<T>(c->W), c->dtbits, c->flags, c->floors, s, as<T>(c->Er)); });
 }
 
 template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_log) {
@@ -301,19 +301,21 @@ template <class T> int run_host_slabs(mhd_ctx* c, double* U_host, int nsteps) {
     const int k = q % S, below = (k + S - 1) % S;
     cudaStreamWaitEvent(s, evH[k], 0);
     cudaStreamWaitEvent(s, evH[below], 0);
-    Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
+    Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, nullptr, s, as<T>(c->Er));
   }
   for (int n = 0; n < nsteps; ++n) {
     prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, nullptr, n, c->flags, kNoEnd, s); });
     step_body<T>(c, D, c->cfg.recon);
     if (n + 1 < nsteps) {
-      prof(c, MHD_STAGE_PRIM, [&] { Launch<T>::prim(g, D, as<T>(c->W), c->dtbits, c->flags, c->floors, s); });
+      prof(c, MHD_STAGE_PRIM,
+           [&] { Launch<T>::prim(g, D, as<T>(c->W), c->dtbits, c->flags, c->floors, s, as<T>(c->Er)); });
       continue;
     }
     // the last step's floors and primitives slab by slab, each slab copied back once done
     for (int k = 0; k < S; ++k) {
       prof(c, MHD_STAGE_PRIM, [&] {
-        Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, c->floors, s);
+        Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, c->floors, s,
+                             as<T>(c->Er));
       });
       cudaEventRecord(evP[k], s);
       cudaStreamWaitEvent(c->io_stream[k & 1], evP[k], 0);
@@ -358,7 +360,7 @@ template <class T> int one_step(mhd_ctx* c, double* U, double dt, double* next_d
   cudaStream_t s = c->stream;
   mhd::launch_set_dt(c->scal, dt, s);
   double* S = enter(c, U);
-  Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, nullptr, s);
+  Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, nullptr, s, as<T>(c->Er));
   step_body<T>(c, S, c->cfg.recon);
   refill(c, S);
   if (next_dt) cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
@@ -383,7 +385,7 @@ template <class T> int step_sub(mhd_ctx* c, const double* Ug, const int gn[3], c
   gg.N = (long long)gn[0] * gn[1] * gn[2];
   mhd::launch_set_dt(c->scal, dt, s);
   mhd::launch_gather_sub(g, gg, off, Ug, c->Up, s);
-  Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, nullptr, s);
+  Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, nullptr, s, as<T>(c->Er));
   step_body<T>(c, c->Up, c->cfg.recon);
   Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, c->floors, s);
   mhd::launch_scatter_sub(g, gg, off, c->Up, Ug_out, s);
@@ -699,6 +701,7 @@ int mhd_init(mhd_ctx** out, const mhd_config* cfg, void* stream) {
   c->WL = b + L.WL;
   c->WR = b + L.WR;
   c->Bh = b + L.Bh;
+  c->Er = b + L.Er;
   c->scal = reinterpret_cast<double*>(b + L.scal);
   c->dtbits = reinterpret_cast<unsigned long long*>(b + L.dtbits);
   c->floors = reinterpret_cast<unsigned long long*>(b + L.floors);
@@ -762,7 +765,7 @@ int mhd_profile_read(mhd_ctx* c, double ms[MHD_NUM_STAGES], long long launches[M
 
 const char* mhd_stage_name(int stage) {
   static const char* names[MHD_NUM_STAGES] = {"prim", "flux_pcm", "emf", "update_half", "recon",
-                                              "flux_hlld", "update_full", "dt", "recon_flux"};
+                                              "flux_hlld", "update_full", "dt"};
   if (stage < 0 || stage >= MHD_NUM_STAGES) return "unknown";
   return names[stage];
 }

@@ -176,16 +176,26 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
   const T bn2 = bn * bn;
   // total pressures of both sides; the conserved energy is formed only for
   // the side whose states the flux is taken from
-  const T bbL = bn2 + wl[5] * wl[5] + wl[6] * wl[6];
-  const T bbR = bn2 + wr[5] * wr[5] + wr[6] * wr[6];
+  const T btL = wl[5] * wl[5] + wl[6] * wl[6], btR = wr[5] * wr[5] + wr[6] * wr[6];
+  const T bbL = bn2 + btL;
+  const T bbR = bn2 + btR;
   const T ptL = wl[4] + T(0.5) * bbL;
   const T ptR = wr[4] + T(0.5) * bbR;
   auto energy = [&](const T* w, T bb) {
     return w[4] * gm1i + T(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) + T(0.5) * bb;
   };
-  // max(c_f,L, c_f,R) as the root of the larger square (the root is monotone)
-  const T cmax = tsqrt<T>(max_nonneg<T>(fast_speed_sq<T>(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
-                                        fast_speed_sq<T>(gamma, wr[0], wr[4], bn, wr[5], wr[6])));
+  // max(c_f,L, c_f,R) (Eq. c_f with the face B_n): rho c_f^2 =
+  // (gamma P + B^2 + sqrt((gamma P - B^2)^2 + 4 gamma P B_t^2)) / 2 needs no
+  // division, the larger c_f^2 = X / rho is chosen by cross-multiplication,
+  // and only its side takes a reciprocal and a root
+  auto rho_cf2 = [&](T p, T bb, T bt) {
+    const T gp = gamma * p;
+    const T dd = gp - bb;
+    return T(0.5) * (gp + bb + tsqrt<T>(dd * dd + T(4) * gp * bt));
+  };
+  const T XL = rho_cf2(wl[4], bbL, btL), XR = rho_cf2(wr[4], bbR, btR);
+  const bool lmax = !nonneg_lt<T>(XL * wr[0], XR * wl[0]);
+  const T cmax = tsqrt<T>((lmax ? XL : XR) * trcp<T>(lmax ? wl[0] : wr[0]));
   const T SL = min_s<T>(wl[1], wr[1]) - cmax;
   const T SR = max_s<T>(wl[1], wr[1]) + cmax;
 

@@ -107,6 +107,21 @@ __device__ __forceinline__ PrimD prim_core(const Grid& g, double r, double m0, d
   return prim_core_ir(g, rho, __drcp_rn(rho), m0, m1, m2, e, b);
 }
 
+// Cell-centred reference electric field E = -(v x B_cc) of one cell (Sec. 2.2
+// Step 4, the reference field of the edge-field slopes), component A, from
+// the stored primitives.  The kernels that write W write it beside W once per
+// cell, so the edge fields read one value per cell instead of four primitives.
+template <class T, int A> __device__ __forceinline__ T cell_ref(const T* w8) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  return -(w8[1 + B] * w8[5 + C] - w8[1 + C] * w8[5 + B]);
+}
+template <class T> __device__ __forceinline__ void store_ref(T* __restrict__ Er, long long N, long long c, const T* w8) {
+  if (!Er) return;
+  Er[c] = cell_ref<T, 0>(w8);
+  Er[N + c] = cell_ref<T, 1>(w8);
+  Er[2 * N + c] = cell_ref<T, 2>(w8);
+}
+
 template <class T>
 __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
   w8[0] = from_d<T>(p.rho);
@@ -157,7 +172,8 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
 // (z0: first z plane of the launch, which covers planes z0 .. z0 + gridDim.z - 1)
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
-                                                 unsigned* flags, unsigned long long* floors, int z0) {
+                                                 unsigned* flags, unsigned long long* floors, int z0,
+                                                 T* __restrict__ Er) {
   CellIdx ci = cell_of_thread(g);
   ci.k += z0;
   T inv = T(0);
@@ -183,6 +199,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
                             U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c],
                             U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]};
       const double kem = prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8);
+      store_ref<T>(Er, N, c, w8);
       if (floors && lt_pos<double>(g.gm1 * (e - kem), g.p_floor)) {
         U[4 * N + c] = g.p_floor * g.igm1 + kem;
         if (in) atomicAdd(&floors[1], 1ull);
@@ -204,6 +221,7 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restric
       }
       const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
       store_w<T>(g, W, c, p, w8);
+      store_ref<T>(Er, N, c, w8);
       if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
     }
   }
@@ -323,114 +341,6 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
   for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
 }
 
-// ------------------------------------------------------ Steps 6-7 fused --
-// Reconstruction and HLLD of one axis in one pass: the interface states stay
-// in registers (W_L, W_R never reach memory) and every cell is reconstructed
-// once, up to one cell per tile or segment.  Same arithmetic as k_recon
-// followed by k_flux_hlld, so the same fluxes bit for bit.
-template <class T> __device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-template <> __device__ __forceinline__ df shfl_up1<df>(df v) {
-  return df(__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1));
-}
-
-// Faces of x: each warp reconstructs 32 consecutive cells x0 - 1 .. x0 + 30
-// and solves the 31 faces between them (x0 = 31 * tile); the state at the
-// upper face of cell x - 1 comes from the neighbouring lane.  Face f + 1/2 is
-// stored at cell f; tile 0 computes f = -1, the periodic face of cell nx - 1.
-constexpr int kFacesPerWarp = BX - 1;
-template <class T, int RECON>
-__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v)
-    k_recon_flux_x(Grid g, const T* __restrict__ W, const T* __restrict__ Bf, T* __restrict__ F) {
-  const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (j >= g.n[1]) return;  // uniform over the warp (one warp per row)
-  const int nx = g.n[0];
-  const int lane = threadIdx.x;
-  const int f = blockIdx.x * kFacesPerWarp + lane - 2;  // face f + 1/2 of this lane
-  int x = (f + 1) % nx;                                 // cell reconstructed by this lane (f + 1 >= -1)
-  if (x < 0) x += nx;
-  T wl[7], wr[7], pl[7];
-  recon_cell<T, RECON, 0>(g, W, x, j, k, wl, wr);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) pl[q] = shfl_up1<T>(wl[q]);
-  if (lane == 0 || f > nx - 2) return;
-  const long long N = g.N, c = cidx(g, f < 0 ? f + nx : f, j, k);
-  T fl[7];
-  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), pl, wr, Bf[c], fl);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) F[(long long)q * N + c] = fl[q];
-}
-
-// Faces of y (A = 1) or z (A = 2): each thread owns one column along A and
-// marches through a segment [s0, s1) of it, carrying the upper-face state of
-// the previous cell in its own slot of shared memory (in registers it would
-// push the reconstruction past its register budget); the segment starts
-// with the reconstruction of cell s0 - 1.  Face c - 1/2 is stored at cell
-// c - 1.  Warps span consecutive x, so every load and store is a coalesced
-// row.
-// one step of the column march: reconstruct cell (i, j, k), solve the face
-// below it (stored at cell cprev) with the carried upper-face state of the
-// cell below, then carry this cell's upper-face state.  Not inlined: inlined
-// into the loop, the reconstruction's constants and addresses are hoisted
-// out of it and the kernel spills.
-#ifdef MHD_AB_INLINE_MARCH
-#define MHD_MARCH_INL __forceinline__
-#else
-#define MHD_MARCH_INL __noinline__
-#endif
-template <class T, int RECON, int A>
-__device__ MHD_MARCH_INL void march_face(const Grid& g, const T* __restrict__ W, const T* __restrict__ Bf,
-                                        T* __restrict__ F, int i, int j, int k, long long cprev, T* carry) {
-  T wl[7], wr[7], pl[7], fl[7];
-  recon_cell<T, RECON, A>(g, W, i, j, k, wl, wr);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) pl[q] = carry[q * BX * BY];
-  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), pl, wr, Bf[A * g.N + cprev], fl);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * g.N + cprev] = fl[q];
-#pragma unroll
-  for (int q = 0; q < 7; ++q) carry[q * BX * BY] = wl[q];
-}
-
-// blocks per SM requested for the column march: its loop keeps the column's
-// indices live beside the reconstruction and the Riemann solver, which at
-// 128 registers spill for double and float pairs; float fits in 96
-template <class T, int RECON> struct MarchMinBlocks { static constexpr int v = 4; };
-template <int RECON> struct MarchMinBlocks<float, RECON> { static constexpr int v = 4; };
-
-template <class T, int RECON, int A>
-__global__ void __launch_bounds__(BX* BY, MarchMinBlocks<T, RECON>::v)
-    k_recon_flux_col(Grid g, const T* __restrict__ W, const T* __restrict__ Bf, T* __restrict__ F, int seg) {
-  static_assert(A == 1 || A == 2, "column march along y or z");
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int t = blockIdx.y * BY + threadIdx.y;  // z index (A = 1) or y index (A = 2)
-  constexpr int O = A == 1 ? 2 : 1;
-  if (i >= g.n[0] || t >= g.n[O]) return;
-  const int nA = g.n[A];
-  const int s0 = blockIdx.z * seg;
-  const int s1 = min(s0 + seg, nA);
-  auto at = [&](int c, int* ijk) {
-    ijk[0] = i;
-    ijk[A] = c;
-    ijk[O] = t;
-  };
-  __shared__ T carry[7][BX * BY];
-  const int slot = threadIdx.y * BX + threadIdx.x;
-  int p[3];
-  T wl[7], wr[7];
-  at(s0 == 0 ? nA - 1 : s0 - 1, p);
-  recon_cell<T, RECON, A>(g, W, p[0], p[1], p[2], wl, wr);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) carry[q][slot] = wl[q];
-  long long cprev = cidx(g, p[0], p[1], p[2]);
-#pragma unroll 1
-  for (int c = s0; c < s1; ++c) {
-    at(c, p);
-    const long long cc = cidx(g, p[0], p[1], p[2]);
-    march_face<T, RECON, A>(g, W, Bf, F, p[0], p[1], p[2], cprev, &carry[0][slot]);
-    cprev = cc;
-  }
-}
-
 // ------------------------------------------------------------ Steps 4, 8 --
 // Edge A of cell p at p + e_B/2 + e_C/2, (B, C) = (A+1, A+2): mean of the four
 // face fields plus the upwinded "face minus reference" slopes (Eq. emf-edge,
@@ -447,9 +357,9 @@ template <> __device__ __forceinline__ double upwind<double>(double m, double lo
   return b > 0 ? lo : hi;
 }
 
-template <class T, int A>
-__device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, const T* __restrict__ F, int i,
-                                        int j, int k) {
+template <class T, int A, bool REF>
+__device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
+                                        const T* __restrict__ Er, int i, int j, int k) {
   constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
   const long long N = g.N;
   int p[3] = {i, j, k};
@@ -462,7 +372,14 @@ __device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, 
   const long long qc = cidx(g, pc[0], pc[1], pc[2]), qbc = cidx(g, pbc[0], pbc[1], pbc[2]);
   const T* Fb = F + (long long)B * 7 * N;
   const T* Fc = F + (long long)C * 7 * N;
-  auto ref = [&](long long q) { return -(W[(1 + B) * N + q] * W[(5 + C) * N + q] - W[(1 + C) * N + q] * W[(5 + B) * N + q]); };
+  auto ref = [&](long long q) {
+    if constexpr (REF) {
+      return Er[(long long)A * N + q];
+    } else {
+      const T w8[8] = {T(0), W[N + q], W[2 * N + q], W[3 * N + q], T(0), W[5 * N + q], W[6 * N + q], W[7 * N + q]};
+      return cell_ref<T, A>(w8);
+    }
+  };
   const T bf0 = -Fb[5 * N + q00], bfc = -Fb[5 * N + qc];
   const T cf0 = Fc[6 * N + q00], cfb = Fc[6 * N + qb];
   const T r00 = ref(q00), rb = ref(qb), rc = ref(qc), rbc = ref(qbc);
@@ -474,15 +391,16 @@ __device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, 
   return avg + T(0.25) * (Dcp + Dcm + Dbp + Dbm);
 }
 
-template <class T>
+// REF: the cells' reference fields come from Er (written with W), else from W
+template <class T, bool REF>
 __global__ void __launch_bounds__(BX* BY) k_emf(Grid g, const T* __restrict__ W, const T* __restrict__ F,
-                                                T* __restrict__ E) {
+                                                const T* __restrict__ Er, T* __restrict__ E) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
   const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
-  E[c] = edge_field<T, 0>(g, W, F, ci.i, ci.j, ci.k);
-  E[N + c] = edge_field<T, 1>(g, W, F, ci.i, ci.j, ci.k);
-  E[2 * N + c] = edge_field<T, 2>(g, W, F, ci.i, ci.j, ci.k);
+  E[c] = edge_field<T, 0, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
+  E[N + c] = edge_field<T, 1, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
+  E[2 * N + c] = edge_field<T, 2, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
 }
 
 // ------------------------------------------------------------ Steps 5, 9 --
@@ -573,7 +491,8 @@ __device__ __forceinline__ double face_update(const Grid& g, const double* __res
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __restrict__ U0, const T* __restrict__ F,
                                                         const T* __restrict__ E, const double* __restrict__ dtp,
-                                                        T* __restrict__ W, T* __restrict__ Bh, unsigned* flags) {
+                                                        T* __restrict__ W, T* __restrict__ Bh, unsigned* flags,
+                                                        T* __restrict__ Er) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
   const int i = ci.i, j = ci.j, k = ci.k;
@@ -604,6 +523,7 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
     const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
     store_w<T>(g, W, c, p, w8);
   }
+  store_ref<T>(Er, N, c, w8);
 }
 
 // Step 9: U^{n+1} in place.  Each thread reads and writes only its own cell of
@@ -845,15 +765,15 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, dou
 
 template <class T>
 void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                   unsigned long long* floors, cudaStream_t s) {
-    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, 0);
+                   unsigned long long* floors, cudaStream_t s, T* Er) {
+    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, 0, Er);
   }
 template <class T>
 void Launch<T>::prim_slab(const Grid& g, int z0, int z1, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                          unsigned long long* floors, cudaStream_t s) {
+                          unsigned long long* floors, cudaStream_t s, T* Er) {
     dim3 gr = grid_of(g);
     gr.z = z1 - z0;
-    k_prim<T><<<gr, dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, z0);
+    k_prim<T><<<gr, dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, z0, Er);
   }
 template <class T>
 void Launch<T>::flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s) {
@@ -890,44 +810,15 @@ void Launch<T>::flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const 
     if (a == 1) k_flux_hlld<T, 1><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
     if (a == 2) k_flux_hlld<T, 2><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
   }
-// segments per column of the y and z marches: enough threads to fill the GPU
-// (152 SMs x 2048 threads, twice over), segments of at least 16 cells
-inline int march_segments(const Grid& g, int a) {
-  const long long cols = (long long)g.n[0] * g.n[a == 1 ? 2 : 1];
-  const long long want = (2LL * 152 * 2048 + cols - 1) / cols;
-  long long most = g.n[a] / 16;
-  if (most < 1) most = 1;
-  return (int)(want < 1 ? 1 : (want > most ? most : want));
-}
-template <class T, int RC>
-void recon_flux_rc(const Grid& g, int a, const T* W, const T* Bf, T* F, cudaStream_t s) {
-  if (a == 0) {
-    const dim3 gr((g.n[0] + kFacesPerWarp - 1) / kFacesPerWarp, (g.n[1] + BY - 1) / BY, g.n[2]);
-    k_recon_flux_x<T, RC><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F);
-    return;
-  }
-  const int nseg = march_segments(g, a);
-  const int seg = (g.n[a] + nseg - 1) / nseg;
-  const int o = a == 1 ? 2 : 1;
-  const dim3 gr((g.n[0] + BX - 1) / BX, (g.n[o] + BY - 1) / BY, (g.n[a] + seg - 1) / seg);
-  if (a == 1) k_recon_flux_col<T, RC, 1><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F, seg);
-  else k_recon_flux_col<T, RC, 2><<<gr, dim3(BX, BY), 0, s>>>(g, W, Bf, F, seg);
-}
 template <class T>
-void Launch<T>::recon_flux(const Grid& g, int rc, int a, const T* W, const T* Bf, T* F, cudaStream_t s) {
-  if (rc == 0) recon_flux_rc<T, 0>(g, a, W, Bf, F, s);
-  else if (rc == 1) recon_flux_rc<T, 1>(g, a, W, Bf, F, s);
-  else if (rc == 2) recon_flux_rc<T, 2>(g, a, W, Bf, F, s);
-  else recon_flux_rc<T, 3>(g, a, W, Bf, F, s);
-}
-template <class T>
-void Launch<T>::emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s) {
-    k_emf<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, E);
+void Launch<T>::emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s, const T* Er) {
+    if (Er) k_emf<T, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
+    else k_emf<T, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
   }
 template <class T>
 void Launch<T>::update_half(const Grid& g, const double* U, const T* F, const T* E, const double* dtp, T* W, T* Bh,
-                          unsigned* flags, cudaStream_t s) {
-    k_update_half<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp, W, Bh, flags);
+                          unsigned* flags, cudaStream_t s, T* Er) {
+    k_update_half<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp, W, Bh, flags, Er);
   }
 template <class T>
 void Launch<T>::update_full(const Grid& g, double* U, const T* F, const T* E, const double* dtp, cudaStream_t s) {

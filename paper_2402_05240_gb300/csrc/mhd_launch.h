@@ -31,19 +31,19 @@ struct Grid {
 // Launchers of the step kernels for compute type T (double: FP64 step,
 // float: FP32-bulk step); all asynchronous on stream s.
 template <class T> struct Launch {
+  // Er (may be null): also the cells' reference fields -(v x B_cc), 3 x N
   static void prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                   unsigned long long* floors, cudaStream_t s);
+                   unsigned long long* floors, cudaStream_t s, T* Er = nullptr);
   // prim on the z planes [z0, z1) only (0 <= z0 < z1 <= g.n[2])
   static void prim_slab(const Grid& g, int z0, int z1, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                        unsigned long long* floors, cudaStream_t s);
+                        unsigned long long* floors, cudaStream_t s, T* Er = nullptr);
   static void flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s);  // axis a
   static void recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s);
   static void flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s);
-  // recon then flux_hlld of axis a in one pass (the interface states stay on chip)
-  static void recon_flux(const Grid& g, int rc, int a, const T* W, const T* Bf, T* F, cudaStream_t s);
-  static void emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s);
+  // Er: the reference fields written with W (null: formed from W)
+  static void emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s, const T* Er = nullptr);
   static void update_half(const Grid& g, const double* U, const T* F, const T* E, const double* dtp, T* W, T* Bh,
-                          unsigned* flags, cudaStream_t s);
+                          unsigned* flags, cudaStream_t s, T* Er = nullptr);
   static void update_full(const Grid& g, double* U, const T* F, const T* E, const double* dtp, cudaStream_t s);
   static void widen(const T* src, double* dst, long long n, cudaStream_t s);
   static void narrow(const double* src, T* dst, long long n, cudaStream_t s);

@@ -306,7 +306,7 @@ def mhd_stage_hlld_vjp(gamma, precision: int, wl, wr, bn, gf, gwl, gwr, gbn, f, 
            "mhd_stage_hlld_vjp")
 
 
-MHD_NUM_STAGES = 9
+MHD_NUM_STAGES = 8
 
 
 def mhd_profile_enable(ctx, on: bool):

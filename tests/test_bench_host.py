@@ -50,14 +50,28 @@ def test_roofline_of_a_counted_stage(bench):
 
 
 def test_roofline_without_counters_is_hbm_bound(bench):
-    """A dominant stage without counters (here the PPMC reconstruction before
-    its capture) is reported against HBM with no traffic figure."""
+    """A dominant stage without counters (here the PCM predictor, changed
+    since its capture) is reported against HBM with no traffic figure."""
     n3 = 128 ** 3
-    ms = {"prim": 0.5, "flux_pcm": 1.0, "emf": 0.4, "update_half": 0.4, "recon": 2.4, "flux_hlld": 1.0,
+    ms = {"prim": 0.5, "flux_pcm": 3.0, "emf": 0.4, "update_half": 0.4, "recon": 2.4, "flux_hlld": 1.0,
           "update_full": 0.2}
+    assert "flux_pcm" not in bench.COUNTERS["ppmc"]["fp64"]
     r = bench.roofline_of(_prof(ms, 2), "fp64", n3, 6791.4, "measured", "ppmc")
+    assert r["kernel"] == "flux_pcm"
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
-    assert r["frac"] == pytest.approx(176 * n3 / 2.4e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
+    assert r["frac"] == pytest.approx(120 * n3 / 3.0e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
+
+
+def test_ppmc_reconstruction_is_bound_by_the_fp64_pipe(bench):
+    """The 512^3 PPMC headline's dominant stage: counted FP64-pipe operations
+    per launch over the launch time against the measured pipe rate."""
+    n3 = 512 ** 3
+    ms = {"prim": 32.2, "flux_pcm": 59.7, "emf": 23.8, "update_half": 21.8, "recon": 158.0, "flux_hlld": 59.6,
+          "update_full": 12.2}
+    r = bench.roofline_of(_prof(ms, 10), "fp64", n3, 6762.3, "measured", "ppmc")
+    ops = bench.COUNTERS["ppmc"]["fp64"]["recon"][0]
+    assert r["kernel"] == "recon" and r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(ops * n3 / 158.0e-3 / 1e9 / bench.FP64_PIPE_GINST, rel=1e-3)
 
 
 def test_partial_counters_give_no_step_dram_figure(bench):
