@@ -37,11 +37,6 @@ struct mhd_ctx {
   unsigned* flags;              // [0] error flags
   double* red;                  // diagnostics partials
   double* host_state;           // lazily allocated device copy for mhd_run_host
-  // mhd_run_host's copy pipeline (created on its first call): two copy
-  // streams and the events ordering slab copies against the slab primitives
-  cudaStream_t io_stream[2];
-  cudaEvent_t io_ev[2 * 16 + 3];
-  bool io_ready;
   size_t red_count;
   void* adj_ws;                 // adjoint workspace, allocated by the first adjoint call
   size_t adj_bytes;
@@ -246,86 +241,6 @@ template <class T> int run_steps(mhd_ctx* c, double* U, int nsteps, double* dt_l
   run_begin<T>(c, S);
   for (int n = 0; n < nsteps; ++n) run_one<T>(c, S, dt_log, n, kNoEnd);
   leave(c, U);
-  return cuda_status();
-}
-
-// mhd_run_host on a periodic grid with the host copies in z slabs on two copy
-// streams: the primitives of Step 1 start on each slab as soon as it and the
-// slab below it (whose top plane holds the lower z faces) have arrived, and
-// the last step's floors and primitives release each slab for its copy back
-// while the next slab is processed.  Same kernels and order of arithmetic as
-// mhd_run: the result is bit for bit that of copy, mhd_run, copy.
-constexpr int kIoSlabs = 16;
-int io_setup(mhd_ctx* c) {
-  if (c->io_ready) return MHD_OK;
-  for (int i = 0; i < 2; ++i)
-    if (cudaStreamCreateWithFlags(&c->io_stream[i], cudaStreamNonBlocking) != cudaSuccess) return MHD_ERR_CUDA;
-  for (cudaEvent_t& e : c->io_ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MHD_ERR_CUDA;
-  c->io_ready = true;
-  return MHD_OK;
-}
-
-template <class T> int run_host_slabs(mhd_ctx* c, double* U_host, int nsteps) {
-  const Grid& g = c->g;
-  cudaStream_t s = c->stream;
-  const int nz = g.n[2];
-  const int S = nz < kIoSlabs ? nz : kIoSlabs;
-  const size_t plane = (size_t)g.n[0] * g.n[1];
-  cudaEvent_t* evH = c->io_ev;
-  cudaEvent_t* evP = c->io_ev + kIoSlabs;
-  cudaEvent_t ev0 = c->io_ev[2 * kIoSlabs], evD0 = c->io_ev[2 * kIoSlabs + 1], evD1 = c->io_ev[2 * kIoSlabs + 2];
-  double* D = c->host_state;
-  auto zb = [&](int k) { return (int)((long long)k * nz / S); };
-  auto copy_slab = [&](int k, cudaMemcpyKind kind, cudaStream_t cs) {
-    const size_t off = (size_t)zb(k) * plane, n = (size_t)(zb(k + 1) - zb(k)) * plane * sizeof(double);
-    for (int f = 0; f < 8; ++f) {
-      const size_t o = (size_t)f * g.N + off;
-      const cudaError_t e = kind == cudaMemcpyHostToDevice ? cudaMemcpyAsync(D + o, U_host + o, n, kind, cs)
-                                                           : cudaMemcpyAsync(U_host + o, D + o, n, kind, cs);
-      if (e != cudaSuccess) return false;
-    }
-    return true;
-  };
-  // the device buffer may still be read by earlier work on the context's stream
-  cudaEventRecord(ev0, s);
-  for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(c->io_stream[i], ev0, 0);
-  for (int k = 0; k < S; ++k) {
-    if (!copy_slab(k, cudaMemcpyHostToDevice, c->io_stream[k & 1])) return MHD_ERR_CUDA;
-    cudaEventRecord(evH[k], c->io_stream[k & 1]);
-  }
-  // run_begin in slabs: slab k needs slabs k and k - 1; slab 0 the last one
-  cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
-  cudaMemsetAsync(c->scal + 1, 0, sizeof(double), s);
-  for (int q = 1; q <= S; ++q) {
-    const int k = q % S, below = (k + S - 1) % S;
-    cudaStreamWaitEvent(s, evH[k], 0);
-    cudaStreamWaitEvent(s, evH[below], 0);
-    Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, nullptr, s, as<T>(c->Er));
-  }
-  for (int n = 0; n < nsteps; ++n) {
-    prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, nullptr, n, c->flags, kNoEnd, s); });
-    step_body<T>(c, D, c->cfg.recon);
-    if (n + 1 < nsteps) {
-      prof(c, MHD_STAGE_PRIM,
-           [&] { Launch<T>::prim(g, D, as<T>(c->W), c->dtbits, c->flags, c->floors, s, as<T>(c->Er)); });
-      continue;
-    }
-    // the last step's floors and primitives slab by slab, each slab copied back once done
-    for (int k = 0; k < S; ++k) {
-      prof(c, MHD_STAGE_PRIM, [&] {
-        Launch<T>::prim_slab(g, zb(k), zb(k + 1), D, as<T>(c->W), c->dtbits, c->flags, c->floors, s,
-                             as<T>(c->Er));
-      });
-      cudaEventRecord(evP[k], s);
-      cudaStreamWaitEvent(c->io_stream[k & 1], evP[k], 0);
-      if (!copy_slab(k, cudaMemcpyDeviceToHost, c->io_stream[k & 1])) return MHD_ERR_CUDA;
-    }
-  }
-  cudaEventRecord(evD0, c->io_stream[0]);
-  cudaEventRecord(evD1, c->io_stream[1]);
-  cudaStreamWaitEvent(s, evD0, 0);
-  cudaStreamWaitEvent(s, evD1, 0);
   return cuda_status();
 }
 
@@ -724,13 +639,6 @@ void mhd_destroy(mhd_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
   if (c->host_state) cudaFree(c->host_state);
-  if (c->io_ready) {
-    for (int i = 0; i < 2; ++i) {
-      cudaStreamSynchronize(c->io_stream[i]);
-      cudaStreamDestroy(c->io_stream[i]);
-    }
-    for (cudaEvent_t e : c->io_ev) cudaEventDestroy(e);
-  }
   if (c->adj_ws) cudaFree(c->adj_ws);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
@@ -851,17 +759,10 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
     }
   }
   cudaStream_t s = c->stream;
-  if (!c->Up && nsteps > 0) {
-    int st = io_setup(c);
-    if (st != MHD_OK) return st;
-    st = with_type(c->cfg.precision, [&](auto t) { return run_host_slabs<MHD_T>(c, U_host, nsteps); });
-    if (st != MHD_OK) return st;
-  } else {
-    if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
-    int st = mhd_run(c, c->host_state, nsteps, nullptr);
-    if (st != MHD_OK) return st;
-    if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
-  }
+  if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
+  int st = mhd_run(c, c->host_state, nsteps, nullptr);
+  if (st != MHD_OK) return st;
+  if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   double t = 0;
   if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;

@@ -169,13 +169,10 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
 // rho and E are written, so this is race-free in place.  The CFL maximum and
 // the floor counters take interior cells only (ghost cells of a padded grid
 // are copies).
-// (z0: first z plane of the launch, which covers planes z0 .. z0 + gridDim.z - 1)
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
-                                                 unsigned* flags, unsigned long long* floors, int z0,
-                                                 T* __restrict__ Er) {
-  CellIdx ci = cell_of_thread(g);
-  ci.k += z0;
+                                                 unsigned* flags, unsigned long long* floors, T* __restrict__ Er) {
+  const CellIdx ci = cell_of_thread(g);
   T inv = T(0);
   if (ci.ok) {
     const int i = ci.i, j = ci.j, k = ci.k;
@@ -766,14 +763,7 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, dou
 template <class T>
 void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
                    unsigned long long* floors, cudaStream_t s, T* Er) {
-    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, 0, Er);
-  }
-template <class T>
-void Launch<T>::prim_slab(const Grid& g, int z0, int z1, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                          unsigned long long* floors, cudaStream_t s, T* Er) {
-    dim3 gr = grid_of(g);
-    gr.z = z1 - z0;
-    k_prim<T><<<gr, dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, z0, Er);
+    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, Er);
   }
 template <class T>
 void Launch<T>::flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s) {

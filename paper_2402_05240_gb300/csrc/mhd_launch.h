@@ -34,9 +34,6 @@ template <class T> struct Launch {
   // Er (may be null): also the cells' reference fields -(v x B_cc), 3 x N
   static void prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
                    unsigned long long* floors, cudaStream_t s, T* Er = nullptr);
-  // prim on the z planes [z0, z1) only (0 <= z0 < z1 <= g.n[2])
-  static void prim_slab(const Grid& g, int z0, int z1, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                        unsigned long long* floors, cudaStream_t s, T* Er = nullptr);
   static void flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s);  // axis a
   static void recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s);
   static void flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s);

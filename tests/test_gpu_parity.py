@@ -167,13 +167,12 @@ def test_fixed_dt_step_matches_run(mhd):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk", "fp64_df"])
-@pytest.mark.parametrize("n,steps", [((40, 28, 21), 1), ((40, 28, 21), 3), ((20, 12, 5), 2)])
+@pytest.mark.parametrize("n,steps", [((40, 28, 21), 3), ((20, 12, 5), 2)])
 def test_run_host_equals_copy_run_copy(mhd, precision, n, steps):
-    """mhd_run_host pipelines its host copies in z slabs against the slab
-    primitives of the first and last step (16 slabs; fewer than 16 planes
-    give one plane each): the state (floors included, set high enough to
-    fire) and the simulated time equal those of a copy, mhd_run and a copy
-    back, bit for bit, from pinned and from pageable host memory."""
+    """mhd_run_host (the host-buffer entry point): the state (floors
+    included, set high enough to fire) and the simulated time equal those of
+    a copy, mhd_run and a copy back, bit for bit, from pinned and from
+    pageable host memory, in every precision."""
     U0 = turb(n, seed=11)
     ref_sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision, rho_floor=0.9, p_floor=0.5)
     ref = cuda(U0)
