@@ -106,6 +106,9 @@ __device__ __forceinline__ bool pos_bits(double x) {
   const long long b = dbits(x);
   return b > 0 && b <= 0x7ff0000000000000LL;
 }
+// |x|; for double on the bit pattern
+template <class T> __device__ __forceinline__ T absv(T x) { return fabs(x); }
+template <> __device__ __forceinline__ double absv<double>(double x) { return __longlong_as_double(dbits(x) & kAbsBits); }
 // order key: sign-magnitude patterns mapped to a monotone signed integer
 __device__ __forceinline__ long long dkey(double x) {
   const long long b = dbits(x);
@@ -340,17 +343,19 @@ template <class T> __device__ __forceinline__ void eig_build(T gamma, const T* w
   E.cs = E.a * fabs(bn) * E.isr * rcf;
   const T ibt = gt0<T>(bt2r) ? trsqrt<T>(bt2r) : T(0);
   const T btn = bt2r * ibt * E.isr;  // |B_t| / sqrt(rho)
+  // one formula for both signs of D (only the assignment of the two members
+  // to alpha_f and alpha_s depends on it), so neighbouring cells with
+  // different signs share one path through the FP64 pipe
   if (is0<T>(sd)) {
     E.af = T(1);
     E.as = T(0);
-  } else if (ge0<T>(D)) {
-    const T q = trsqrt<T>(T(2) * sd * (sd + D));
-    E.af = (sd + D) * q;
-    E.as = T(2) * E.a * btn * q;
   } else {
-    const T q = trsqrt<T>(T(2) * sd * (sd - D));
-    E.af = T(2) * E.a * btn * q;
-    E.as = (sd - D) * q;
+    const bool dpos = ge0<T>(D);
+    const T sa = sd + absv<T>(D);
+    const T q = trsqrt<T>(T(2) * sd * sa);
+    const T big = sa * q, small = T(2) * E.a * btn * q;
+    E.af = dpos ? big : small;
+    E.as = dpos ? small : big;
   }
   if (is0<T>(bt2r)) {
     E.b1 = T(0.70710678118654752440);
@@ -463,6 +468,10 @@ template <class T> __device__ __forceinline__ void van_leer7(const T* dL, const 
 // denominator lies in [2^-140, 2^140] so that no partial product leaves the
 // normal range; otherwise one reciprocal each.  The FP64 pipe bounds the
 // FP64 step and a reciprocal costs about 7 of its multiplies.
+static __device__ __noinline__ void rcp7_call(const double* s, double* inv) {
+#pragma unroll
+  for (int q = 0; q < 7; ++q) inv[q] = trcp<double>(s[q]);
+}
 template <> __device__ __forceinline__ void van_leer7<double>(const double* dL, const double* dR, double* dG) {
   double s[7], p[7], inv[7];
   bool act[7];
@@ -474,20 +483,19 @@ template <> __device__ __forceinline__ void van_leer7<double>(const double* dL, 
     const long long e = (dbits(s[q]) >> 52) & 0x7ff;
     ok &= (e >= 1023 - 140) & (e <= 1023 + 140);
   }
-  if (ok) {
-    p[0] = s[0];
+  p[0] = s[0];
 #pragma unroll
-    for (int q = 1; q < 7; ++q) p[q] = p[q - 1] * s[q];
-    double r = trcp<double>(p[6]);
+  for (int q = 1; q < 7; ++q) p[q] = p[q - 1] * s[q];
+  double r = trcp<double>(p[6]);
 #pragma unroll
-    for (int q = 6; q > 0; --q) {
-      inv[q] = r * p[q - 1];
-      r = r * s[q];
-    }
-    inv[0] = r;
-  } else {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) inv[q] = trcp<double>(s[q]);
+  for (int q = 6; q > 0; --q) {
+    inv[q] = r * p[q - 1];
+    r = r * s[q];
+  }
+  inv[0] = r;
+  // the rare fallback is a call made only in warps where some lane needs it
+  if (__any_sync(__activemask(), !ok)) {
+    if (!ok) rcp7_call(s, inv);
   }
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -571,40 +579,62 @@ template <class T> __device__ __forceinline__ T d2lim4(T x, T y, T z, T t) {
 
 // a / b for |a| <= |b|, b != 0
 template <class T> __device__ __forceinline__ T ratio_le1(T a, T b) { return a / b; }
+static __device__ __noinline__ double div_call(double a, double b) { return a / b; }
 template <> __device__ __forceinline__ double ratio_le1<double>(double a, double b) {
-  // biased exponent >= 64: 1/b is finite and normal
-  return ((dbits(b) >> 52) & 0x7ff) >= 64 ? a * trcp<double>(b) : a / b;
+  // biased exponent >= 64: 1/b is finite and normal.  The division for
+  // smaller b is a call made only in warps where some lane needs it (inlined,
+  // the compiler evaluates it in every warp, on the FP64 pipe)
+  const bool tiny = ((dbits(b) >> 52) & 0x7ff) < 64;
+  double r = a * trcp<double>(b);
+  if (__any_sync(__activemask(), tiny)) {
+    if (tiny) r = div_call(a, b);
+  }
+  return r;
 }
 
 // q[0..4] = characteristic deviations of cells i-2..i+2 from cell i (q[2] = 0);
-// returns the limited deviations of the two interface values.
+// returns the limited deviations of the two interface values.  Written for
+// the deviation form: the centre's zero is not added, subtracted or
+// multiplied, and sign flips and doublings are exact bit operations, so
+// only the arithmetic the limiter needs reaches the FP64 pipe.  Same values
+// as the formulas with q[2] kept, up to the sign of zero results.
+template <class T> __device__ __forceinline__ T neg(T x) { return -x; }
+template <> __device__ __forceinline__ double neg<double>(double x) { return __longlong_as_double(dbits(x) ^ kNegZero); }
 template <class T> __device__ __forceinline__ void ppm_one(const T* q, T& qm, T& qp) {
   const T c7 = from_d<T>(7.0 / 12.0), c1 = from_d<T>(1.0 / 12.0), c6 = from_d<T>(1.0 / 6.0);
-  qm = c7 * (q[1] + q[2]) - c1 * (q[0] + q[3]);
-  qp = c7 * (q[2] + q[3]) - c1 * (q[1] + q[4]);
-  const T d2m1 = q[0] - T(2) * q[1] + q[2];
-  const T d20 = q[1] - T(2) * q[2] + q[3];
-  const T d2p1 = q[2] - T(2) * q[3] + q[4];
-  if (neg_prod<T>(qm - q[1], q[2] - qm)) {
-    const T d2c = T(3) * (q[1] - T(2) * qm + q[2]);
-    qm = T(0.5) * (q[1] + q[2]) - d2lim3<T>(d2c, d2m1, d20) * c6;
+  const T a = q[0], b = q[1], d = q[3], e = q[4];  // cells i-2, i-1, i+1, i+2
+  qm = c7 * b - c1 * (a + d);
+  qp = c7 * d - c1 * (b + e);
+  const T d2m1 = a - T(2) * b;
+  const T d20 = b + d;
+  const T d2p1 = e - T(2) * d;
+  // interface limiter where the value leaves the range of its two cells.
+  // Both interfaces share one body, fed the operands of the lower interface
+  // where it needs limiting, else of the upper: a warp whose lanes limit
+  // different interfaces runs it once; a second pass runs only where a lane
+  // limits both.
+  const bool lm = pos_prod<T>(qm - b, qm), lp = neg_prod<T>(qp, d - qp);
+  if (lm || lp) {
+    const T x = lm ? b : d, v = lm ? qm : qp, y = lm ? d2m1 : d20, z = lm ? d20 : d2p1;
+    const T lim = T(0.5) * x - d2lim3<T>(T(3) * (x - T(2) * v), y, z) * c6;
+    if (lm) qm = lim;
+    else qp = lim;
+    if (lm && lp) qp = T(0.5) * d - d2lim3<T>(T(3) * (d - T(2) * qp), d20, d2p1) * c6;
   }
-  if (neg_prod<T>(qp - q[2], q[3] - qp)) {
-    const T d2c = T(3) * (q[2] - T(2) * qp + q[3]);
-    qp = T(0.5) * (q[2] + q[3]) - d2lim3<T>(d2c, d20, d2p1) * c6;
-  }
-  const T dqm = q[2] - qm, dqp = qp - q[2];
-  if (!pos_prod<T>(dqm, dqp) || !pos_prod<T>(q[2] - q[1], q[3] - q[2])) {
-    const T d2f = T(6) * (qm - T(2) * q[2] + qp);
+  // cell limiter: at an extremum both deviations scale by the curvature
+  // ratio, elsewhere an overshoot is clipped to twice the other deviation
+  if (!neg_prod<T>(qm, qp) || !neg_prod<T>(b, d)) {
+    const T d2f = T(6) * (qm + qp);
     T r = T(0);
     // (|d2lim4 / d2f| <= 1: a reciprocal where d2f is far from the
     // underflow range, else the division)
     if (!is0<T>(d2f)) r = ratio_le1<T>(d2lim4<T>(d2f, d2m1, d20, d2p1), d2f);
-    qm = q[2] - r * dqm;
-    qp = q[2] + r * dqp;
+    qm = r * qm;
+    qp = r * qp;
   } else {
-    if (abs_ge_twice<T>(dqm, dqp)) qm = q[2] - twice<T>(dqp);
-    if (abs_ge_twice<T>(dqp, dqm)) qp = q[2] + twice<T>(dqm);
+    const T m0 = qm;
+    if (abs_ge_twice<T>(qm, qp)) qm = neg<T>(twice<T>(qp));
+    if (abs_ge_twice<T>(qp, m0)) qp = neg<T>(twice<T>(m0));
   }
 }
 

@@ -343,15 +343,29 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restric
 // face fields plus the upwinded "face minus reference" slopes (Eq. emf-edge,
 // Eqs. emf-upwind-slope, emf-slope), upwinded by the sign of the mass flux of
 // the face the slope sits on (mean when it is exactly zero).
-template <class T> __device__ __forceinline__ T upwind(T m, T lo, T hi) {
+// The slope upwinded by the mass flux m: (f_lo - r_lo) where m > 0, (f_hi -
+// r_hi) where m < 0, their mean where m == 0.
+template <class T> __device__ __forceinline__ T upwind(T m, T flo, T rlo, T fhi, T rhi) {
+  const T lo = flo - rlo, hi = fhi - rhi;
   return m > T(0) ? lo : (m < T(0) ? hi : T(0.5) * (lo + hi));
 }
-// double: the sign test on the bit pattern (integer pipes), the mean only
-// for an exactly zero mass flux
-template <> __device__ __forceinline__ double upwind<double>(double m, double lo, double hi) {
+// double: the sign tests on the bit pattern (integer pipes); the operands are
+// selected first, so one difference is formed per slope, and the mean
+// (needed only for an exactly zero mass flux, e.g. a fluid at rest) is a
+// call made only in warps where some lane needs it -- inlined, the compiler
+// evaluates it in every warp, two FP64-pipe instructions per slope
+__device__ __noinline__ static double upwind_mean(double flo, double rlo, double fhi, double rhi) {
+  return 0.5 * ((flo - rlo) + (fhi - rhi));
+}
+template <> __device__ __forceinline__ double upwind<double>(double m, double flo, double rlo, double fhi, double rhi) {
   const long long b = dbits(m);
-  if (__builtin_expect((b & kAbsBits) == 0, 0)) return 0.5 * (lo + hi);
-  return b > 0 ? lo : hi;
+  const bool z = (b & kAbsBits) == 0;
+  const bool lo = b > 0;
+  double d = (lo ? flo : fhi) - (lo ? rlo : rhi);
+  if (__any_sync(__activemask(), z)) {
+    if (z) d = upwind_mean(flo, rlo, fhi, rhi);
+  }
+  return d;
 }
 
 template <class T, int A, bool REF>
@@ -381,10 +395,10 @@ __device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, 
   const T cf0 = Fc[6 * N + q00], cfb = Fc[6 * N + qb];
   const T r00 = ref(q00), rb = ref(qb), rc = ref(qc), rbc = ref(qbc);
   const T avg = T(0.25) * (bfc + bf0 + cfb + cf0);
-  const T Dcp = upwind<T>(Fb[qc], cf0 - rc, cfb - rbc);
-  const T Dcm = upwind<T>(Fb[q00], cf0 - r00, cfb - rb);
-  const T Dbp = upwind<T>(Fc[qb], bf0 - rb, bfc - rbc);
-  const T Dbm = upwind<T>(Fc[q00], bf0 - r00, bfc - rc);
+  const T Dcp = upwind<T>(Fb[qc], cf0, rc, cfb, rbc);
+  const T Dcm = upwind<T>(Fb[q00], cf0, r00, cfb, rb);
+  const T Dbp = upwind<T>(Fc[qb], bf0, rb, bfc, rbc);
+  const T Dbm = upwind<T>(Fc[q00], bf0, r00, bfc, rc);
   return avg + T(0.25) * (Dcp + Dcm + Dbp + Dbm);
 }
 
