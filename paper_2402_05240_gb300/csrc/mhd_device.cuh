@@ -212,59 +212,67 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     F[5] = w[5] * w[1] - bn * w[2];
     F[6] = w[6] * w[1] - bn * w[3];
   };
-  if (ge0<T>(SL)) {
-    phys(wl, energy(wl, bbL), ptL, f);
+  // Supersonic faces take the upwind side's physical flux; the others its
+  // star or double-star flux.  One physical flux serves both cases, so a
+  // warp mixing them evaluates it once.
+  const bool sub = !ge0<T>(SL) && !le0<T>(SR);
+  T dL = T(0), dR = T(0), rdL = T(0), rdR = T(0), SM = T(0), pts = T(0);
+  if (sub) {
+    dL = SL - wl[1];
+    dR = SR - wr[1];
+    rdL = wl[0] * dL;
+    rdR = wr[0] * dR;
+    const T iden = trcp<T>(rdR - rdL);
+    SM = (rdR * wr[1] - rdL * wl[1] - ptR + ptL) * iden;
+    pts = (rdR * ptL - rdL * ptR + rdL * rdR * (wr[1] - wl[1])) * iden;
+  }
+  // the side whose states the flux comes from (ties to the left)
+  const bool left = sub ? ge0<T>(SM) : ge0<T>(SL);
+  const T* w = left ? wl : wr;
+  const T pt = left ? ptL : ptR;
+  const T e = energy(w, left ? bbL : bbR);
+  T F[7];
+  phys(w, e, pt, F);
+  if (!sub) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) f[q] = F[q];
     return;
   }
-  if (le0<T>(SR)) {
-    phys(wr, energy(wr, bbR), ptR, f);
-    return;
-  }
-  const T dL = SL - wl[1], dR = SR - wr[1];
-  const T rdL = wl[0] * dL, rdR = wr[0] * dR;
-  const T iden = trcp<T>(rdR - rdL);
-  const T SM = (rdR * wr[1] - rdL * wl[1] - ptR + ptL) * iden;
-  const T pts = (rdR * ptL - rdL * ptR + rdL * rdR * (wr[1] - wl[1])) * iden;
 
   // single-star states of one side: rho*, v*, w*, By*, Bz* (both sides feed
   // the double-star states)
   struct Star {
     T r, v, w, by, bz, sq, rsq, iSM;
   };
-  auto star = [&](const T* w, T S, T d, T rd) {
-    Star s;
-    s.iSM = trcp<T>(S - SM);
-    s.r = rd * s.iSM;
+  auto star = [&](const T* ws, T S, T d, T rd) {
+    Star st;
+    st.iSM = trcp<T>(S - SM);
+    st.r = rd * st.iSM;
     const T D = rd * (S - SM) - bn2;
     if (abs_lt<T>(D, Eps<T>::hlld * pts)) {
-      s.v = w[2];
-      s.w = w[3];
-      s.by = w[5];
-      s.bz = w[6];
+      st.v = ws[2];
+      st.w = ws[3];
+      st.by = ws[5];
+      st.bz = ws[6];
     } else {
       const T iD = trcp<T>(D);
-      const T t = bn * (SM - w[1]) * iD;
-      s.v = w[2] - w[5] * t;
-      s.w = w[3] - w[6] * t;
+      const T t = bn * (SM - ws[1]) * iD;
+      st.v = ws[2] - ws[5] * t;
+      st.w = ws[3] - ws[6] * t;
       const T q = (rd * d - bn2) * iD;
-      s.by = w[5] * q;
-      s.bz = w[6] * q;
+      st.by = ws[5] * q;
+      st.bz = ws[6] * q;
     }
-    s.rsq = trsqrt<T>(s.r);
-    s.sq = s.r * s.rsq;
-    return s;
+    st.rsq = trsqrt<T>(st.r);
+    st.sq = st.r * st.rsq;
+    return st;
   };
   const Star sL = star(wl, SL, dL, rdL);
   const Star sR = star(wr, SR, dR, rdR);
 
-  // the region containing x/t = 0 lies on the side of S_M (ties to the left)
-  const bool left = ge0<T>(SM);
-  const T* w = left ? wl : wr;
   const Star& s = left ? sL : sR;
   const T S = left ? SL : SR;
   const T d = left ? dL : dR;
-  const T pt = left ? ptL : ptR;
-  const T e = energy(w, left ? bbL : bbR);
   // star energy E* of that side
   const T vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
   const T vbs = SM * bn + s.v * s.by + s.w * s.bz;
@@ -291,8 +299,6 @@ __device__ __forceinline__ void hlld(T gamma, T gm1i, const T* wl, const T* wr, 
     else
       ess = es + s.sq * (SM * bn + s.v * s.by + s.w * s.bz - vbss) * sg;
   }
-  T F[7];
-  phys(w, e, pt, F);
   const T U0[7] = {w[0], w[0] * w[1], w[0] * w[2], w[0] * w[3], e, w[5], w[6]};
   const T Us[7] = {s.r, s.r * SM, s.r * s.v, s.r * s.w, es, s.by, s.bz};
   // F* = F + S (U* - U)
