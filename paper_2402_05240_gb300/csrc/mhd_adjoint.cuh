@@ -544,29 +544,34 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
   gq[2] += gq2;
 }
 
-// w[0..4]: cells i-2..i+2; accumulates gw[0..4] and gbn
-template <class T>
-__device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, const T (*w)[7], T bn, const T* gwl_in, const T* gwr_in,
-                         T (*gw)[7], T& gbn) {
+// Reverse of PPMC for one cell.  wload(m, w7) loads the directional state of
+// stencil cell m (0..4 for i-2..i+2); put(m, g7) receives the cotangent of
+// stencil cell m != 2, once each; gw2 (7) receives that of cell i and gbn
+// that of its cell-centred B_n.  The stencil is loaded where it is used and
+// the slots are written as they are formed, so the live state is the
+// eigensystem, the characteristic deviations and their cotangents (holding
+// the whole stencil and its cotangents spilled the float-pair kernel).
+template <class T, class Load, class Put>
+__device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, Load wload, T bn, const T* gwl_in, const T* gwr_in,
+                         Put put, T* gw2, T& gbn) {
+  T w2[7];
+  wload(2, w2);
   Eig<T> E;
-  eig_build<T>(gamma, w[2], bn, E);
+  eig_build<T>(gamma, w2, bn, E);
   const T ir = E.ir;
-  T d[5][7], qs[5][7];
+  T qs[4][7];  // deviations of cells i-2, i-1, i+1, i+2 (q of cell i is 0)
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
+  for (int k = 0; k < 4; ++k) {
+    T wm[7], d[7];
+    wload(k < 2 ? k : k + 1, wm);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) d[m][c] = w[m][c] - w[2][c];
-    if (m == 2) {
-#pragma unroll
-      for (int c = 0; c < 7; ++c) qs[2][c] = T(0);
-    } else {
-      eig_left<T>(E, d[m], qs[m]);
-    }
+    for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
+    eig_left<T>(E, d, qs[k]);
   }
   T dm[7], dp[7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
-    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[3][c], qs[4][c]};
+    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
     T qm, qp;
     ppm_one<T>(col, qm, qp);
     dm[c] = qm;
@@ -581,48 +586,45 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, const T (*w)[7], T bn,
     gwl[c] = gwl_in[c];
     gwr[c] = gwr_in[c];
   }
-  if (w[2][0] + Wp[0] < rho_floor) gwl[0] = T(0);
-  if (w[2][4] + Wp[4] < p_floor) gwl[4] = T(0);
-  if (w[2][0] + Wm[0] < rho_floor) gwr[0] = T(0);
-  if (w[2][4] + Wm[4] < p_floor) gwr[4] = T(0);
+  if (w2[0] + Wp[0] < rho_floor) gwl[0] = T(0);
+  if (w2[4] + Wp[4] < p_floor) gwl[4] = T(0);
+  if (w2[0] + Wm[0] < rho_floor) gwr[0] = T(0);
+  if (w2[4] + Wm[4] < p_floor) gwr[4] = T(0);
   EigG<T> gE;
   gE.zero();
   T gdm[7], gdp[7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
-    gw[2][c] += gwl[c] + gwr[c];
+    gw2[c] = gwl[c] + gwr[c];
     gdm[c] = gdp[c] = T(0);
   }
   eig_right_vjp<T>(E, dp, gwl, gdp, gE);
   eig_right_vjp<T>(E, dm, gwr, gdm, gE);
-  T gqs[5][7];
-#pragma unroll
-  for (int m = 0; m < 5; ++m)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) gqs[m][c] = T(0);
+  T gqs[4][7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
-    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[3][c], qs[4][c]};
+    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
     T gcol[5] = {T(0), T(0), T(0), T(0), T(0)};
     ppm_one_vjp<T>(col, gdm[c], gdp[c], gcol);
     gqs[0][c] = gcol[0];
     gqs[1][c] = gcol[1];
-    gqs[3][c] = gcol[3];
-    gqs[4][c] = gcol[4];
+    gqs[2][c] = gcol[3];
+    gqs[3][c] = gcol[4];
     // gcol[2] is the cotangent of q_0, which is identically 0 (deviation form)
   }
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
-    if (m == 2) continue;
-    T gd[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    eig_left_vjp<T>(E, ir, d[m], gqs[m], gd, gE);
+  for (int k = 0; k < 4; ++k) {
+    T wm[7], d[7];
+    wload(k < 2 ? k : k + 1, wm);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      gw[m][c] += gd[c];
-      gw[2][c] -= gd[c];
-    }
+    for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
+    T gd[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    eig_left_vjp<T>(E, ir, d, gqs[k], gd, gE);
+    put(k < 2 ? k : k + 1, gd);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) gw2[c] -= gd[c];
   }
-  eig_fields_vjp<T>(gamma, w[2], bn, E, gE, gw[2], gbn);
+  eig_fields_vjp<T>(gamma, w2, bn, E, gE, gw2, gbn);
 }
 
 

@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
   for (int m = 0; m < NS; ++m)
 #pragma unroll
     for (int q = 0; q < 7; ++q) gw[m][q] = T(0);
-  if (RECON == 0) {
+  if constexpr (RECON == 0) {
     // W_L = W_R = W_p, with the face floors
     T w0[7];
     load_dir<A>(W, N, c, w0);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
       if (q == 4 && w0[4] < from_d<T>(g.p_floor)) a = b = T(0);
       gw[1][q] = a + b;
     }
-  } else if (RECON == 1) {
+  } else if constexpr (RECON == 1) {
     T wm[7], w0[7], wp[7];
     load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, -1), wm);
     load_dir<A>(W, N, c, w0);
@@ -397,10 +397,18 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
     plmc_vjp<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), wm, w0, wp, bn, gl, gr, gw[0], gw[1],
                 gw[2], gbn);
   } else {
-    T w[5][7];
+    // stencil cells loaded where the reverse sweep uses them (from L1), the
+    // slots of the neighbours written as they are formed
+    auto wload = [&](int m, T* out) { load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, m - 2), out); };
+    auto put = [&](int m, const T* gm) {
 #pragma unroll
-    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, s), w[s + 2]);
-    ppmc_vjp<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), w, bn, gl, gr, (T(*)[7])gw, gbn);
+      for (int q = 0; q < 7; ++q) S[((long long)m * 7 + q) * N + c] = gm[q];
+    };
+    T gw2[7];
+    ppmc_vjp<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), wload, bn, gl, gr, put, gw2, gbn);
+    put(2, gw2);
+    S[(long long)NS * 7 * N + c] = gbn;
+    return;
   }
 #pragma unroll
   for (int m = 0; m < NS; ++m)
