@@ -287,6 +287,39 @@ __device__ __forceinline__ void eig_fields_vjp(T gamma, const T* w0, T bn, const
 }
 
 
+// With every call inlined, the float-pair reverse reconstruction kernels
+// outgrow the instruction cache (ncu: warps stalled mostly on instruction
+// fetch; the PPMC kernels of y and z ran 3x slower than that of x).  For
+// float pairs the per-field PPM limiter (forward and reverse), the
+// projections and their reverses are calls: one copy each.
+template <class T> struct OutlineRev { static constexpr bool v = false; };
+template <> struct OutlineRev<df> { static constexpr bool v = true; };
+template <class T> __device__ __noinline__ void ppm_one_call(const T* q, T& qm, T& qp) { ppm_one<T>(q, qm, qp); }
+template <class T>
+__device__ __noinline__ void eig_left_vjp_call(const Eig<T>& E, T ir, const T* dw, const T* gq, T* gdw, EigG<T>& gE) {
+  eig_left_vjp<T>(E, ir, dw, gq, gdw, gE);
+}
+template <class T> __device__ __noinline__ void eig_left_call(const Eig<T>& E, const T* dw, T* q) { eig_left<T>(E, dw, q); }
+template <class T>
+__device__ __noinline__ void eig_right_vjp_call(const Eig<T>& E, const T* q, const T* gdw, T* gq, EigG<T>& gE) {
+  eig_right_vjp<T>(E, q, gdw, gq, gE);
+}
+// the calls above where OutlineRev<T> holds, else the inlined functions
+template <class T> __device__ __forceinline__ void eig_left_o(const Eig<T>& E, const T* dw, T* q) {
+  if constexpr (OutlineRev<T>::v) eig_left_call<T>(E, dw, q);
+  else eig_left<T>(E, dw, q);
+}
+template <class T>
+__device__ __forceinline__ void eig_left_vjp_o(const Eig<T>& E, T ir, const T* dw, const T* gq, T* gdw, EigG<T>& gE) {
+  if constexpr (OutlineRev<T>::v) eig_left_vjp_call<T>(E, ir, dw, gq, gdw, gE);
+  else eig_left_vjp<T>(E, ir, dw, gq, gdw, gE);
+}
+template <class T>
+__device__ __forceinline__ void eig_right_vjp_o(const Eig<T>& E, const T* q, const T* gdw, T* gq, EigG<T>& gE) {
+  if constexpr (OutlineRev<T>::v) eig_right_vjp_call<T>(E, q, gdw, gq, gE);
+  else eig_right_vjp<T>(E, q, gdw, gq, gE);
+}
+
 // ------------------------------------------------------------- PLMC VJP --
 // gwl, gwr: cotangents of W_{L,i+1/2}, W_{R,i-1/2} (after the face floors).
 // Accumulates into gwm, gw0, gwp (cells i-1, i, i+1) and gbn.
@@ -304,9 +337,9 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
   eig_build<T>(gamma, w0, bn, E);
   const T ir = E.ir;
   T aL[7], aR[7], aC[7], aG[7], am[7], dW[7];
-  eig_left<T>(E, dL, aL);
-  eig_left<T>(E, dR, aR);
-  eig_left<T>(E, dG, aG);
+  eig_left_o<T>(E, dL, aL);
+  eig_left_o<T>(E, dR, aR);
+  eig_left_o<T>(E, dG, aG);
 #pragma unroll
   for (int q = 0; q < 7; ++q) aC[q] = T(0.5) * (aL[q] + aR[q]);
   int sel[7];  // -1: zero slope; 0..3: candidate 2|aL|, 2|aR|, |aC|, |aG|
@@ -348,7 +381,7 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
   }
   EigG<T> gE;
   gE.zero();
-  eig_right_vjp<T>(E, am, gdW, gam, gE);
+  eig_right_vjp_o<T>(E, am, gdW, gam, gE);
   T gaL[7], gaR[7], gaC[7], gaG[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -369,9 +402,9 @@ __device__ void plmc_vjp(T gamma, T rho_floor, T p_floor, const T* wm, const T* 
     gaL[q] += T(0.5) * gaC[q];
     gaR[q] += T(0.5) * gaC[q];
   }
-  eig_left_vjp<T>(E, ir, dL, gaL, gdL, gE);
-  eig_left_vjp<T>(E, ir, dR, gaR, gdR, gE);
-  eig_left_vjp<T>(E, ir, dG, gaG, gdG, gE);
+  eig_left_vjp_o<T>(E, ir, dL, gaL, gdL, gE);
+  eig_left_vjp_o<T>(E, ir, dR, gaR, gdR, gE);
+  eig_left_vjp_o<T>(E, ir, dG, gaG, gdG, gE);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     const T pr = dL[q] * dR[q];
@@ -544,6 +577,10 @@ template <class T> __device__ void ppm_one_vjp(const T* q, T gqm, T gqp, T* gq) 
   gq[2] += gq2;
 }
 
+template <class T> __device__ __noinline__ void ppm_one_vjp_call(const T* q, T gqm, T gqp, T* gq) {
+  ppm_one_vjp<T>(q, gqm, gqp, gq);
+}
+
 // Reverse of PPMC for one cell.  wload(m, w7) loads the directional state of
 // stencil cell m (0..4 for i-2..i+2); put(m, g7) receives the cotangent of
 // stencil cell m != 2, once each; gw2 (7) receives that of cell i and gbn
@@ -566,14 +603,15 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, Load wload, T bn, cons
     wload(k < 2 ? k : k + 1, wm);
 #pragma unroll
     for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
-    eig_left<T>(E, d, qs[k]);
+    eig_left_o<T>(E, d, qs[k]);
   }
   T dm[7], dp[7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
     const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
     T qm, qp;
-    ppm_one<T>(col, qm, qp);
+    if constexpr (OutlineRev<T>::v) ppm_one_call<T>(col, qm, qp);
+    else ppm_one<T>(col, qm, qp);
     dm[c] = qm;
     dp[c] = qp;
   }
@@ -598,14 +636,15 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, Load wload, T bn, cons
     gw2[c] = gwl[c] + gwr[c];
     gdm[c] = gdp[c] = T(0);
   }
-  eig_right_vjp<T>(E, dp, gwl, gdp, gE);
-  eig_right_vjp<T>(E, dm, gwr, gdm, gE);
+  eig_right_vjp_o<T>(E, dp, gwl, gdp, gE);
+  eig_right_vjp_o<T>(E, dm, gwr, gdm, gE);
   T gqs[4][7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
     const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
     T gcol[5] = {T(0), T(0), T(0), T(0), T(0)};
-    ppm_one_vjp<T>(col, gdm[c], gdp[c], gcol);
+    if constexpr (OutlineRev<T>::v) ppm_one_vjp_call<T>(col, gdm[c], gdp[c], gcol);
+    else ppm_one_vjp<T>(col, gdm[c], gdp[c], gcol);
     gqs[0][c] = gcol[0];
     gqs[1][c] = gcol[1];
     gqs[2][c] = gcol[3];
@@ -619,7 +658,7 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, Load wload, T bn, cons
 #pragma unroll
     for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
     T gd[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    eig_left_vjp<T>(E, ir, d, gqs[k], gd, gE);
+    eig_left_vjp_o<T>(E, ir, d, gqs[k], gd, gE);
     put(k < 2 ? k : k + 1, gd);
 #pragma unroll
     for (int c = 0; c < 7; ++c) gw2[c] -= gd[c];
