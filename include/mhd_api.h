@@ -86,7 +86,9 @@ extern "C" {
 #define MHD_GHOST 8
 
 typedef struct mhd_config {
-  int nx, ny, nz;          /* cells per axis, each >= 4                       */
+  int nx, ny, nz;          /* cells per axis, each >= 4; nz <= 65535 and at
+                              most 2^31 - 1 cells in all (with the ghost
+                              cells of outflow and halo axes)               */
   double dx, dy, dz;       /* cell widths (> 0)                               */
   double gamma;            /* adiabatic index, P = (gamma-1) eps (Sec. 2.1)   */
   double cfl;              /* Courant number C_CFL of Eq. dt (0 < cfl <= 0.5) */

@@ -5,10 +5,12 @@
 namespace mhd {
 template struct Launch<double>;
 
-void launch_set_dt(double* dt_cur, double value, cudaStream_t s) { k_set_dt<<<1, 1, 0, s>>>(dt_cur, value); }
-void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
+void launch_set_dt(const Grid& g, double* dt_cur, double value, cudaStream_t s) {
+  k_set_dt<<<1, 1, 0, s>>>(g, dt_cur, value);
+}
+void launch_finish_dt(const Grid& g, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
                       unsigned* flags, double t_end, cudaStream_t s) {
-  k_finish_dt<<<1, 1, 0, s>>>(cfl, dtbits, dt_cur, dt_log, step, flags, t_end);
+  k_finish_dt<<<1, 1, 0, s>>>(g, dtbits, dt_cur, dt_log, step, flags, t_end);
 }
 static int copy_blocks(long long n) {
   const long long b = (n + 255) / 256;

@@ -31,7 +31,7 @@ struct mhd_ctx {
   // typed views into ws (element type = compute type)
   void *W, *F, *E, *WL, *WR, *Bh;
   void* Er;                     // cell reference fields -(v x B_cc) written with W (step path)
-  double* scal;                 // [0] dt_cur
+  double* scal;                 // mhd::StepScalars of the current step ([0] dt, [1] t)
   unsigned long long* dtbits;   // [0] dt reduction word
   unsigned long long* floors;   // [0..1] floor counters
   unsigned* flags;              // [0] error flags
@@ -108,7 +108,7 @@ Layout layout_of(const mhd_config& c) {
   L.Er = off;
   off += up(3 * N * ts);
   L.scal = off;
-  off += up(8 * sizeof(double));
+  off += up(mhd::kStepScalarDoubles * sizeof(double));
   L.dtbits = off;
   off += up(sizeof(unsigned long long));
   L.floors = off;
@@ -140,6 +140,8 @@ int check_cfg(const mhd_config* c) {
   int np[3], lo[3];
   padded_dims(*c, np, lo);
   if ((long long)np[0] * np[1] > (1ll << 31) || np[2] > 65535) return MHD_ERR_ARG;
+  // the step kernels index cells with 32-bit integers
+  if ((long long)np[0] * np[1] * np[2] > 2147483647LL) return MHD_ERR_ARG;
   return MHD_OK;
 }
 
@@ -229,7 +231,7 @@ template <class T> void run_begin(mhd_ctx* c, double* U) {
 template <class T> void run_one(mhd_ctx* c, double* U, double* dt_log, int n, double t_end) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
-  prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, dt_log, n, c->flags, t_end, s); });
+  prof(c, MHD_STAGE_DT, [&] { mhd::launch_finish_dt(g, c->dtbits, c->scal, dt_log, n, c->flags, t_end, s); });
   step_body<T>(c, U, c->cfg.recon);
   refill(c, U);
   prof(c, MHD_STAGE_PRIM,
@@ -273,7 +275,7 @@ template <class T> int evolve_to(mhd_ctx* c, double* U, double t_end, int max_st
 template <class T> int one_step(mhd_ctx* c, double* U, double dt, double* next_dt) {
   const Grid& g = c->g;
   cudaStream_t s = c->stream;
-  mhd::launch_set_dt(c->scal, dt, s);
+  mhd::launch_set_dt(c->g, c->scal, dt, s);
   double* S = enter(c, U);
   Launch<T>::prim(g, S, as<T>(c->W), nullptr, c->flags, nullptr, s, as<T>(c->Er));
   step_body<T>(c, S, c->cfg.recon);
@@ -282,7 +284,7 @@ template <class T> int one_step(mhd_ctx* c, double* U, double dt, double* next_d
   Launch<T>::prim(g, S, as<T>(c->W), next_dt ? c->dtbits : nullptr, c->flags, c->floors, s);
   leave(c, U);
   if (!next_dt) return cuda_status();
-  mhd::launch_finish_dt(g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
+  mhd::launch_finish_dt(g, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
   double v = 0;
   if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
@@ -298,7 +300,7 @@ template <class T> int step_sub(mhd_ctx* c, const double* Ug, const int gn[3], c
   Grid gg = c->gi;
   for (int a = 0; a < 3; ++a) gg.n[a] = gn[a];
   gg.N = (long long)gn[0] * gn[1] * gn[2];
-  mhd::launch_set_dt(c->scal, dt, s);
+  mhd::launch_set_dt(c->g, c->scal, dt, s);
   mhd::launch_gather_sub(g, gg, off, Ug, c->Up, s);
   Launch<T>::prim(g, c->Up, as<T>(c->W), nullptr, c->flags, nullptr, s, as<T>(c->Er));
   step_body<T>(c, c->Up, c->cfg.recon);
@@ -315,7 +317,7 @@ template <class T> int dt_sub(mhd_ctx* c, const double* Ug, const int gn[3], con
   mhd::launch_gather_sub(c->g, gg, off, Ug, c->Up, s);
   cudaMemsetAsync(c->dtbits, 0, sizeof(unsigned long long), s);
   Launch<T>::prim(c->g, c->Up, as<T>(c->W), c->dtbits, c->flags, nullptr, s);
-  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
+  mhd::launch_finish_dt(c->g, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
   double v = 0;
   if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
@@ -736,7 +738,7 @@ int mhd_dt(mhd_ctx* c, const double* U, double* dt_host) {
     Launch<MHD_T>::prim(c->g, Um, as<MHD_T>(c->W), c->dtbits, c->flags, nullptr, s);
     return 0;
   });
-  mhd::launch_finish_dt(c->g.cfl, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
+  mhd::launch_finish_dt(c->g, c->dtbits, c->scal, nullptr, 0, c->flags, kNoEnd, s);
   double v = 0;
   unsigned fl = 0;
   if (cudaMemcpyAsync(&v, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;

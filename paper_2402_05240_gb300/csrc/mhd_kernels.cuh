@@ -42,6 +42,68 @@ __device__ __forceinline__ bool interior(const Grid& g, int i, int j, int k) {
   return i >= g.lo[0] && i < g.hi[0] && j >= g.lo[1] && j < g.hi[1] && k >= g.lo[2] && k < g.hi[2];
 }
 
+// ------------------------------------------------------- 32-bit addressing --
+// The step kernels address cells with 32-bit indices: every grid of a context
+// has fewer than 2^31 cells (mhd_init refuses larger ones).  A thread forms
+// its cell index and the periodic offsets to its six face neighbours once;
+// any other stencil cell is the index plus a sum of offsets (the wrap along
+// one axis does not depend on the other coordinates).  Field-major arrays
+// reach the kernels as tables of field pointers (kernel parameters), so the
+// address of field f at cell q is one 32 x 64-bit multiply-add: no 64-bit
+// index arithmetic per access.
+template <class T, int K> struct Fields {
+  T* f[K];
+};
+
+// host side: the K field pointers of a field-major array with N cells per field
+template <int K, class T> inline Fields<T, K> fields(T* base, long long N) {
+  Fields<T, K> r;
+  for (int q = 0; q < K; ++q) r.f[q] = base ? base + q * N : nullptr;
+  return r;
+}
+
+struct Cell {
+  int i, j, k;
+  int c;           // (k ny + j) nx + i
+  int m[3], p[3];  // c + m[a]: the cell p - e_a, c + p[a]: the cell p + e_a (periodic)
+  bool ok;
+};
+
+__device__ __forceinline__ Cell thread_cell(const Grid& g) {
+  Cell p;
+  p.i = blockIdx.x * BX + threadIdx.x;
+  p.j = blockIdx.y * BY + threadIdx.y;
+  p.k = blockIdx.z;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxy = nx * ny;
+  p.ok = p.i < nx && p.j < ny;
+  p.c = (p.k * ny + p.j) * nx + p.i;
+  p.m[0] = p.i == 0 ? nx - 1 : -1;
+  p.p[0] = p.i == nx - 1 ? 1 - nx : 1;
+  p.m[1] = p.j == 0 ? (ny - 1) * nx : -nx;
+  p.p[1] = p.j == ny - 1 ? (1 - ny) * nx : nx;
+  p.m[2] = p.k == 0 ? (nz - 1) * nxy : -nxy;
+  p.p[2] = p.k == nz - 1 ? (1 - nz) * nxy : nxy;
+  return p;
+}
+
+// offset from cell p to p + s e_A (periodic), |s| < n[A]
+template <int A> __device__ __forceinline__ int off(const Grid& g, const Cell& p, int s) {
+  if (s == 0) return 0;
+  if (s == -1) return p.m[A];
+  if (s == 1) return p.p[A];
+  const int x = A == 0 ? p.i : (A == 1 ? p.j : p.k);
+  const int stride = A == 0 ? 1 : (A == 1 ? g.n[0] : g.n[0] * g.n[1]);
+  return (wrapi(x + s, g.n[A]) - x) * stride;
+}
+
+// read-only loads through the non-coherent path (the kernels issue every
+// load of an input before their stores to other arrays)
+template <class T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+template <> __device__ __forceinline__ df ldg<df>(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df(v.x, v.y);
+}
+
 // Positive doubles order like their bit patterns: the maximum inverse
 // crossing time goes through an integer atomicMax.  The block reduces in the
 // compute type and converts once.
@@ -121,9 +183,14 @@ template <class T> __device__ __forceinline__ void store_ref(T* __restrict__ Er,
   Er[N + c] = cell_ref<T, 1>(w8);
   Er[2 * N + c] = cell_ref<T, 2>(w8);
 }
+template <class T> __device__ __forceinline__ void store_ref(const Fields<T, 3>& Er, int c, const T* w8) {
+  if (!Er.f[0]) return;
+  Er.f[0][c] = cell_ref<T, 0>(w8);
+  Er.f[1][c] = cell_ref<T, 1>(w8);
+  Er.f[2][c] = cell_ref<T, 2>(w8);
+}
 
-template <class T>
-__device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
+template <class T> __device__ __forceinline__ void prim_to_w8(const PrimD& p, T* w8) {
   w8[0] = from_d<T>(p.rho);
   w8[1] = from_d<T>(p.v[0]);
   w8[2] = from_d<T>(p.v[1]);
@@ -132,8 +199,18 @@ __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long l
   w8[5] = from_d<T>(p.b[0]);
   w8[6] = from_d<T>(p.b[1]);
   w8[7] = from_d<T>(p.b[2]);
+}
+
+template <class T>
+__device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
+  prim_to_w8<T>(p, w8);
 #pragma unroll
   for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
+}
+template <class T> __device__ __forceinline__ void store_w(const Fields<T, 8>& W, int c, const PrimD& p, T* w8) {
+  prim_to_w8<T>(p, w8);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) W.f[f][c] = w8[f];
 }
 
 // FP32-bulk primitives of one cell: the gas-pressure recovery
@@ -141,7 +218,7 @@ __device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long l
 // the outputs that are stored as float (v = m / rho', B_cc) formed on the FP32
 // pipes from the rounded inputs.  bsum = twice the cell-centred field (sum of
 // the two face values).  Returns ke + me in double for the floor reset.
-__device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restrict__ W, long long c, double rho,
+__device__ __forceinline__ double prim_store_f32(const Grid& g, const Fields<float, 8>& W, int c, double rho,
                                                  double ir, double m0, double m1, double m2, double e,
                                                  const double* bsum, float* w8) {
   const double mm = m0 * m0 + m1 * m1 + m2 * m2;
@@ -158,7 +235,7 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
   w8[6] = 0.5f * d2f_bits(bsum[1]);
   w8[7] = 0.5f * d2f_bits(bsum[2]);
 #pragma unroll
-  for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
+  for (int f = 0; f < 8; ++f) W.f[f][c] = w8[f];
   return kem;
 }
 
@@ -170,55 +247,57 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, float* __restric
 // the floor counters take interior cells only (ghost cells of a padded grid
 // are copies).
 template <class T>
-__global__ void __launch_bounds__(BX* BY) k_prim(Grid g, double* U, T* __restrict__ W, unsigned long long* dtbits,
-                                                 unsigned* flags, unsigned long long* floors, T* __restrict__ Er) {
-  const CellIdx ci = cell_of_thread(g);
+__global__ void __launch_bounds__(BX* BY) k_prim(Grid g, Fields<double, 8> U, Fields<T, 8> W, unsigned long long* dtbits,
+                                                 unsigned* flags, unsigned long long* floors, Fields<T, 3> Er) {
+  const Cell p = thread_cell(g);
   T inv = T(0);
-  if (ci.ok) {
-    const int i = ci.i, j = ci.j, k = ci.k;
-    const long long c = cidx(g, i, j, k), N = g.N;
-    const bool in = interior(g, i, j, k);
-    double r = U[c], e = U[4 * N + c];
-    const double m0 = U[N + c], m1 = U[2 * N + c], m2 = U[3 * N + c];
+  if (p.ok) {
+    const int c = p.c;
+    const bool in = interior(g, p.i, p.j, p.k);
+    // (rho and E are written below with the floors: plain loads; the face
+    // fields are only read)
+    double r = U.f[0][c], e = U.f[4][c];
+    const double m0 = U.f[1][c], m1 = U.f[2][c], m2 = U.f[3][c];
+    const double b0m = ldg(U.f[5] + c + p.m[0]), b0p = ldg(U.f[5] + c);
+    const double b1m = ldg(U.f[6] + c + p.m[1]), b1p = ldg(U.f[6] + c);
+    const double b2m = ldg(U.f[7] + c + p.m[2]), b2p = ldg(U.f[7] + c);
     // (bit-pattern tests on the integer pipes: the FP64 pipe bounds this kernel)
     if ((!pos_bits(r) || !finite_bits(e) || !finite_bits(m0) || !finite_bits(m1) || !finite_bits(m2)) && in)
       atomicOr(flags, 1u);
     if (floors && lt_pos<double>(r, g.rho_floor)) {
       r = g.rho_floor;
-      U[c] = r;
+      U.f[0][c] = r;
       if (in) atomicAdd(&floors[0], 1ull);
     }
     const double rho = max_pos<double>(r, g.rho_floor);
     const double ir = __drcp_rn(rho);
     T w8[8];
     if constexpr (std::is_same<T, float>::value) {
-      const double bs[3] = {U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c],
-                            U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c],
-                            U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]};
+      const double bs[3] = {b0m + b0p, b1m + b1p, b2m + b2p};
       const double kem = prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8);
-      store_ref<T>(Er, N, c, w8);
+      store_ref<T>(Er, c, w8);
       if (floors && lt_pos<double>(g.gm1 * (e - kem), g.p_floor)) {
-        U[4 * N + c] = g.p_floor * g.igm1 + kem;
+        U.f[4][c] = g.p_floor * g.igm1 + kem;
         if (in) atomicAdd(&floors[1], 1ull);
       }
       if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
     } else {
       double b[3];
-      b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
-      b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
-      b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
+      b[0] = 0.5 * (b0m + b0p);
+      b[1] = 0.5 * (b1m + b1p);
+      b[2] = 0.5 * (b2m + b2p);
       if (floors) {
         const double ke = 0.5 * (m0 * (m0 * ir) + m1 * (m1 * ir) + m2 * (m2 * ir));
         const double me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
         if (lt_pos<double>(g.gm1 * (e - ke - me), g.p_floor)) {
           e = g.p_floor * g.igm1 + ke + me;
-          U[4 * N + c] = e;
+          U.f[4][c] = e;
           if (in) atomicAdd(&floors[1], 1ull);
         }
       }
-      const PrimD p = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
-      store_w<T>(g, W, c, p, w8);
-      store_ref<T>(Er, N, c, w8);
+      const PrimD pw = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
+      store_w<T>(W, c, pw, w8);
+      store_ref<T>(Er, c, w8);
       if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
     }
   }
@@ -236,29 +315,33 @@ template <int A, class T> __device__ __forceinline__ void load_dir(const T* __re
   w[5] = W[(5 + B) * N + q];
   w[6] = W[(5 + C) * N + q];
 }
-
-// -------------------------------------------------------------- Steps 2-3 --
-template <class T, int A>
-__device__ __forceinline__ void pcm_face(const Grid& g, const T* __restrict__ W, const double* __restrict__ U,
-                                         T* __restrict__ F, int i, int j, int k) {
-  const long long N = g.N, c = cidx(g, i, j, k), cn = nb<A>(g, i, j, k, 1);
-  T wl[7], wr[7], f[7];
-  load_dir<A>(W, N, c, wl);
-  load_dir<A>(W, N, cn, wr);
-  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, from_d<T>(U[(5 + A) * N + c]), f);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+template <int A, class T> __device__ __forceinline__ void load_dir(const Fields<const T, 8>& W, int q, T* w) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  w[0] = ldg(W.f[0] + q);
+  w[1] = ldg(W.f[1 + A] + q);
+  w[2] = ldg(W.f[1 + B] + q);
+  w[3] = ldg(W.f[1 + C] + q);
+  w[4] = ldg(W.f[4] + q);
+  w[5] = ldg(W.f[5 + B] + q);
+  w[6] = ldg(W.f[5 + C] + q);
 }
 
+// -------------------------------------------------------------- Steps 2-3 --
 // one axis per launch: a thread solving three Riemann problems in sequence
 // holds too many registers for the occupancy the double-float arithmetic
-// needs to hide its latencies
+// needs to hide its latencies.  BA: the face field B_A of the state.
 template <class T, int A>
-__global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, const T* __restrict__ W, const double* __restrict__ U,
-                                                     T* __restrict__ F) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  pcm_face<T, A>(g, W, U, F, ci.i, ci.j, ci.k);
+__global__ void __launch_bounds__(BX* BY) k_flux_pcm(Grid g, Fields<const T, 8> W, const double* __restrict__ BA,
+                                                     Fields<T, 7> FA) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const int c = p.c;
+  T wl[7], wr[7], f[7];
+  load_dir<A>(W, c, wl);
+  load_dir<A>(W, c + p.p[A], wr);
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, from_d<T>(ldg(BA + c)), f);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) FA.f[q][c] = f[q];
 }
 
 // ------------------------------------------------------------------ Step 6 --
@@ -277,28 +360,27 @@ template <class T> __device__ __forceinline__ void floor_face(const Grid& g, T* 
 // kernel, 108 registers, loses 5 % at 5 blocks, 96 registers.)
 template <class T, int RECON> struct ReconMinBlocks { static constexpr int v = 4; };
 
-// interface states of cell (i, j, k) along A (Step 6): wl = W_{L,i+1/2} (the
-// cell's state at its upper face), wr = W_{R,i-1/2} (at its lower face), floored
+// interface states of cell p along A (Step 6): wl = W_{L,i+1/2} (the cell's
+// state at its upper face), wr = W_{R,i-1/2} (at its lower face), floored
 template <class T, int RECON, int A>
-__device__ __forceinline__ void recon_cell(const Grid& g, const T* __restrict__ W, int i, int j, int k, T* wl,
-                                           T* wr) {
-  const long long N = g.N, c = cidx(g, i, j, k);
-  const T bn = W[(5 + A) * N + c];
+__device__ __forceinline__ void recon_cell(const Grid& g, const Fields<const T, 8>& W, const Cell& p, T* wl, T* wr) {
+  const int c = p.c;
+  const T bn = ldg(W.f[5 + A] + c);
   if (RECON == 0) {
-    load_dir<A>(W, N, c, wl);
+    load_dir<A>(W, c, wl);
 #pragma unroll
     for (int q = 0; q < 7; ++q) wr[q] = wl[q];
   } else if (RECON == 1 || RECON == 3) {
     T wm[7], w0[7], wp[7];
-    load_dir<A>(W, N, nb<A>(g, i, j, k, -1), wm);
-    load_dir<A>(W, N, c, w0);
-    load_dir<A>(W, N, nb<A>(g, i, j, k, 1), wp);
+    load_dir<A>(W, c + p.m[A], wm);
+    load_dir<A>(W, c, w0);
+    load_dir<A>(W, c + p.p[A], wp);
     if (RECON == 1) plmc<T>(from_d<T>(g.gamma), wm, w0, wp, bn, wl, wr);
     else plm_prim<T>(wm, w0, wp, wl, wr);
   } else {
     T w[5][7];
 #pragma unroll
-    for (int s = -2; s <= 2; ++s) load_dir<A>(W, N, nb<A>(g, i, j, k, s), w[s + 2]);
+    for (int s = -2; s <= 2; ++s) load_dir<A>(W, c + off<A>(g, p, s), w[s + 2]);
     ppmc<T>(from_d<T>(g.gamma), w, bn, wl, wr);
   }
   floor_face<T>(g, wl);
@@ -306,36 +388,36 @@ __device__ __forceinline__ void recon_cell(const Grid& g, const T* __restrict__ 
 }
 
 template <class T, int RECON, int A>
-__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, const T* __restrict__ W, T* __restrict__ WL,
-                                                  T* __restrict__ WR) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+__global__ void __launch_bounds__(BX* BY, ReconMinBlocks<T, RECON>::v) k_recon(Grid g, Fields<const T, 8> W,
+                                                                             Fields<T, 7> WL, Fields<T, 7> WR) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
   T wl[7], wr[7];
-  recon_cell<T, RECON, A>(g, W, ci.i, ci.j, ci.k, wl, wr);
+  recon_cell<T, RECON, A>(g, W, p, wl, wr);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    WL[q * N + c] = wl[q];
-    WR[q * N + c] = wr[q];
+    WL.f[q][p.c] = wl[q];
+    WR.f[q][p.c] = wr[q];
   }
 }
 
 // ------------------------------------------------------------------ Step 7 --
+// BfA: the half-step face field B_A
 template <class T, int A>
-__global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
-                                                      const T* __restrict__ Bf, T* __restrict__ F) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k), cn = nb<A>(g, ci.i, ci.j, ci.k, 1);
+__global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, Fields<const T, 7> WL, Fields<const T, 7> WR,
+                                                      const T* __restrict__ BfA, Fields<T, 7> FA) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const int c = p.c, cn = c + p.p[A];
   T wl[7], wr[7], f[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    wl[q] = WL[q * N + c];
-    wr[q] = WR[q * N + cn];
+    wl[q] = ldg(WL.f[q] + c);
+    wr[q] = ldg(WR.f[q] + cn);
   }
-  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, Bf[A * N + c], f);
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, ldg(BfA + c), f);
 #pragma unroll
-  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+  for (int q = 0; q < 7; ++q) FA.f[q][c] = f[q];
 }
 
 // ------------------------------------------------------------ Steps 4, 8 --
@@ -369,17 +451,65 @@ template <> __device__ __forceinline__ double upwind<double>(double m, double fl
 }
 
 template <class T, int A, bool REF>
-__device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
-                                        const T* __restrict__ Er, int i, int j, int k) {
+__device__ __forceinline__ T edge_field(const Grid& g, const Fields<const T, 8>& W, const Fields<const T, 21>& F,
+                                        const Fields<const T, 3>& Er, const Cell& p) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  const int q00 = p.c, qb = q00 + p.p[B], qc = q00 + p.p[C], qbc = qb + p.p[C];
+  const T* Fbm = F.f[B * 7];      // mass flux of axis B
+  const T* Fbb = F.f[B * 7 + 5];  // B-field flux 5 of axis B
+  const T* Fcm = F.f[C * 7];
+  const T* Fcb = F.f[C * 7 + 6];
+  auto ref = [&](int q) {
+    if constexpr (REF) {
+      return ldg(Er.f[A] + q);
+    } else {
+      const T w8[8] = {T(0), ldg(W.f[1] + q), ldg(W.f[2] + q), ldg(W.f[3] + q),
+                       T(0), ldg(W.f[5] + q), ldg(W.f[6] + q), ldg(W.f[7] + q)};
+      return cell_ref<T, A>(w8);
+    }
+  };
+  const T bf0 = -ldg(Fbb + q00), bfc = -ldg(Fbb + qc);
+  const T cf0 = ldg(Fcb + q00), cfb = ldg(Fcb + qb);
+  const T r00 = ref(q00), rb = ref(qb), rc = ref(qc), rbc = ref(qbc);
+  const T avg = T(0.25) * (bfc + bf0 + cfb + cf0);
+  const T Dcp = upwind<T>(ldg(Fbm + qc), cf0, rc, cfb, rbc);
+  const T Dcm = upwind<T>(ldg(Fbm + q00), cf0, r00, cfb, rb);
+  const T Dbp = upwind<T>(ldg(Fcm + qb), bf0, rb, bfc, rbc);
+  const T Dbm = upwind<T>(ldg(Fcm + q00), bf0, r00, bfc, rc);
+  return avg + T(0.25) * (Dcp + Dcm + Dbp + Dbm);
+}
+
+// REF: the cells' reference fields come from Er (written with W), else from W
+template <class T, bool REF>
+__global__ void __launch_bounds__(BX* BY) k_emf(Grid g, Fields<const T, 8> W, Fields<const T, 21> F,
+                                                Fields<const T, 3> Er, Fields<T, 3> E) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const T e0 = edge_field<T, 0, REF>(g, W, F, Er, p);
+  const T e1 = edge_field<T, 1, REF>(g, W, F, Er, p);
+  const T e2 = edge_field<T, 2, REF>(g, W, F, Er, p);
+  E.f[0][p.c] = e0;
+  E.f[1][p.c] = e1;
+  E.f[2][p.c] = e2;
+}
+
+// The edge fields of the FP64 step keep the addressing of restrict-qualified
+// base pointers with 64-bit indices: measured at 512^3 (PPMC turbulent box),
+// this form takes 24.4 ms per step against 36.6 ms for the pointer-table form
+// above (same registers, no spill), while the float and double-float edge
+// kernels are faster in the table form (3.2 against 4.8 ms, 7.8 against
+// 8.9 ms).
+template <class T, int A, bool REF>
+__device__ __forceinline__ T edge_field_r(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
+                                          const T* __restrict__ Er, int i, int j, int k) {
   constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
   const long long N = g.N;
-  int p[3] = {i, j, k};
   int pb[3] = {i, j, k}, pc[3] = {i, j, k}, pbc[3] = {i, j, k};
   pb[B] = wrapi(pb[B] + 1, g.n[B]);
   pc[C] = wrapi(pc[C] + 1, g.n[C]);
   pbc[B] = pb[B];
   pbc[C] = pc[C];
-  const long long q00 = cidx(g, p[0], p[1], p[2]), qb = cidx(g, pb[0], pb[1], pb[2]);
+  const long long q00 = cidx(g, i, j, k), qb = cidx(g, pb[0], pb[1], pb[2]);
   const long long qc = cidx(g, pc[0], pc[1], pc[2]), qbc = cidx(g, pbc[0], pbc[1], pbc[2]);
   const T* Fb = F + (long long)B * 7 * N;
   const T* Fc = F + (long long)C * 7 * N;
@@ -402,16 +532,15 @@ __device__ __forceinline__ T edge_field(const Grid& g, const T* __restrict__ W, 
   return avg + T(0.25) * (Dcp + Dcm + Dbp + Dbm);
 }
 
-// REF: the cells' reference fields come from Er (written with W), else from W
 template <class T, bool REF>
-__global__ void __launch_bounds__(BX* BY) k_emf(Grid g, const T* __restrict__ W, const T* __restrict__ F,
-                                                const T* __restrict__ Er, T* __restrict__ E) {
+__global__ void __launch_bounds__(BX* BY) k_emf_r(Grid g, const T* __restrict__ W, const T* __restrict__ F,
+                                                  const T* __restrict__ Er, T* __restrict__ E) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
   const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
-  E[c] = edge_field<T, 0, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
-  E[N + c] = edge_field<T, 1, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
-  E[2 * N + c] = edge_field<T, 2, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
+  E[c] = edge_field_r<T, 0, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
+  E[N + c] = edge_field_r<T, 1, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
+  E[2 * N + c] = edge_field_r<T, 2, REF>(g, W, F, Er, ci.i, ci.j, ci.k);
 }
 
 // ------------------------------------------------------------ Steps 5, 9 --
@@ -498,32 +627,121 @@ __device__ __forceinline__ double face_update(const Grid& g, const double* __res
   return U0[(5 + A) * g.N + cidx(g, ii, jj, kk)] - h * cu;
 }
 
-// Step 5: W^{n+1/2} (from U^{n+1/2}) and the half-step faces; h = dt/2 (D-1)
+// The same three operations on the 32-bit addressing of the step kernels.
+// q: the cell whose upper face A is updated; oB, oC: the offsets from q to
+// q - e_B and q - e_C.  NC: U0 is read-only in the kernel (non-coherent loads).
+template <class T, bool EXACT, int A>
+__device__ __forceinline__ double face_curl(const Grid& g, const Fields<const T, 3>& E, int q, int oB, int oC) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  const T* EB = E.f[B];
+  const T* EC = E.f[C];
+  if constexpr (EXACT && std::is_same<T, float>::value) {
+    const df dc = two_sum(ldg(EC + q), -ldg(EC + q + oB));
+    const df db = two_sum(ldg(EB + q), -ldg(EB + q + oC));
+    return (double)(dc * df(g.id[B]) - db * df(g.id[C]));
+  } else if (EXACT) {
+    return (to_d<T>(ldg(EC + q)) - to_d<T>(ldg(EC + q + oB))) * g.id[B] -
+           (to_d<T>(ldg(EB + q)) - to_d<T>(ldg(EB + q + oC))) * g.id[C];
+  }
+  return to_d<T>((ldg(EC + q) - ldg(EC + q + oB)) * from_d<T>(g.id[B]) -
+                 (ldg(EB + q) - ldg(EB + q + oC)) * from_d<T>(g.id[C]));
+}
+
+template <bool NC> __device__ __forceinline__ double ldu(const double* p) {
+  if constexpr (NC) return ldg(p);
+  else return *p;
+}
+
+// the factor (dt or dt / 2) / d_a of axis a in the compute type, from the
+// step scalars (formed once per step by the dt kernels)
+template <class T, bool HALF> __device__ __forceinline__ T step_factor(const StepScalars& S, int a) {
+  if constexpr (std::is_same<T, float>::value) {
+    return HALF ? S.hd_half_f[a] : d2f_bits(S.hd_full[a]);
+  } else if constexpr (std::is_same<T, df>::value) {
+    return HALF ? df(S.hd_half_hi[a], S.hd_half_lo[a]) : df(S.hd_full_hi[a], S.hd_full_lo[a]);
+  } else {
+    return HALF ? S.hd_half[a] : S.hd_full[a];
+  }
+}
+
+template <class T, bool EXACT, bool NC, bool HALF>
+__device__ __forceinline__ void hydro_update(const Fields<const double, 8>& U0, const Fields<const T, 21>& F,
+                                             const StepScalars& S, const Cell& p, double* out5) {
+  const int c = p.c;
+  const double* hd = HALF ? S.hd_half : S.hd_full;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    if constexpr (EXACT && std::is_same<T, float>::value) {
+      df inc(0.0f, 0.0f);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F.f[a * 7 + comp_of(f, a)];
+        const df hdf = HALF ? df(S.hd_half_hi[a], S.hd_half_lo[a]) : df(S.hd_full_hi[a], S.hd_full_lo[a]);
+        inc += hdf * two_sum(ldg(Fa + c), -ldg(Fa + c + p.m[a]));
+      }
+      out5[f] = ldu<NC>(U0.f[f] + c) - (double)inc;
+    } else if (EXACT) {
+      double acc = ldu<NC>(U0.f[f] + c);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F.f[a * 7 + comp_of(f, a)];
+        acc -= hd[a] * (to_d<T>(ldg(Fa + c)) - to_d<T>(ldg(Fa + c + p.m[a])));
+      }
+      out5[f] = acc;
+    } else {
+      T inc = T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* Fa = F.f[a * 7 + comp_of(f, a)];
+        inc -= step_factor<T, HALF>(S, a) * (ldg(Fa + c) - ldg(Fa + c + p.m[a]));
+      }
+      out5[f] = ldu<NC>(U0.f[f] + c) + to_d<T>(inc);
+    }
+  }
+}
+
+template <class T, bool EXACT, bool NC, int A>
+__device__ __forceinline__ double face_update(const Grid& g, const Fields<const double, 8>& U0,
+                                              const Fields<const T, 3>& E, double h, int q, int oB, int oC) {
+  const double cu = face_curl<T, EXACT, A>(g, E, q, oB, oC);
+  return ldu<NC>(U0.f[5 + A] + q) - h * cu;
+}
+
+template <class T, int K> __device__ __forceinline__ Fields<const T, K> as_const(const Fields<T, K>& a) {
+  Fields<const T, K> r;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.f[q] = a.f[q];
+  return r;
+}
+
+// Step 5: W^{n+1/2} (from U^{n+1/2}) and the half-step faces; h = dt/2 (D-1).
+// dtp: the StepScalars of the step.
 template <class T>
-__global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __restrict__ U0, const T* __restrict__ F,
-                                                        const T* __restrict__ E, const double* __restrict__ dtp,
-                                                        T* __restrict__ W, T* __restrict__ Bh, unsigned* flags,
-                                                        T* __restrict__ Er) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const double h = 0.5 * dtp[0];
-  const long long N = g.N, c = cidx(g, i, j, k);
+__global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, Fields<const double, 8> U0, Fields<const T, 21> F,
+                                                        Fields<const T, 3> E, const double* __restrict__ dtp,
+                                                        Fields<T, 8> W, Fields<T, 3> Bh, unsigned* flags,
+                                                        Fields<T, 3> Er) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const int c = p.c;
+  const StepScalars& S = *reinterpret_cast<const StepScalars*>(dtp);
+  const double h = S.h_half;
   // FP64: double differences; FP32-bulk and df half step: increments in T
   constexpr bool X = sizeof(T) == 8 && Exact<T>::full;
   double u5[5];
-  hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
-  const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
-  const double by = face_update<T, X, 1>(g, U0, E, h, i, j, k);
-  const double bz = face_update<T, X, 2>(g, U0, E, h, i, j, k);
-  const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
-  const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
-  const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
-  Bh[c] = from_d<T>(bx);
-  Bh[N + c] = from_d<T>(by);
-  Bh[2 * N + c] = from_d<T>(bz);
+  hydro_update<T, X, true, true>(U0, F, S, p, u5);
+  // the cell's upper faces and its lower faces (the upper faces of p - e_a)
+  const double bx = face_update<T, X, true, 0>(g, U0, E, h, c, p.m[1], p.m[2]);
+  const double by = face_update<T, X, true, 1>(g, U0, E, h, c, p.m[2], p.m[0]);
+  const double bz = face_update<T, X, true, 2>(g, U0, E, h, c, p.m[0], p.m[1]);
+  const double bxm = face_update<T, X, true, 0>(g, U0, E, h, c + p.m[0], p.m[1], p.m[2]);
+  const double bym = face_update<T, X, true, 1>(g, U0, E, h, c + p.m[1], p.m[2], p.m[0]);
+  const double bzm = face_update<T, X, true, 2>(g, U0, E, h, c + p.m[2], p.m[0], p.m[1]);
+  Bh.f[0][c] = from_d<T>(bx);
+  Bh.f[1][c] = from_d<T>(by);
+  Bh.f[2][c] = from_d<T>(bz);
   // (the outer ghost layers of a padded grid see the wrap and carry no check)
-  if ((!pos_bits(u5[0]) || !finite_bits(u5[4])) && interior(g, i, j, k)) atomicOr(flags, 1u);
+  if ((!pos_bits(u5[0]) || !finite_bits(u5[4])) && interior(g, p.i, p.j, p.k)) atomicOr(flags, 1u);
   T w8[8];
   if constexpr (std::is_same<T, float>::value) {
     const double bs[3] = {bxm + bx, bym + by, bzm + bz};
@@ -531,34 +749,35 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, const double* __
     prim_store_f32(g, W, c, rho, __drcp_rn(rho), u5[1], u5[2], u5[3], u5[4], bs, w8);
   } else {
     const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
-    const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
-    store_w<T>(g, W, c, p, w8);
+    const PrimD pw = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
+    store_w<T>(W, c, pw, w8);
   }
-  store_ref<T>(Er, N, c, w8);
+  store_ref<T>(Er, c, w8);
 }
 
 // Step 9: U^{n+1} in place.  Each thread reads and writes only its own cell of
 // U (hydro fields and its three upper faces), so the update is race-free in
 // place; floors, W^{n+1} and the next dt follow in k_prim with floors on.
 template <class T>
-__global__ void __launch_bounds__(BX* BY) k_update_full(Grid g, double* U, const T* __restrict__ F,
-                                                        const T* __restrict__ E, const double* __restrict__ dtp) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const double h = dtp[0];
-  const long long N = g.N, c = cidx(g, i, j, k);
+__global__ void __launch_bounds__(BX* BY) k_update_full(Grid g, Fields<double, 8> U, Fields<const T, 21> F,
+                                                        Fields<const T, 3> E, const double* __restrict__ dtp) {
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const int c = p.c;
+  const StepScalars& S = *reinterpret_cast<const StepScalars*>(dtp);
+  const double h = S.dt;
+  const Fields<const double, 8> Uc = as_const(U);
   double u5[5];
   constexpr bool X = Exact<T>::full;
-  hydro_update<T, X>(g, U, F, h, i, j, k, u5);
-  const double bx = face_update<T, X, 0>(g, U, E, h, i, j, k);
-  const double by = face_update<T, X, 1>(g, U, E, h, i, j, k);
-  const double bz = face_update<T, X, 2>(g, U, E, h, i, j, k);
+  hydro_update<T, X, false, false>(Uc, F, S, p, u5);
+  const double bx = face_update<T, X, false, 0>(g, Uc, E, h, c, p.m[1], p.m[2]);
+  const double by = face_update<T, X, false, 1>(g, Uc, E, h, c, p.m[2], p.m[0]);
+  const double bz = face_update<T, X, false, 2>(g, Uc, E, h, c, p.m[0], p.m[1]);
 #pragma unroll
-  for (int f = 0; f < 5; ++f) U[f * N + c] = u5[f];
-  U[5 * N + c] = bx;
-  U[6 * N + c] = by;
-  U[7 * N + c] = bz;
+  for (int f = 0; f < 5; ++f) U.f[f][c] = u5[f];
+  U.f[5][c] = bx;
+  U.f[6][c] = by;
+  U.f[7][c] = bz;
 }
 
 template <class T> __global__ void k_widen(const T* __restrict__ src, double* __restrict__ dst, long long n) {
@@ -573,15 +792,35 @@ template <class T> __global__ void k_narrow(const double* __restrict__ src, T* _
 
 #ifdef MHD_SCALAR_KERNELS
 // --------------------------------------------------------- small kernels --
-__global__ void k_set_dt(double* dt_cur, double value) { dt_cur[0] = value; }
+// the step scalars of step size dt (the factors formed exactly as the
+// update kernels would form them: (dt / 2) / d_a = (0.5 dt) id_a)
+__device__ __forceinline__ void set_step_scalars(const Grid& g, StepScalars* S, double dt) {
+  S->dt = dt;
+  S->h_half = 0.5 * dt;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S->hd_full[a] = dt * g.id[a];
+    S->hd_half[a] = S->h_half * g.id[a];
+    S->hd_half_f[a] = d2f_bits(S->hd_half[a]);
+    const df x(S->hd_full[a]), y(S->hd_half[a]);
+    S->hd_full_hi[a] = x.hi;
+    S->hd_full_lo[a] = x.lo;
+    S->hd_half_hi[a] = y.hi;
+    S->hd_half_lo[a] = y.lo;
+  }
+}
+
+__global__ void k_set_dt(Grid g, double* dt_cur, double value) {
+  set_step_scalars(g, reinterpret_cast<StepScalars*>(dt_cur), value);
+}
 
 // dt = cfl / max inverse crossing time; records it and re-arms the reduction word
 // dt = C_CFL / max rate (Eq. dt), shortened to t_end - t when it would step
 // past t_end (t_end = +inf: no end time); the shortened step lands on t_end.
-__global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int s,
+__global__ void k_finish_dt(Grid g, unsigned long long* dtbits, double* dt_cur, double* dt_log, int s,
                             unsigned* flags, double t_end) {
   const double m = __longlong_as_double((long long)dtbits[0]);
-  double dt = cfl / m;
+  double dt = g.cfl / m;
   if (!(dt > 0.0) || !isfinite(dt)) atomicOr(flags, 2u);
   const double t = dt_cur[1];  // simulated time of the current run
   if (dt >= t_end - t) {
@@ -590,7 +829,7 @@ __global__ void k_finish_dt(double cfl, unsigned long long* dtbits, double* dt_c
   } else {
     dt_cur[1] = t + dt;
   }
-  dt_cur[0] = dt;
+  set_step_scalars(g, reinterpret_cast<StepScalars*>(dt_cur), dt);
   if (dt_log) dt_log[s] = dt;
   dtbits[0] = 0ull;  // +0.0
 }
@@ -776,58 +1015,73 @@ __global__ void __launch_bounds__(DIAG_T) k_diag_final(const double* red_in, dou
 
 template <class T>
 void Launch<T>::prim(const Grid& g, double* U, T* W, unsigned long long* dtbits, unsigned* flags,
-                   unsigned long long* floors, cudaStream_t s, T* Er) {
-    k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, W, dtbits, flags, floors, Er);
-  }
+                     unsigned long long* floors, cudaStream_t s, T* Er) {
+  k_prim<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, fields<8>(U, g.N), fields<8>(W, g.N), dtbits, flags, floors,
+                                                fields<3>(Er, g.N));
+}
 template <class T>
 void Launch<T>::flux_pcm(const Grid& g, int a, const T* W, const double* U, T* F, cudaStream_t s) {
-    const dim3 gr = grid_of(g), bl(BX, BY);
-    if (a == 0) k_flux_pcm<T, 0><<<gr, bl, 0, s>>>(g, W, U, F);
-    if (a == 1) k_flux_pcm<T, 1><<<gr, bl, 0, s>>>(g, W, U, F);
-    if (a == 2) k_flux_pcm<T, 2><<<gr, bl, 0, s>>>(g, W, U, F);
-  }
+  const dim3 gr = grid_of(g), bl(BX, BY);
+  const Fields<const T, 8> Wf = fields<8>(W, g.N);
+  const Fields<T, 7> Fa = fields<7>(F + a * 7 * g.N, g.N);
+  const double* Ba = U + (5 + a) * g.N;
+  if (a == 0) k_flux_pcm<T, 0><<<gr, bl, 0, s>>>(g, Wf, Ba, Fa);
+  if (a == 1) k_flux_pcm<T, 1><<<gr, bl, 0, s>>>(g, Wf, Ba, Fa);
+  if (a == 2) k_flux_pcm<T, 2><<<gr, bl, 0, s>>>(g, Wf, Ba, Fa);
+}
+template <class T, int RC>
+static void launch_recon(const Grid& g, int a, const Fields<const T, 8>& W, const Fields<T, 7>& WL,
+                         const Fields<T, 7>& WR, cudaStream_t s) {
+  const dim3 gr = grid_of(g), bl(BX, BY);
+  if (a == 0) k_recon<T, RC, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
+  if (a == 1) k_recon<T, RC, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
+  if (a == 2) k_recon<T, RC, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
+}
 template <class T>
 void Launch<T>::recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cudaStream_t s) {
-    const dim3 gr = grid_of(g), bl(BX, BY);
-    if (rc == 0) {
-      if (a == 0) k_recon<T, 0, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 1) k_recon<T, 0, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 2) k_recon<T, 0, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
-    } else if (rc == 1) {
-      if (a == 0) k_recon<T, 1, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 1) k_recon<T, 1, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 2) k_recon<T, 1, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
-    } else if (rc == 2) {
-      if (a == 0) k_recon<T, 2, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 1) k_recon<T, 2, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 2) k_recon<T, 2, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
-    } else {
-      if (a == 0) k_recon<T, 3, 0><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 1) k_recon<T, 3, 1><<<gr, bl, 0, s>>>(g, W, WL, WR);
-      if (a == 2) k_recon<T, 3, 2><<<gr, bl, 0, s>>>(g, W, WL, WR);
-    }
-  }
+  const Fields<const T, 8> Wf = fields<8>(W, g.N);
+  const Fields<T, 7> L = fields<7>(WL, g.N), R = fields<7>(WR, g.N);
+  if (rc == 0) launch_recon<T, 0>(g, a, Wf, L, R, s);
+  else if (rc == 1) launch_recon<T, 1>(g, a, Wf, L, R, s);
+  else if (rc == 2) launch_recon<T, 2>(g, a, Wf, L, R, s);
+  else launch_recon<T, 3>(g, a, Wf, L, R, s);
+}
 template <class T>
 void Launch<T>::flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s) {
-    const dim3 gr = grid_of(g), bl(BX, BY);
-    if (a == 0) k_flux_hlld<T, 0><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
-    if (a == 1) k_flux_hlld<T, 1><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
-    if (a == 2) k_flux_hlld<T, 2><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
-  }
+  const dim3 gr = grid_of(g), bl(BX, BY);
+  const Fields<const T, 7> L = fields<7>(WL, g.N), R = fields<7>(WR, g.N);
+  const Fields<T, 7> Fa = fields<7>(F + a * 7 * g.N, g.N);
+  const T* Ba = Bf + a * g.N;
+  if (a == 0) k_flux_hlld<T, 0><<<gr, bl, 0, s>>>(g, L, R, Ba, Fa);
+  if (a == 1) k_flux_hlld<T, 1><<<gr, bl, 0, s>>>(g, L, R, Ba, Fa);
+  if (a == 2) k_flux_hlld<T, 2><<<gr, bl, 0, s>>>(g, L, R, Ba, Fa);
+}
 template <class T>
 void Launch<T>::emf(const Grid& g, const T* W, const T* F, T* E, cudaStream_t s, const T* Er) {
-    if (Er) k_emf<T, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
-    else k_emf<T, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
+  if constexpr (std::is_same<T, double>::value) {
+    if (Er) k_emf_r<T, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
+    else k_emf_r<T, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, W, F, Er, E);
+    return;
   }
+  const Fields<const T, 8> Wf = fields<8>(W, g.N);
+  const Fields<const T, 21> Ff = fields<21>(F, g.N);
+  const Fields<const T, 3> Rf = fields<3>(Er, g.N);
+  const Fields<T, 3> Ef = fields<3>(E, g.N);
+  if (Er) k_emf<T, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, Wf, Ff, Rf, Ef);
+  else k_emf<T, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, Wf, Ff, Rf, Ef);
+}
 template <class T>
 void Launch<T>::update_half(const Grid& g, const double* U, const T* F, const T* E, const double* dtp, T* W, T* Bh,
-                          unsigned* flags, cudaStream_t s, T* Er) {
-    k_update_half<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp, W, Bh, flags, Er);
-  }
+                            unsigned* flags, cudaStream_t s, T* Er) {
+  k_update_half<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, fields<8>(U, g.N), fields<21>(F, g.N), fields<3>(E, g.N),
+                                                       dtp, fields<8>(W, g.N), fields<3>(Bh, g.N), flags,
+                                                       fields<3>(Er, g.N));
+}
 template <class T>
 void Launch<T>::update_full(const Grid& g, double* U, const T* F, const T* E, const double* dtp, cudaStream_t s) {
-    k_update_full<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, U, F, E, dtp);
-  }
+  k_update_full<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, fields<8>(U, g.N), fields<21>(F, g.N), fields<3>(E, g.N),
+                                                       dtp);
+}
 template <class T>
 void Launch<T>::widen(const T* src, double* dst, long long n, cudaStream_t s) {
     k_widen<T><<<1216, 256, 0, s>>>(src, dst, n);

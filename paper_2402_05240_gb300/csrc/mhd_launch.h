@@ -76,9 +76,29 @@ template <class T> struct AdjLaunch {
                          double* gwl, double* gwr, double* gbn, double* f, cudaStream_t s);
 };
 
-void launch_set_dt(double* dt_cur, double value, cudaStream_t s);
-// dt of the next step from the reduction word; t_end = +inf for no end time
-void launch_finish_dt(double cfl, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
+// Scalars of the current step on the device, written with its dt by
+// k_set_dt / k_finish_dt so that the update kernels read the dt-derived
+// factors instead of forming them per cell.  Lives in the context's scalar
+// area (kStepScalarDoubles doubles).
+struct StepScalars {
+  double dt, t;           // step size, simulated time of the current run
+  double h_half;          // dt / 2 (Step 5)
+  double hd_full[3];      // dt / d_a (Step 9)
+  double hd_half[3];      // (dt / 2) / d_a (Step 5)
+  float hd_half_f[3];     // hd_half rounded to float (FP32-bulk half step)
+  float hd_full_hi[3];    // hd_full and hd_half as float pairs (the
+  float hd_full_lo[3];    // double-float conversion of the double values)
+  float hd_half_hi[3];
+  float hd_half_lo[3];
+};
+constexpr int kStepScalarDoubles = 32;
+static_assert(sizeof(StepScalars) <= kStepScalarDoubles * sizeof(double), "step scalars fit their area");
+
+// dt of a step given by the caller
+void launch_set_dt(const Grid& g, double* dt_cur, double value, cudaStream_t s);
+// dt of the next step from the reduction word (C_CFL = g.cfl); t_end = +inf
+// for no end time
+void launch_finish_dt(const Grid& g, unsigned long long* dtbits, double* dt_cur, double* dt_log, int step,
                       unsigned* flags, double t_end, cudaStream_t s);
 
 // Diagnostics scratch layout (doubles): the 9 results (8 field sums, then
