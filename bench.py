@@ -70,59 +70,50 @@ FP64_PEAK_GFLOPS = 2 * FP64_PIPE_GINST
 # Warp-instruction issue limit: 4 schedulers per SM, 152 SMs, 2.07 GHz.
 ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 
-# Per-cell counters of one launch of each stage, from ncu captures at 128^3 of
-# the turbulent box (per-kernel SASS op counters and DRAM bytes), keyed by
-# reconstruction and precision: (FP64 pipe ops DFMA + DADD + DMUL, FP64 flop
-# 2 DFMA + DADD + DMUL, warp instructions, DRAM bytes read + written).  They
-# hold for the kernels as profiled; a kernel changed since has no entry.  The
-# double-float entries predate the comparison helpers whose double
-# specialisations decide branches on bit patterns; for the float-pair type
-# those helpers are the comparisons they replaced, so the float-pair kernels
-# listed compute and access memory as profiled.  The PCM predictor, edge
-# fields and updates do not depend on the reconstruction.
-_PLMC = {
+# Per-cell counters of one launch of each stage, from ncu captures at 192^3 of
+# the turbulent box, PPMC (one kernel per capture; per-kernel SASS op counters
+# and DRAM bytes; the x-axis launch of the per-axis stages, the mean of the x
+# and z launches for the reconstruction), keyed by precision: (FP64 pipe ops
+# DFMA + DADD + DMUL, FP64 flop 2 DFMA + DADD + DMUL, warp instructions, DRAM
+# bytes read + written).  They hold for the kernels as profiled; a kernel
+# changed since has no entry.  The PCM predictor, edge fields, updates and
+# primitives do not depend on the reconstruction; PLMC has no reconstruction
+# entry (its kernel changed after its capture).
+_STAGES = {
     "fp64": {
-        "prim": (121.0, 171.0, 918 / 32, 106.0),
-        "flux_pcm": (235.3, 358.6, 1525 / 32, 101.2),
-        "emf": (72.0, 87.0, 977 / 32, 139.9),
-        "update_half": (88.0, 126.0, 809 / 32, 283.1),
-        "recon": (295.9, 379.9, 2183 / 32, 150.3),
-        "flux_hlld": (234.5, 357.3, 1516 / 32, 162.4),
-        "update_full": (50.0, 71.0, 524 / 32, 260.9),
+        "prim": (130.0, 183.0, 924.3 / 32, 144.3),
+        "flux_pcm": (232.6, 350.8, 1416.9 / 32, 114.2),
+        "emf": (48.0, 51.0, 698.0 / 32, 118.3),
+        "update_half": (92.0, 133.0, 646.0 / 32, 315.6),
+        "flux_hlld": (232.1, 349.9, 1422.6 / 32, 171.9),
+        "update_full": (45.0, 66.0, 352.0 / 32, 268.3),
     },
     "fp32_bulk": {
-        "prim": (19.0, 29.0, 730 / 32, 82.0),
-        "flux_pcm": (0.0, 0.0, 554 / 32, 45.9),
-        "emf": (0.0, 0.0, 570 / 32, 66.8),
-        "update_half": (33.0, 50.0, 1575 / 32, 171.6),
-        "recon": (0.0, 0.0, 774 / 32, 62.7),
-        "flux_hlld": (0.0, 0.0, 530 / 32, 74.3),
-        "update_full": (19.0, 22.0, 1433 / 32, 180.5),
+        "prim": (19.0, 29.0, 707.0 / 32, 102.5),
+        "flux_pcm": (0.0, 0.0, 493.3 / 32, 58.8),
+        "emf": (0.0, 0.0, 224.0 / 32, 58.0),
+        "update_half": (29.0, 46.0, 1094.0 / 32, 188.5),
+        "flux_hlld": (0.0, 0.0, 486.2 / 32, 84.4),
+        "update_full": (16.0, 19.0, 1040.8 / 32, 194.4),
     },
-    # prim, update_half and update_full are left out: their double pressure
-    # recovery and floors (shared by every mode) changed after this capture
     "fp64_df": {
-        "flux_pcm": (0.0, 0.0, 3034 / 32, 101.1),
-        "emf": (0.0, 0.0, 1515 / 32, 140.0),
-        "recon": (0.0, 0.0, 3832 / 32, 151.8),
-        "flux_hlld": (0.0, 0.0, 3000 / 32, 162.5),
+        "prim": (37.0, 53.0, 1517.3 / 32, 144.2),
+        "flux_pcm": (0.0, 0.0, 2876.8 / 32, 114.2),
+        "emf": (0.0, 0.0, 801.9 / 32, 118.2),
+        "update_half": (45.0, 62.0, 2051.0 / 32, 315.5),
+        "flux_hlld": (0.0, 0.0, 2816.5 / 32, 172.0),
+        "update_full": (16.0, 19.0, 1145.0 / 32, 268.1),
     },
 }
-# PPMC: the reconstruction kernels captured on their own (-k regex:k_recon,
-# the three axes of one step at 128^3); the other stages do not depend on the
-# reconstruction and carry over where they are unchanged since their capture
-_PPMC = {prec: {k: v for k, v in tab.items() if k not in ("recon", "flux_hlld")} for prec, tab in _PLMC.items()}
-_PPMC["fp64"]["recon"] = (485.3, 599.0, 4356 / 32, 151.4)
-_PPMC["fp32_bulk"]["recon"] = (0.0, 0.0, 1565 / 32, 63.8)
-_PPMC["fp64_df"]["recon"] = (0.0, 0.0, 8646 / 32, 151.1)
-# the Riemann solver's fast-speed maximum, the edge fields and the kernels that
-# write W (which now also write the cells' reference fields) changed after
-# the captures above
-for _tab in (_PLMC, _PPMC):
-    for _prec in _tab:
-        for _k in ("flux_pcm", "flux_hlld", "emf", "prim", "update_half"):
-            _tab[_prec].pop(_k, None)
-COUNTERS = {"plmc": _PLMC, "ppmc": _PPMC}
+_RECON_PPMC = {
+    "fp64": (420.2, 529.6, 3675.0 / 32, 169.6),
+    "fp32_bulk": (0.0, 0.0, 1260.9 / 32, 80.9),
+    "fp64_df": (0.0, 0.0, 7048.3 / 32, 169.4),
+}
+COUNTERS = {
+    "plmc": {prec: dict(tab) for prec, tab in _STAGES.items()},
+    "ppmc": {prec: dict(tab, recon=_RECON_PPMC[prec]) for prec, tab in _STAGES.items()},
+}
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -273,7 +264,7 @@ def adjoint_fits(mhd, torch, n, recon, precision):
 def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     """Roofline of the dominant stage (largest share of the timed region).
 
-    With per-cell counters of the stage (ncu capture at 128^3):
+    With per-cell counters of the stage (ncu capture at 192^3):
     the stage is bound by the FP64 pipe or by instruction issue, whichever
     runs closer to its peak -- achieved = counted FP64-pipe operations
     (DFMA + DADD + DMUL) per launch / live launch time against the measured
@@ -281,7 +272,7 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
     against the 4-per-clock-per-SM issue limit; both are reported, with the
     HBM view and the flop view.  Without counters: algorithmic bytes per
     launch / launch time against the measured HBM copy bandwidth.  `traffic`
-    is the ncu DRAM bytes per cell of the profiled 128^3 launch scaled to
+    is the ncu DRAM bytes per cell of the profiled 192^3 launch scaled to
     this launch's cells (null without counters).
     """
     T = 4 if precision == "fp32_bulk" else 8
@@ -321,7 +312,7 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
         main = fp64 if fp64["frac"] >= issue["frac"] else issue
         out.update({"bound": "alu", **main, "fp64_pipe": fp64, "issue": issue,
                     "traffic": round(cnt[3] * n3),
-                    "traffic_note": "ncu DRAM bytes per cell at 128^3 scaled to this launch's cells"})
+                    "traffic_note": "ncu DRAM bytes per cell at 192^3 scaled to this launch's cells"})
         if cnt[1]:
             gf = cnt[1] * n3 / per_launch_s / 1e9
             out["flop"] = {"achieved_gflops": round(gf, 1), "peak_gflops": FP64_PEAK_GFLOPS,
@@ -421,6 +412,20 @@ def run_workload(args, mhd, torch, rank):
         r = Wk.adjoint_rollout(mhd, torch, n=args.n or 256, steps=100, every=10)
         value, ms, dtype = r["backward_cell_updates_per_s"], r["backward_s"] / r["steps"] * 1e3, "f32 (FP64 state)"
         wl = f"blast beta=0.1 {r['n']}^3, PPMC + HLLD, FP32-bulk, 100-step adjoint rollout, checkpoints every 10"
+    elif args.workload == "adjoint":
+        # the adjoint step alone (and the forward step it is compared with)
+        # on the turbulent box, in the precision and reconstruction given
+        n = args.n or 512
+        U0 = torch.from_numpy(make_state(n)).cuda()
+        fwd_ms, _, _, sim, U = time_gpu(mhd, torch, U0, n, args.steps, args.warmup, args.recon, args.precision,
+                                        lambda: None)
+        sim.close()
+        del sim, U
+        torch.cuda.empty_cache()
+        r = time_adjoint(mhd, torch, U0, n, args.steps, args.warmup, args.recon, args.precision, lambda: None, fwd_ms)
+        r["forward_ms_per_step"] = fwd_ms
+        value, ms, dtype = r["value"], r["ms_per_step"], DTYPES[args.precision]
+        wl = f"turbulent box {n}^3, {args.recon.upper()} + HLLD, {MODE_NAMES[args.precision]} adjoint step"
     else:
         n = args.n or 459
         r = Wk.slow_wave(mhd, torch, n=n, steps=args.steps, warmup=args.warmup, precision=args.precision)
@@ -457,8 +462,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="turbulent",
-                    choices=["turbulent", "precision512", "adjoint_rollout", "slow_wave"],
-                    help="turbulent: the default step timing; the others are the extra measurements of "
+                    choices=["turbulent", "precision512", "adjoint_rollout", "slow_wave", "adjoint"],
+                    help="turbulent: the default step timing; adjoint: the adjoint step alone (--precision, "
+                         "--recon, --n); the others are the extra measurements of "
                          "paper_2402_05240_gb300.workloads (one JSON line each)")
     args = ap.parse_args()
     if args.warmup < 3:

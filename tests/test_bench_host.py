@@ -37,9 +37,9 @@ def test_roofline_of_a_counted_stage(bench):
     n3 = 256 ** 3
     ms = {"prim": 3.5, "flux_pcm": 7.7, "emf": 3.0, "update_half": 2.8, "recon": 10.9, "flux_hlld": 7.7,
           "update_full": 1.5}
-    r = bench.roofline_of(_prof(ms, 10), "fp64", n3, 6791.4, "measured", "plmc")
+    r = bench.roofline_of(_prof(ms, 10), "fp64", n3, 6791.4, "measured", "ppmc")
     assert r["kernel"] == "recon" and r["bound"] == "alu"
-    ops, flop, winst, dram = bench.COUNTERS["plmc"]["fp64"]["recon"]
+    ops, flop, winst, dram = bench.COUNTERS["ppmc"]["fp64"]["recon"]
     assert r["fp64_pipe"]["achieved"] == pytest.approx(ops * n3 / 10.9e-3 / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(max(r["fp64_pipe"]["frac"], r["issue"]["frac"]), rel=1e-9)
     assert r["traffic"] == round(dram * n3)
@@ -47,19 +47,25 @@ def test_roofline_of_a_counted_stage(bench):
     step_s = sum(ms[k] * n for k, n in LAUNCHES.items()) * 1e-3 + 0.001e-3
     assert r["step_hbm"]["frac_counted"] == pytest.approx(n3 / step_s * 2400 / 1e9 / 6791.4, rel=1e-3)
     assert sum(r["stage_share"].values()) == pytest.approx(1.0, abs=1e-3)
+    # every stage has counters: the step's ncu DRAM bytes per cell
+    tab = bench.COUNTERS["ppmc"]["fp64"]
+    assert r["step_hbm"]["ncu_dram_bytes_per_cell"] == pytest.approx(
+        sum(tab[k][3] * n for k, n in LAUNCHES.items()), abs=0.1)
 
 
 def test_roofline_without_counters_is_hbm_bound(bench):
-    """A dominant stage without counters (here the PCM predictor, changed
-    since its capture) is reported against HBM with no traffic figure."""
+    """A dominant stage without counters (the PLMC reconstruction, changed
+    since its capture) is reported against HBM with no traffic figure, and
+    the step-level ncu DRAM figure is left out."""
     n3 = 128 ** 3
-    ms = {"prim": 0.5, "flux_pcm": 3.0, "emf": 0.4, "update_half": 0.4, "recon": 2.4, "flux_hlld": 1.0,
+    ms = {"prim": 0.5, "flux_pcm": 1.0, "emf": 0.4, "update_half": 0.4, "recon": 3.0, "flux_hlld": 1.0,
           "update_full": 0.2}
-    assert "flux_pcm" not in bench.COUNTERS["ppmc"]["fp64"]
-    r = bench.roofline_of(_prof(ms, 2), "fp64", n3, 6791.4, "measured", "ppmc")
-    assert r["kernel"] == "flux_pcm"
+    assert "recon" not in bench.COUNTERS["plmc"]["fp64"]
+    r = bench.roofline_of(_prof(ms, 2), "fp64", n3, 6791.4, "measured", "plmc")
+    assert r["kernel"] == "recon"
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
-    assert r["frac"] == pytest.approx(120 * n3 / 3.0e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
+    assert r["frac"] == pytest.approx(176 * n3 / 3.0e-3 / 1e9 / 6791.4, abs=1e-4)  # (rounded to 4 places)
+    assert "ncu_dram_bytes_per_cell" not in r["step_hbm"]
 
 
 def test_ppmc_reconstruction_is_bound_by_the_fp64_pipe(bench):
@@ -74,14 +80,16 @@ def test_ppmc_reconstruction_is_bound_by_the_fp64_pipe(bench):
     assert r["frac"] == pytest.approx(ops * n3 / 158.0e-3 / 1e9 / bench.FP64_PIPE_GINST, rel=1e-3)
 
 
-def test_partial_counters_give_no_step_dram_figure(bench):
-    """Double-float: the dominant stage has counters, the primitive and update
-    stages (changed after the capture) do not, so the stage's own figures
-    are reported and the step-level ncu DRAM figure is left out."""
-    n3 = 256 ** 3
-    ms = {"prim": 0.9, "flux_pcm": 3.0, "emf": 0.9, "update_half": 0.6, "recon": 6.2, "flux_hlld": 3.9,
-          "update_full": 0.4}
-    assert "prim" not in bench.COUNTERS["plmc"]["fp64_df"] and "recon" in bench.COUNTERS["plmc"]["fp64_df"]
-    r = bench.roofline_of(_prof(ms, 10), "fp64_df", n3, 6791.4, "measured", "plmc")
-    assert r["kernel"] == "recon" and r["bound"] == "alu" and r["traffic"] is not None
-    assert "ncu_dram_bytes_per_cell" not in r["step_hbm"]
+def test_issue_bound_stage_of_the_fp32_bulk_step(bench):
+    """FP32-bulk: the dominant float reconstruction has no FP64 work, so its
+    roofline is the warp-instruction issue rate against 4 per clock per SM."""
+    n3 = 512 ** 3
+    ms = {"prim": 5.8, "flux_pcm": 2.0, "emf": 1.6, "update_half": 7.3, "recon": 4.3, "flux_hlld": 2.3,
+          "update_full": 5.3}
+    r = bench.roofline_of(_prof(ms, 10), "fp32_bulk", n3, 6762.3, "measured", "ppmc")
+    assert r["kernel"] == "recon" and r["bound"] == "alu"
+    ops, flop, winst, dram = bench.COUNTERS["ppmc"]["fp32_bulk"]["recon"]
+    assert ops == 0.0 and r["fp64_pipe"]["achieved"] == 0.0
+    assert r["unit"] == "G warp-inst/s issued"
+    assert r["achieved"] == pytest.approx(winst * n3 / 4.3e-3 / 1e9, rel=1e-3)
+    assert r["traffic"] == round(dram * n3)
