@@ -667,6 +667,129 @@ __device__ void ppmc_vjp(T gamma, T rho_floor, T p_floor, Load wload, T bn, cons
 }
 
 
+// The same reverse in three passes, for kernels that pass the intermediates
+// through global memory (one-kernel form: the eigensystem, the 28
+// characteristic deviations and their cotangents live at once; for float
+// pairs that is 230 registers and a 1 KB stack frame per thread).  Every sum
+// keeps the order of ppmc_vjp, so the three passes give its result bit for
+// bit.
+//   pass 1: forward reconstruction, face floors and the reverse of the
+//           back-projections: gdm, gdp (7 each), gE, and gw2 = gwl + gwr;
+//   pass 2: the deviations again and the reverse of the PPM limiter per
+//           field: gq(k, 7) for the stencil cells k = 0, 1, 3, 4;
+//   pass 3: the reverse of the projections (put(m, g7) per stencil cell m,
+//           gw2 -= its cotangent) and of the eigensystem (gw2, gbn).
+template <class T, class Load>
+__device__ __forceinline__ void ppmc_deviations(T gamma, Load wload, T bn, T* w2, Eig<T>& E, T (*qs)[7]) {
+  wload(2, w2);
+  eig_build<T>(gamma, w2, bn, E);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T wm[7], d[7];
+    wload(k < 2 ? k : k + 1, wm);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
+    eig_left_o<T>(E, d, qs[k]);
+  }
+}
+
+template <class T, class Load>
+__device__ void ppmc_vjp_pass1(T gamma, T rho_floor, T p_floor, Load wload, T bn, const T* gwl_in, const T* gwr_in,
+                               T* gdm, T* gdp, EigG<T>& gE, T* gw2) {
+  T w2[7];
+  Eig<T> E;
+  T dm[7], dp[7];
+  {
+    T qs[4][7];
+    ppmc_deviations<T>(gamma, wload, bn, w2, E, qs);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
+      T qm, qp;
+      if constexpr (OutlineRev<T>::v) ppm_one_call<T>(col, qm, qp);
+      else ppm_one<T>(col, qm, qp);
+      dm[c] = qm;
+      dp[c] = qp;
+    }
+  }
+  T Wm[7], Wp[7];
+  eig_right<T>(E, dm, Wm);
+  eig_right<T>(E, dp, Wp);
+  T gwl[7], gwr[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    gwl[c] = gwl_in[c];
+    gwr[c] = gwr_in[c];
+  }
+  if (w2[0] + Wp[0] < rho_floor) gwl[0] = T(0);
+  if (w2[4] + Wp[4] < p_floor) gwl[4] = T(0);
+  if (w2[0] + Wm[0] < rho_floor) gwr[0] = T(0);
+  if (w2[4] + Wm[4] < p_floor) gwr[4] = T(0);
+  gE.zero();
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    gw2[c] = gwl[c] + gwr[c];
+    gdm[c] = gdp[c] = T(0);
+  }
+  eig_right_vjp_o<T>(E, dp, gwl, gdp, gE);
+  eig_right_vjp_o<T>(E, dm, gwr, gdm, gE);
+}
+
+// gq[k][c]: cotangent of the deviation of stencil cell (0, 1, 3, 4)[k], field c
+template <class T, class Load>
+__device__ void ppmc_vjp_pass2(T gamma, Load wload, T bn, const T* gdm, const T* gdp, T (*gq)[7]) {
+  T w2[7], qs[4][7];
+  Eig<T> E;
+  ppmc_deviations<T>(gamma, wload, bn, w2, E, qs);
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    const T col[5] = {qs[0][c], qs[1][c], T(0), qs[2][c], qs[3][c]};
+    T gcol[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if constexpr (OutlineRev<T>::v) ppm_one_vjp_call<T>(col, gdm[c], gdp[c], gcol);
+    else ppm_one_vjp<T>(col, gdm[c], gdp[c], gcol);
+    gq[0][c] = gcol[0];
+    gq[1][c] = gcol[1];
+    gq[2][c] = gcol[3];
+    gq[3][c] = gcol[4];
+  }
+}
+
+// gqload(k, g7): the pass-2 cotangents of stencil cell (0, 1, 3, 4)[k]
+template <class T, class Load, class GqLoad, class Put>
+__device__ void ppmc_vjp_pass3(T gamma, Load wload, T bn, GqLoad gqload, EigG<T>& gE, T* gw2, Put put, T& gbn) {
+  T w2[7];
+  wload(2, w2);
+  Eig<T> E;
+  eig_build<T>(gamma, w2, bn, E);
+  const T ir = E.ir;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T wm[7], d[7], gq[7];
+    wload(k < 2 ? k : k + 1, wm);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) d[c] = wm[c] - w2[c];
+    gqload(k, gq);
+    T gd[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    eig_left_vjp_o<T>(E, ir, d, gq, gd, gE);
+    put(k < 2 ? k : k + 1, gd);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) gw2[c] -= gd[c];
+  }
+  eig_fields_vjp<T>(gamma, w2, bn, E, gE, gw2, gbn);
+}
+
+// the 17 eigensystem cotangents as an array (the pass-1 output)
+template <class T> __device__ __forceinline__ void eigg_pack(const EigG<T>& e, T* v) {
+  v[0] = e.rho; v[1] = e.ir; v[2] = e.sr; v[3] = e.isr; v[4] = e.a; v[5] = e.a2; v[6] = e.ia2; v[7] = e.af;
+  v[8] = e.as; v[9] = e.cf; v[10] = e.cs; v[11] = e.Qf; v[12] = e.Qs; v[13] = e.Af; v[14] = e.As; v[15] = e.b1;
+  v[16] = e.b2;
+}
+template <class T> __device__ __forceinline__ void eigg_unpack(const T* v, EigG<T>& e) {
+  e.rho = v[0]; e.ir = v[1]; e.sr = v[2]; e.isr = v[3]; e.a = v[4]; e.a2 = v[5]; e.ia2 = v[6]; e.af = v[7];
+  e.as = v[8]; e.cf = v[9]; e.cs = v[10]; e.Qf = v[11]; e.Qs = v[12]; e.Af = v[13]; e.As = v[14]; e.b1 = v[15];
+  e.b2 = v[16];
+}
+
 // ------------------------------------------------------------- HLLD VJP --
 // reverse of fast_speed: accumulates d c_f / d(rho, p, bl, bt1, bt2) * gcf
 template <class T>

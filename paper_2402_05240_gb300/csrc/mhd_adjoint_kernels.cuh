@@ -417,6 +417,96 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
   S[(long long)NS * 7 * N + c] = gbn;
 }
 
+// PPMC reverse in three passes (ppmc_vjp_pass1..3).  X (kPpmcRevFields
+// arrays) carries gdm, gdp, the 17 eigensystem cotangents and the cell's own
+// cotangent from pass 1 to passes 2 and 3; pass 2 writes its deviation
+// cotangents into the slots of S that pass 3 then overwrites with the
+// stencil cells' cotangents (each cell's slots are read and written by its
+// own thread only).  S has the slot layout of k_adj_recon.
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_ppmc1(Grid g, const T* __restrict__ W, const T* __restrict__ gWL,
+                                                      const T* __restrict__ gWR, Fields<T, kPpmcRevFields> X) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T gl[7], gr[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gl[q] = gWL[q * N + c];
+    gr[q] = gWR[q * N + c];
+  }
+  const T bn = W[(5 + A) * N + c];
+  auto wload = [&](int m, T* out) { load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, m - 2), out); };
+  T gdm[7], gdp[7], gw2[7], ge[17];
+  EigG<T> gE;
+  ppmc_vjp_pass1<T>(from_d<T>(g.gamma), from_d<T>(g.rho_floor), from_d<T>(g.p_floor), wload, bn, gl, gr, gdm, gdp,
+                    gE, gw2);
+  eigg_pack<T>(gE, ge);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    X.f[q][c] = gdm[q];
+    X.f[7 + q][c] = gdp[q];
+    X.f[31 + q][c] = gw2[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 17; ++q) X.f[14 + q][c] = ge[q];
+}
+
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_ppmc2(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
+                                                      T* __restrict__ S) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T gdm[7], gdp[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gdm[q] = X.f[q][c];
+    gdp[q] = X.f[7 + q][c];
+  }
+  const T bn = W[(5 + A) * N + c];
+  auto wload = [&](int m, T* out) { load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, m - 2), out); };
+  T gq[4][7];
+  ppmc_vjp_pass2<T>(from_d<T>(g.gamma), wload, bn, gdm, gdp, gq);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int m = k < 2 ? k : k + 1;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) S[((long long)m * 7 + q) * N + c] = gq[k][q];
+  }
+}
+
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_adj_ppmc3(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
+                                                      T* __restrict__ S) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T gw2[7], ge[17];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) gw2[q] = X.f[31 + q][c];
+#pragma unroll
+  for (int q = 0; q < 17; ++q) ge[q] = X.f[14 + q][c];
+  EigG<T> gE;
+  eigg_unpack<T>(ge, gE);
+  const T bn = W[(5 + A) * N + c];
+  auto wload = [&](int m, T* out) { load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, m - 2), out); };
+  auto gqload = [&](int k, T* out) {
+    const int m = k < 2 ? k : k + 1;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) out[q] = S[((long long)m * 7 + q) * N + c];
+  };
+  auto put = [&](int m, const T* gm) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) S[((long long)m * 7 + q) * N + c] = gm[q];
+  };
+  T gbn = T(0);
+  ppmc_vjp_pass3<T>(from_d<T>(g.gamma), wload, bn, gqload, gE, gw2, put, gbn);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) S[(2LL * 7 + q) * N + c] = gw2[q];
+  S[5LL * 7 * N + c] = gbn;
+}
+
 // cell p gathers slot m from cell p - (m - h) along A, h = NS/2
 template <class T, int RECON, int A>
 __global__ void __launch_bounds__(BX* BY) k_adj_recon_gather(Grid g, const T* __restrict__ S, T* __restrict__ gW) {
@@ -729,6 +819,22 @@ void AdjLaunch<T>::pcm_gather(const Grid& g, int a, const T* gWL, const T* gWR, 
     if (a == 1) k_adj_pcm_gather<T, 1><<<gr, bl, 0, s>>>(g, gWL, gWR, gW);
     if (a == 2) k_adj_pcm_gather<T, 2><<<gr, bl, 0, s>>>(g, gWL, gWR, gW);
   }
+// Which compute types take the three-pass PPMC reverse (else one kernel).
+// Measured, adjoint step of the 256^3 turbulent box: float pairs 317 ->
+// 222 ms (one kernel: 230 registers and a 1 KB stack frame, 2 blocks per
+// SM), float 36.6 -> 34.2 ms; double 505 ms in one kernel against 536 ms in
+// three (it recomputes the eigensystem and the deviations on the FP64 pipe).
+template <class T> struct SplitPpmcRev { static constexpr bool v = !std::is_same<T, double>::value; };
+
+template <class T, int A>
+static void launch_ppmc_rev(const Grid& g, const T* W, const T* gWL, const T* gWR, T* S, T* gW,
+                            const Fields<T, kPpmcRevFields>& X, cudaStream_t s) {
+  const dim3 gr = grid_of(g), bl(BX, BY);
+  k_adj_ppmc1<T, A><<<gr, bl, 0, s>>>(g, W, gWL, gWR, X);
+  k_adj_ppmc2<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+  k_adj_ppmc3<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+  k_adj_recon_gather<T, 2, A><<<gr, bl, 0, s>>>(g, S, gW);
+}
 template <class T>
 template <int R>
 void AdjLaunch<T>::recon_r(const Grid& g, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW,
@@ -748,10 +854,19 @@ void AdjLaunch<T>::recon_r(const Grid& g, int a, const T* W, const T* gWL, const
     }
   }
 template <class T>
-void AdjLaunch<T>::recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s) {
+void AdjLaunch<T>::recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW,
+                         const Fields<T, kPpmcRevFields>& X, cudaStream_t s) {
     if (rc == 0) recon_r<0>(g, a, W, gWL, gWR, S, gW, s);
     if (rc == 1) recon_r<1>(g, a, W, gWL, gWR, S, gW, s);
-    if (rc == 2) recon_r<2>(g, a, W, gWL, gWR, S, gW, s);
+    if (rc == 2) {
+      if constexpr (SplitPpmcRev<T>::v) {
+        if (a == 0) launch_ppmc_rev<T, 0>(g, W, gWL, gWR, S, gW, X, s);
+        if (a == 1) launch_ppmc_rev<T, 1>(g, W, gWL, gWR, S, gW, X, s);
+        if (a == 2) launch_ppmc_rev<T, 2>(g, W, gWL, gWR, S, gW, X, s);
+      } else {
+        recon_r<2>(g, a, W, gWL, gWR, S, gW, s);
+      }
+    }
   }
 template <class T>
 void AdjLaunch<T>::prim(const Grid& g, bool half, const double* U, const double* Uh, const T* Bh, const T* gW, double* g5,

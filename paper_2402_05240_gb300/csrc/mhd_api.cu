@@ -364,6 +364,21 @@ template <class T> struct AdjView {
   unsigned long long* idx;   // argmax word
 };
 
+// Scratch of the three-pass PPMC reverse of axis a: arrays that are dead
+// while it runs -- the corrector fluxes F^{n+1/2} (used by the Step 9 and
+// Step 8 reverses, which come first), the interface states of axis a and the
+// flux cotangents of axis a (both used up by that axis's HLLD reverse, which
+// comes just before).
+template <class T> mhd::Fields<T, mhd::kPpmcRevFields> ppmc_rev_scratch(const AdjView<T>& b, int a, long long N) {
+  mhd::Fields<T, mhd::kPpmcRevFields> X;
+  int q = 0;
+  for (int f = 0; f < 21; ++f) X.f[q++] = b.Fh + f * N;
+  for (int f = 0; f < 7; ++f) X.f[q++] = b.WLa + (a * 7 + f) * N;
+  for (int f = 0; f < 7; ++f) X.f[q++] = b.WRa + (a * 7 + f) * N;
+  for (int f = 0; f < 3; ++f) X.f[q++] = b.gF + (a * 7 + f) * N;
+  return X;
+}
+
 template <class T> int adj_view(mhd_ctx* c, AdjView<T>& v) {
   if (!c->adj_ws) {
     const size_t b = adj_bytes_of(c->cfg);
@@ -460,7 +475,7 @@ int adjoint_step(mhd_ctx* c, const double* Un, double dt, const double* gUp, dou
   for (int a = 0; a < 3; ++a) {
     mhd::AdjLaunch<T>::hlld(g, a, false, b.WLa + a * 7 * N, b.WRa + a * 7 * N, nullptr, nullptr, b.Bh, b.gF, b.gWL,
                             b.gWR, b.gBf, s);
-    mhd::AdjLaunch<T>::recon(g, rc, a, b.Wh, b.gWL, b.gWR, b.gS, b.gW, s);
+    mhd::AdjLaunch<T>::recon(g, rc, a, b.Wh, b.gWL, b.gWR, b.gS, b.gW, ppmc_rev_scratch<T>(b, a, N), s);
   }
   // Step 5 (primitives of the half state, half update)
   mhd::AdjLaunch<T>::prim(g, true, U, b.Uh, b.Bh, b.gW, b.g5, b.gBcc, s);
@@ -502,7 +517,7 @@ int stage_recon_vjp(mhd_ctx* c, const double* U, int axis, int recon, const doub
   cudaMemsetAsync(b.gW, 0, 8 * N * sizeof(T), s);
   cudaMemsetAsync(b.gBf, 0, 3 * N * sizeof(T), s);
   cudaMemsetAsync(gU, 0, 8 * N * sizeof(double), s);
-  mhd::AdjLaunch<T>::recon(g, recon, axis, b.Wn, b.gWL, b.gWR, b.gS, b.gW, s);
+  mhd::AdjLaunch<T>::recon(g, recon, axis, b.Wn, b.gWL, b.gWR, b.gS, b.gW, ppmc_rev_scratch<T>(b, axis, N), s);
   mhd::AdjLaunch<T>::prim(g, false, U, nullptr, nullptr, b.gW, b.g5, b.gBcc, s);
   mhd::AdjLaunch<T>::faces_n(g, b.g5, b.gBcc, b.gBf, gU, s);
   return cuda_status();

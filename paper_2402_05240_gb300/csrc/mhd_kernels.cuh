@@ -51,17 +51,6 @@ __device__ __forceinline__ bool interior(const Grid& g, int i, int j, int k) {
 // reach the kernels as tables of field pointers (kernel parameters), so the
 // address of field f at cell q is one 32 x 64-bit multiply-add: no 64-bit
 // index arithmetic per access.
-template <class T, int K> struct Fields {
-  T* f[K];
-};
-
-// host side: the K field pointers of a field-major array with N cells per field
-template <int K, class T> inline Fields<T, K> fields(T* base, long long N) {
-  Fields<T, K> r;
-  for (int q = 0; q < K; ++q) r.f[q] = base ? base + q * N : nullptr;
-  return r;
-}
-
 struct Cell {
   int i, j, k;
   int c;           // (k ny + j) nx + i

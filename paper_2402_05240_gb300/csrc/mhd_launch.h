@@ -28,6 +28,24 @@ struct Grid {
   int bc[3];         // boundary condition per axis of the caller's grid (0 periodic, 1 outflow)
 };
 
+// A field-major array as a table of field pointers (a kernel parameter):
+// field q of cell c is f[q][c].
+template <class T, int K> struct Fields {
+  T* f[K];
+};
+
+// the K field pointers of a field-major array with N cells per field
+template <int K, class T> inline Fields<T, K> fields(T* base, long long N) {
+  Fields<T, K> r;
+  for (int q = 0; q < K; ++q) r.f[q] = base ? base + q * N : nullptr;
+  return r;
+}
+
+// Intermediates of the three-pass PPMC reverse (per cell: the cotangents of
+// the two limited interface deviations, 7 + 7, of the eigensystem fields,
+// 17, and of the cell's own state after the back-projection, 7).
+constexpr int kPpmcRevFields = 38;
+
 // Launchers of the step kernels for compute type T (double: FP64 step,
 // float: FP32-bulk step); all asynchronous on stream s.
 template <class T> struct Launch {
@@ -66,7 +84,10 @@ template <class T> struct AdjLaunch {
   static void pcm_gather(const Grid& g, int a, const T* gWL, const T* gWR, T* gW, cudaStream_t s);
   template <int R>
   static void recon_r(const Grid& g, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s);
-  static void recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW, cudaStream_t s);
+  // X: scratch of the PPMC reverse (kPpmcRevFields arrays of N values; unused
+  // for the other reconstructions)
+  static void recon(const Grid& g, int rc, int a, const T* W, const T* gWL, const T* gWR, T* S, T* gW,
+                    const Fields<T, kPpmcRevFields>& X, cudaStream_t s);
   static void prim(const Grid& g, bool half, const double* U, const double* Uh, const T* Bh, const T* gW, double* g5,
                    T* gBcc, cudaStream_t s);
   static void faces_n(const Grid& g, const double* g5, const T* gBcc, const T* gBf, double* gU, cudaStream_t s);
