@@ -51,6 +51,8 @@ def stage_bytes(T: int) -> dict:
         "flux_hlld": 15 * T + 7 * T,         # W_L, W_R, face B in; 7 fluxes out (one axis)
         "update_full": 64 + 18 * T + 64,     # U, fluxes, edges in; U out
         "dt": 0,
+        "h2d": 0,                            # host copies of mhd_run_host (not step stages)
+        "d2h": 0,
     }
 
 
@@ -296,7 +298,7 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
                 "frac_min_128B": round(cells_per_s * 128 / 1e9 / hbm_peak, 4)}
     table = COUNTERS.get(recon, {}).get(precision, {})
     if table and all(k in table for k in prof if k != "dt" and prof[k][1]):
-        ncu_b = sum(table[k][3] * v[1] for k, v in prof.items() if k != "dt") / steps
+        ncu_b = sum(table[k][3] * v[1] for k, v in prof.items() if k != "dt" and v[1]) / steps
         step_hbm.update({"ncu_dram_bytes_per_cell": round(ncu_b, 1),
                          "frac_ncu": round(cells_per_s * ncu_b / 1e9 / hbm_peak, 4)})
     out["step_hbm"] = step_hbm
@@ -515,15 +517,24 @@ def main():
     del U
 
     # end to end through the public host-buffer entry point (copies inside)
-    e2e_s = None
+    e2e_s, e2e_parts = None, None
     if args.e2e_steps > 0:
-        host = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True)
+        # page-locked, huge-page backed host memory from the library
+        # (mhd_host_alloc): the copies stay at the link rate between steps
+        host = mhd.host_buffer(8, n, n, n)
         host.copy_(U0.cpu())
         mhd.mhd_run_host(sim.ctx, host, 1)  # warm the host-state buffer
+        mhd.mhd_profile_enable(sim.ctx, True)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             mhd.mhd_run_host(sim.ctx, host, 1)
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        # device time of each part of a call (CUDA events on the library's stream)
+        p = mhd.mhd_profile_read(sim.ctx)
+        mhd.mhd_profile_enable(sim.ctx, False)
+        e2e_parts = {"h2d_ms": p["h2d"][0] / args.e2e_steps, "d2h_ms": p["d2h"][0] / args.e2e_steps,
+                     "step_ms": sum(v[0] for k, v in p.items() if k not in ("h2d", "d2h")) / args.e2e_steps,
+                     "wall_ms": e2e_s * 1e3}
         del host
     sim.close()
     del sim
@@ -598,7 +609,7 @@ def main():
                    "input_generation_s": round(gen_s, 1)},
         "roofline": roof,
         "e2e": ({"value": world * n3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 64 * n3,
-                 "d2h_bytes_per_step": 64 * n3} if e2e_s else None),
+                 "d2h_bytes_per_step": 64 * n3, "parts": e2e_parts} if e2e_s else None),
         "gpu_launches": launches64,
         "clocks": clk,
         "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in prof64.items()},

@@ -182,6 +182,27 @@ int mhd_evolve(mhd_ctx* ctx, double* U_dev, double t_end, int max_steps, double*
  * mhd_status returns them. */
 int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
 
+/* Library infrastructure, not in the paper.  Allocates bytes of
+ * page-locked host memory for mhd_run_host (or any host<->device copy):
+ * aligned to and rounded up to a multiple of the transparent huge page size
+ * (2 MiB or 512 MiB, from the kernel; 2 MiB if it does not say), advised as
+ * huge pages, then registered with cudaHostRegister on the current device.
+ * On hosts whose DMA reaches host memory through an IOMMU (the Grace host of
+ * a GB300), copies from ordinary page-locked memory slow down to a fraction
+ * of the link rate after GPU work has run in between (translation misses
+ * over the many small pages), while copies from huge-page memory keep the
+ * full rate.  Where the kernel gives no huge pages, the memory is ordinary
+ * page-locked memory.  *out_host receives the address (owned by the caller,
+ * freed by mhd_host_free; contents undefined).  No device work.  Errors:
+ * MHD_ERR_ARG (out_host NULL or bytes 0), MHD_ERR_OOM (host allocation
+ * failed), MHD_ERR_CUDA (registration failed, e.g. no CUDA device). */
+int mhd_host_alloc(size_t bytes, void** out_host);
+
+/* Library infrastructure, not in the paper.  Unregisters and frees memory
+ * from mhd_host_alloc (NULL: no-op).  Errors: MHD_ERR_CUDA (unregistration
+ * failed; the memory is not freed). */
+int mhd_host_free(void* host);
+
 /* Vector-Jacobian product of one mhd_step at fixed dt (not in the paper):
  * gU_n = (dU^{n+1}/dU^n)^T gU_np1.  U_n_dev: the state the forward step
  * started from (read only); gU_np1_dev: cotangent of U^{n+1}; gU_n_dev:
@@ -282,7 +303,9 @@ const char* mhd_strerror(int code);
 #define MHD_STAGE_FLUX_HLLD 5   /* corrector HLLD fluxes (Step 7)             */
 #define MHD_STAGE_UPDATE_FULL 6 /* full-step update (Step 9)                  */
 #define MHD_STAGE_DT 7          /* dt finalisation                            */
-#define MHD_NUM_STAGES 8
+#define MHD_STAGE_H2D 8         /* host -> device copy of mhd_run_host        */
+#define MHD_STAGE_D2H 9         /* device -> host copy of mhd_run_host        */
+#define MHD_NUM_STAGES 10
 
 /* Library infrastructure, not in the paper.  Synchronises the context's
  * stream, turns the per-stage timing on (on != 0) or off and clears what

@@ -2,7 +2,12 @@
 // sequencing.  Every numerical stage runs in the kernels of mhd_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <sys/mman.h>
+
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -689,8 +694,8 @@ int mhd_profile_read(mhd_ctx* c, double ms[MHD_NUM_STAGES], long long launches[M
 }
 
 const char* mhd_stage_name(int stage) {
-  static const char* names[MHD_NUM_STAGES] = {"prim", "flux_pcm", "emf", "update_half", "recon",
-                                              "flux_hlld", "update_full", "dt"};
+  static const char* names[MHD_NUM_STAGES] = {"prim", "flux_pcm",    "emf", "update_half", "recon",
+                                              "flux_hlld", "update_full", "dt",  "h2d",         "d2h"};
   if (stage < 0 || stage >= MHD_NUM_STAGES) return "unknown";
   return names[stage];
 }
@@ -776,15 +781,61 @@ int mhd_run_host(mhd_ctx* c, double* U_host, int nsteps, double* t_host) {
     }
   }
   cudaStream_t s = c->stream;
-  if (cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MHD_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  prof(c, MHD_STAGE_H2D, [&] { e = cudaMemcpyAsync(c->host_state, U_host, bytes, cudaMemcpyHostToDevice, s); });
+  if (e != cudaSuccess) return MHD_ERR_CUDA;
   int st = mhd_run(c, c->host_state, nsteps, nullptr);
   if (st != MHD_OK) return st;
-  if (cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
+  prof(c, MHD_STAGE_D2H, [&] { e = cudaMemcpyAsync(U_host, c->host_state, bytes, cudaMemcpyDeviceToHost, s); });
+  if (e != cudaSuccess) return MHD_ERR_CUDA;
   double t = 0;
   if (cudaMemcpyAsync(&t, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MHD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MHD_ERR_CUDA;
   if (t_host) *t_host = t;
   return mhd_status(c, nullptr);
+}
+
+namespace {
+// the kernel's transparent huge page size (PMD size), 2 MiB if not given
+size_t huge_page_bytes() {
+  size_t v = 0;
+  if (FILE* f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+    unsigned long long x = 0;
+    if (std::fscanf(f, "%llu", &x) == 1) v = (size_t)x;
+    std::fclose(f);
+  }
+  return (v >= 4096 && (v & (v - 1)) == 0) ? v : ((size_t)2 << 20);
+}
+}  // namespace
+
+int mhd_host_alloc(size_t bytes, void** out) {
+  if (!out || bytes == 0) return MHD_ERR_ARG;
+  *out = nullptr;
+  const size_t hp = huge_page_bytes();
+  if (bytes > SIZE_MAX - hp) return MHD_ERR_ARG;
+  const size_t total = (bytes + hp - 1) / hp * hp;
+  void* p = nullptr;
+  if (posix_memalign(&p, hp, total) != 0 || !p) return MHD_ERR_OOM;
+#ifdef MADV_HUGEPAGE
+  madvise(p, total, MADV_HUGEPAGE);  // advice only: without huge pages the memory stays usable
+#endif
+  if (cudaHostRegister(p, total, cudaHostRegisterDefault) != cudaSuccess) {
+    cudaGetLastError();
+    std::free(p);
+    return MHD_ERR_CUDA;
+  }
+  *out = p;
+  return MHD_OK;
+}
+
+int mhd_host_free(void* p) {
+  if (!p) return MHD_OK;
+  if (cudaHostUnregister(p) != cudaSuccess) {
+    cudaGetLastError();
+    return MHD_ERR_CUDA;
+  }
+  std::free(p);
+  return MHD_OK;
 }
 
 int mhd_adjoint_step(mhd_ctx* c, const double* U_n, double dt, const double* gU_np1, double* gU_n) {

@@ -409,6 +409,28 @@ __global__ void __launch_bounds__(BX* BY) k_flux_hlld(Grid g, Fields<const T, 7>
   for (int q = 0; q < 7; ++q) FA.f[q][c] = f[q];
 }
 
+// The float Riemann kernel keeps restrict-qualified base pointers with
+// 64-bit indices: measured at 512^3 (PPMC turbulent box), 6.25 ms per step
+// for its three launches against 6.89 ms in the pointer-table form above;
+// the double and float-pair Riemann kernels are as fast or faster in the
+// table form.
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY) k_flux_hlld_r(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
+                                                        const T* __restrict__ Bf, T* __restrict__ F) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k), cn = nb<A>(g, ci.i, ci.j, ci.k, 1);
+  T wl[7], wr[7], f[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    wl[q] = WL[q * N + c];
+    wr[q] = WR[q * N + cn];
+  }
+  hlld<T>(from_d<T>(g.gamma), from_d<T>(g.igm1), wl, wr, Bf[A * N + c], f);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[((long long)A * 7 + q) * N + c] = f[q];
+}
+
 // ------------------------------------------------------------ Steps 4, 8 --
 // Edge A of cell p at p + e_B/2 + e_C/2, (B, C) = (A+1, A+2): mean of the four
 // face fields plus the upwinded "face minus reference" slopes (Eq. emf-edge,
@@ -1038,6 +1060,12 @@ void Launch<T>::recon(const Grid& g, int rc, int a, const T* W, T* WL, T* WR, cu
 template <class T>
 void Launch<T>::flux_hlld(const Grid& g, int a, const T* WL, const T* WR, const T* Bf, T* F, cudaStream_t s) {
   const dim3 gr = grid_of(g), bl(BX, BY);
+  if constexpr (std::is_same<T, float>::value) {
+    if (a == 0) k_flux_hlld_r<T, 0><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+    if (a == 1) k_flux_hlld_r<T, 1><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+    if (a == 2) k_flux_hlld_r<T, 2><<<gr, bl, 0, s>>>(g, WL, WR, Bf, F);
+    return;
+  }
   const Fields<const T, 7> L = fields<7>(WL, g.N), R = fields<7>(WR, g.N);
   const Fields<T, 7> Fa = fields<7>(F + a * 7 * g.N, g.N);
   const T* Ba = Bf + a * g.N;

@@ -11,7 +11,9 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -73,6 +75,8 @@ def _load_library():
         "mhd_adjoint_workspace_bytes": (ip, [ctypes.POINTER(mhd_config), ctypes.POINTER(ctypes.c_size_t)]),
         "mhd_stage_recon_vjp": (ip, [vp, vp, ip, ip, vp, vp, vp]),
         "mhd_stage_hlld_vjp": (ip, [ip, ctypes.c_double, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "mhd_host_alloc": (ip, [ctypes.c_size_t, ctypes.POINTER(vp)]),
+        "mhd_host_free": (ip, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +231,24 @@ def mhd_run_host(ctx, U_host: torch.Tensor, nsteps: int) -> float:
     return t.value
 
 
+def host_buffer(*shape) -> torch.Tensor:
+    """A float64 host tensor of the given shape in page-locked, huge-page
+    backed memory from mhd_host_alloc (the buffer for mhd_run_host that
+    keeps the copies at the link rate); freed when the last tensor viewing
+    it is gone."""
+    numel = 1
+    for s in shape:
+        numel *= int(s)
+    if numel < 1:
+        raise ValueError("host_buffer: empty shape")
+    p = ctypes.c_void_p()
+    _check(LIB.mhd_host_alloc(numel * 8, ctypes.byref(p)), "mhd_host_alloc")
+    raw = (ctypes.c_double * numel).from_address(p.value)
+    arr = np.frombuffer(raw, dtype=np.float64)
+    weakref.finalize(arr, LIB.mhd_host_free, ctypes.c_void_p(p.value))
+    return torch.from_numpy(arr).view(*shape)
+
+
 def mhd_adjoint_step(ctx, U_n: torch.Tensor, dt: float, gU_np1: torch.Tensor, gU_n: torch.Tensor):
     _check(LIB.mhd_adjoint_step(ctx, _field(ctx, U_n, 8, "U_n"), float(dt), _field(ctx, gU_np1, 8, "gU_np1"),
                                 _field(ctx, gU_n, 8, "gU_n")), "mhd_adjoint_step")
@@ -306,7 +328,7 @@ def mhd_stage_hlld_vjp(gamma, precision: int, wl, wr, bn, gf, gwl, gwr, gbn, f, 
            "mhd_stage_hlld_vjp")
 
 
-MHD_NUM_STAGES = 8
+MHD_NUM_STAGES = 10
 
 
 def mhd_profile_enable(ctx, on: bool):

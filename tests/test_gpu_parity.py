@@ -5,6 +5,7 @@ target); per-stage FP64 outputs element-wise within 1e-12 relative to the
 field scale; FP32-bulk step rel L1 <= 1e-5 against the FP64 oracle.
 Sizes span several 32 x 4 thread tiles with ragged tails.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -171,24 +172,50 @@ def test_fixed_dt_step_matches_run(mhd):
 def test_run_host_equals_copy_run_copy(mhd, precision, n, steps):
     """mhd_run_host (the host-buffer entry point): the state (floors
     included, set high enough to fire) and the simulated time equal those of
-    a copy, mhd_run and a copy back, bit for bit, from pinned and from
-    pageable host memory, in every precision."""
+    a copy, mhd_run and a copy back, bit for bit, from pinned, pageable and
+    mhd_host_alloc (huge-page) host memory, in every precision."""
     U0 = turb(n, seed=11)
     ref_sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision, rho_floor=0.9, p_floor=0.5)
     ref = cuda(U0)
     dts = torch.zeros(steps, dtype=torch.float64, device="cuda")
     ref_sim.run(ref, steps, dts)
     ref_sim.status()
-    for pinned in (True, False):
+    for kind in ("pinned", "pageable", "host_buffer"):
         sim = mhd.Sim(*n, cfl=0.3, recon="ppmc", precision=precision, rho_floor=0.9, p_floor=0.5)
         host = torch.from_numpy(U0.copy())
-        if pinned:
+        if kind == "pinned":
             host = host.pin_memory()
+        elif kind == "host_buffer":
+            hb = mhd.host_buffer(*host.shape)
+            hb.copy_(host)
+            host = hb
         t = mhd.mhd_run_host(sim.ctx, host, steps)
-        assert torch.equal(host, ref.cpu()), (precision, n, steps, pinned)
+        assert torch.equal(host, ref.cpu()), (precision, n, steps, kind)
         assert t == float(dts.sum().item()) or abs(t - float(dts.sum().item())) <= 1e-15 * t
         sim.close()
     ref_sim.close()
+
+
+def test_host_alloc_and_free(mhd):
+    """mhd_host_alloc gives registered host memory that copies both ways and
+    frees; size 0 and a NULL output are argument errors; freeing NULL is a
+    no-op."""
+    p = ctypes.c_void_p()
+    assert mhd.LIB.mhd_host_alloc(0, ctypes.byref(p)) == mhd.MHD_ERR_ARG
+    assert mhd.LIB.mhd_host_alloc(64, None) == mhd.MHD_ERR_ARG
+    assert mhd.LIB.mhd_host_free(None) == mhd.MHD_OK
+    nbytes = 3 * (1 << 20) + 8  # not a multiple of the huge page size
+    assert mhd.LIB.mhd_host_alloc(nbytes, ctypes.byref(p)) == mhd.MHD_OK and p.value
+    host = torch.frombuffer((ctypes.c_uint8 * nbytes).from_address(p.value), dtype=torch.uint8)
+    host.copy_(torch.arange(nbytes, dtype=torch.int64).remainder(251).to(torch.uint8))
+    dev = host.to("cuda", non_blocking=True)
+    back = torch.empty_like(host)
+    back.copy_(dev)
+    assert torch.equal(back, host)
+    del host
+    assert mhd.LIB.mhd_host_free(p) == mhd.MHD_OK
+    t = mhd.host_buffer(2, 3)
+    assert t.shape == (2, 3) and t.dtype == torch.float64
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
