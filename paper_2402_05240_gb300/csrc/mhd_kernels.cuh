@@ -115,6 +115,20 @@ template <> __device__ __forceinline__ void block_max_to<df>(df v, unsigned long
   block_max_to<double>((double)v, dst);
 }
 
+// the maximum of v over the thread block, returned to every thread
+// (non-negative values; a NaN is ignored)
+__device__ __forceinline__ float block_max_all(float v) {
+  __shared__ float red_f[BX * BY / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) red_f[t >> 5] = v;
+  __syncthreads();
+  float m = red_f[0];
+#pragma unroll
+  for (int w = 1; w < BX * BY / 32; ++w) m = fmaxf(m, red_f[w]);
+  return m;
+}
+
 // inverse crossing time max over l of (|v_l| + c_f,l) / d_l of one cell; the
 // step is dt = C_CFL / (max over cells) (Eq. dt)
 // (c_f of Eq. c_f per axis, with 1/rho and a^2 = gamma P / rho shared by the three axes)
@@ -240,6 +254,8 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, Fields<double, 8> U, Fi
                                                  unsigned* flags, unsigned long long* floors, Fields<T, 3> Er) {
   const Cell p = thread_cell(g);
   T inv = T(0);
+  bool wd = false;  // (double) this cell's primitives wk enter the CFL maximum
+  double wk[8];
   if (p.ok) {
     const int c = p.c;
     const bool in = interior(g, p.i, p.j, p.k);
@@ -287,10 +303,55 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, Fields<double, 8> U, Fi
       const PrimD pw = prim_core_ir(g, rho, ir, m0, m1, m2, e, b);
       store_w<T>(W, c, pw, w8);
       store_ref<T>(Er, c, w8);
-      if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
+      if constexpr (std::is_same<T, double>::value) {
+        if (dtbits && in) {
+          wd = true;
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wk[f] = w8[f];
+        }
+      } else {
+        if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
+      }
     }
   }
-  if (dtbits) block_max_to<T>(inv, dtbits);
+  if constexpr (std::is_same<T, double>::value) {
+    // The CFL maximum of the FP64 step.  Each interior cell's rate is first
+    // estimated in float from its primitives rounded to float.  Where the
+    // grid's 1/d_l and the cell's density and pressure lie in [1e-9, 1e9],
+    // every intermediate of the estimate is a normal float, an overflow
+    // (giving a non-finite estimate) or an underflow whose absolute error
+    // is negligible against a^2 = gamma P / rho, so a finite estimate is
+    // within a relative 1e-5 of the exact rate.  The block maximum M of
+    // those estimates then bounds their cells' exact rates, and only a cell
+    // whose estimate reaches M (1 - 1e-4), or whose estimate is not trusted
+    // (outside the range, not finite), can hold the block's exact maximum.
+    // Those cells evaluate the double rate: the block's maximum is that of
+    // the per-cell double evaluation, bit for bit, at a fraction of the FP64
+    // work (typically one warp in a few per block).
+    if (dtbits) {
+      auto in_range = [](double x) {  // 1e-9 <= x <= 1e9, on the bit pattern (integer pipes)
+        const long long b = dbits(x);
+        return b >= dbits(1e-9) && b <= dbits(1e9);
+      };
+      const bool grid_ok = in_range(g.id[0]) && in_range(g.id[1]) && in_range(g.id[2]);
+      float est = 0.0f;
+      bool trusted = false;
+      if (wd && grid_ok && in_range(wk[0]) && in_range(wk[4])) {
+        float wf[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wf[f] = d2f_bits(wk[f]);
+        est = cell_inv_crossing<float>(g, wf);
+        trusted = est <= 3.402823466e38f;  // false for an infinity or a NaN
+      }
+      const float m = block_max_all(trusted ? est : 0.0f);
+      const bool cand = wd && (!trusted || !(est < m * (1.0f - 1e-4f)));
+      double inv_d = 0.0;
+      if (cand) inv_d = cell_inv_crossing<double>(g, wk);
+      block_max_to<double>(inv_d, dtbits);
+    }
+  } else {
+    if (dtbits) block_max_to<T>(inv, dtbits);
+  }
 }
 
 // directional 7-vector (rho, v_n, v_t1, v_t2, P, B_t1, B_t2) of cell q

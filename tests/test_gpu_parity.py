@@ -64,6 +64,41 @@ def test_dt(mhd, precision):
     assert abs(dt - ref) <= (1e-14 if precision == "fp64" else 1e-6) * ref
 
 
+def _energy_for_pressure(U, p, gamma=5.0 / 3.0):
+    """Sets E so that the pressure recovered from U is p (face-averaged B)."""
+    bcc = [0.5 * (U[5 + a] + np.roll(U[5 + a], 1, axis=2 - a)) for a in range(3)]
+    ke = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+    U[4] = p / (gamma - 1.0) + ke + 0.5 * (bcc[0] ** 2 + bcc[1] ** 2 + bcc[2] ** 2)
+
+
+@pytest.mark.parametrize("case", ["float_overflow", "float_underflow", "near_ties"])
+def test_dt_extreme_states(mhd, case):
+    """The FP64 CFL maximum selects its candidate cells from float estimates
+    of the rates; states whose float estimates overflow, underflow or tie
+    still give the oracle's dt (the exact per-cell maximum)."""
+    n = RAGGED
+    rng = np.random.default_rng(7)
+    if case == "float_overflow":
+        U = turb(n)
+        # one strong face field: B_cc of two cells ~ 2e19, B^2 beyond float range
+        U[5, 3, 5, 7] = 4e19
+        _energy_for_pressure(U, 1.0)
+    elif case == "float_underflow":
+        U = turb(n)
+        U[0] = 1e-30 * (1.0 + 0.5 * rng.random(U[0].shape))
+        U[1:4] *= 1e-33
+        U[5:8] = 1e-20 * (1.0 + rng.random(U[5:8].shape))  # B^2 ~ 1e-40 underflows in float
+        _energy_for_pressure(U, 1e-35)
+    else:
+        U = I.uniform(I.Box(*n), 1.0, (1.0, 0.0, 0.0), 0.6, (0.3, 0.2, 0.1))
+        U[1] *= 1.0 + 1e-13 * rng.standard_normal(U[1].shape)
+        _energy_for_pressure(U, 0.6)
+    sim = mhd.Sim(*n, cfl=0.3, rho_floor=1e-300, p_floor=1e-300)
+    dt = sim.dt(cuda(U))
+    ref = O.Oracle(*n, rho_floor=1e-300, p_floor=1e-300).dt(U, 0.3)
+    assert abs(dt - ref) <= 1e-14 * ref, (case, dt, ref)
+
+
 @pytest.mark.parametrize("recon", ["pcm", "plmc", "ppmc", "plm_prim"])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_recon_states(mhd, recon, axis):
