@@ -83,7 +83,7 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # entry (its kernel changed after its capture).
 _STAGES = {
     "fp64": {
-        "prim": (130.0, 183.0, 924.3 / 32, 144.3),
+        # (prim: changed after the capture -- the CFL maximum from float estimates)
         "flux_pcm": (232.6, 350.8, 1416.9 / 32, 114.2),
         "emf": (48.0, 51.0, 698.0 / 32, 118.3),
         "update_half": (92.0, 133.0, 646.0 / 32, 315.6),
