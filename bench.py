@@ -83,7 +83,7 @@ ISSUE_PEAK_GWARPINST = 4 * 152 * 2.07
 # entry (its kernel changed after its capture).
 _STAGES = {
     "fp64": {
-        # (prim: changed after the capture -- the CFL maximum from float estimates)
+        "prim": (45.7, 65.1, 1020.3 / 32, 145.0),
         "flux_pcm": (232.6, 350.8, 1416.9 / 32, 114.2),
         "emf": (48.0, 51.0, 698.0 / 32, 118.3),
         "update_half": (92.0, 133.0, 646.0 / 32, 315.6),
@@ -95,7 +95,7 @@ _STAGES = {
         "flux_pcm": (0.0, 0.0, 493.3 / 32, 58.8),
         "emf": (0.0, 0.0, 224.0 / 32, 58.0),
         "update_half": (29.0, 46.0, 1094.0 / 32, 188.5),
-        "flux_hlld": (0.0, 0.0, 486.2 / 32, 84.4),
+        "flux_hlld": (0.0, 0.0, 524.2 / 32, 84.3),
         "update_full": (16.0, 19.0, 1040.8 / 32, 194.4),
     },
     "fp64_df": {

@@ -27,6 +27,22 @@ template <class T> struct AdjBufs {
   double* g5;  // [5][N]
 };
 
+// The reverse kernels address cells like the step kernels: 32-bit cell
+// indices with the periodic neighbour offsets of thread_cell, and field
+// pointers formed once per thread from the restrict-qualified base pointers.
+template <int K, class T> __device__ __forceinline__ Fields<T, K> fields_of(T* base, long long N) {
+  Fields<T, K> r;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.f[q] = base + q * N;
+  return r;
+}
+// the step scalars of a step of size dt (as the dt kernels form them)
+__device__ __forceinline__ StepScalars step_scalars_of(const Grid& g, double dt) {
+  StepScalars S;
+  set_step_scalars(g, &S, dt);
+  return S;
+}
+
 // ------------------------------------------------- R1: floors of Step 9 --
 // Recomputes the pre-floor U^{n+1} of the cell; writes the pre-floor
 // cotangent of the hydro fields into gU and the floor's B_cc cotangent.
@@ -35,19 +51,23 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
                                                        const T* __restrict__ E, double dt,
                                                        const double* __restrict__ gUp, double* __restrict__ gU,
                                                        T* __restrict__ gBccF) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const long long N = g.N, c = cidx(g, i, j, k);
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const long long N = g.N;
+  const int c = p.c;
+  const Fields<const double, 8> Uf = fields_of<8>(U, N);
+  const Fields<const T, 21> Ff = fields_of<21>(F, N);
+  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  const StepScalars S = step_scalars_of(g, dt);
   double u5[5];
   constexpr bool X = Exact<T>::full;  // the arithmetic of k_update_full
-  hydro_update<T, X>(g, U, F, dt, i, j, k, u5);
-  const double bx = face_update<T, X, 0>(g, U, E, dt, i, j, k);
-  const double by = face_update<T, X, 1>(g, U, E, dt, i, j, k);
-  const double bz = face_update<T, X, 2>(g, U, E, dt, i, j, k);
-  const double bxm = face_update<T, X, 0>(g, U, E, dt, wrapi(i - 1, g.n[0]), j, k);
-  const double bym = face_update<T, X, 1>(g, U, E, dt, i, wrapi(j - 1, g.n[1]), k);
-  const double bzm = face_update<T, X, 2>(g, U, E, dt, i, j, wrapi(k - 1, g.n[2]));
+  hydro_update<T, X, true, false>(Uf, Ff, S, p, u5);
+  const double bx = face_update<T, X, true, 0>(g, Uf, Ef, S.dt, c, p.m[1], p.m[2]);
+  const double by = face_update<T, X, true, 1>(g, Uf, Ef, S.dt, c, p.m[2], p.m[0]);
+  const double bz = face_update<T, X, true, 2>(g, Uf, Ef, S.dt, c, p.m[0], p.m[1]);
+  const double bxm = face_update<T, X, true, 0>(g, Uf, Ef, S.dt, c + p.m[0], p.m[1], p.m[2]);
+  const double bym = face_update<T, X, true, 1>(g, Uf, Ef, S.dt, c + p.m[1], p.m[2], p.m[0]);
+  const double bzm = face_update<T, X, true, 2>(g, Uf, Ef, S.dt, c + p.m[2], p.m[0], p.m[1]);
   const double b[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   double g5[5];
 #pragma unroll
@@ -96,11 +116,12 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
 // cotangent of the new face B_a of cell p: gUp face + (1/2)(gBcc_a(p) + gBcc_a(p + e_a))
 template <class T, int A>
 __device__ __forceinline__ double face_cot(const Grid& g, const double* __restrict__ gUpF, const T* __restrict__ gBcc,
-                                           const T* __restrict__ gBfx, int i, int j, int k) {
-  const long long N = g.N, c = cidx(g, i, j, k);
-  double v = 0.5 * (to_d<T>(gBcc[A * N + c]) + to_d<T>(gBcc[A * N + nb<A>(g, i, j, k, 1)]));
-  if (gUpF) v += gUpF[A * N + c];
-  if (gBfx) v += to_d<T>(gBfx[A * N + c]);
+                                           const T* __restrict__ gBfx, int q, int oA) {
+  // q: the cell; oA: the offset from q to q + e_A
+  const long long N = g.N;
+  double v = 0.5 * (to_d<T>(gBcc[A * N + q]) + to_d<T>(gBcc[A * N + q + oA]));
+  if (gUpF) v += gUpF[A * N + q];
+  if (gBfx) v += to_d<T>(gBfx[A * N + q]);
   return v;
 }
 
@@ -124,9 +145,9 @@ __device__ __forceinline__ void block_sum_to(double v, double* part) {
 // and curl_a the face curl of E (the update is U' = U - h D, B' = B - h curl).
 template <class T>
 __device__ __forceinline__ double update_rate_dot(const Grid& g, const T* __restrict__ F, const T* __restrict__ E,
-                                                  const double* g5, const double* gf, int i, int j, int k) {
-  const long long N = g.N, c = cidx(g, i, j, k);
-  const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
+                                                  const double* g5, const double* gf, const Cell& p) {
+  const long long N = g.N;
+  const int c = p.c;
   double s = 0.0;
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
@@ -134,13 +155,14 @@ __device__ __forceinline__ double update_rate_dot(const Grid& g, const T* __rest
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-      d += g.id[a] * (to_d<T>(Fa[c]) - to_d<T>(Fa[cm[a]]));
+      d += g.id[a] * (to_d<T>(Fa[c]) - to_d<T>(Fa[c + p.m[a]]));
     }
     s += g5[f] * d;
   }
-  s += gf[0] * face_curl<T, true, 0>(g, E, i, j, k);
-  s += gf[1] * face_curl<T, true, 1>(g, E, i, j, k);
-  s += gf[2] * face_curl<T, true, 2>(g, E, i, j, k);
+  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  s += gf[0] * face_curl<T, true, 0>(g, Ef, c, p.m[1], p.m[2]);
+  s += gf[1] * face_curl<T, true, 1>(g, Ef, c, p.m[2], p.m[0]);
+  s += gf[2] * face_curl<T, true, 2>(g, Ef, c, p.m[0], p.m[1]);
   return s;
 }
 
@@ -150,9 +172,10 @@ __device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const
                                                   const double* __restrict__ gUpF, const T* __restrict__ gBcc,
                                                   const T* __restrict__ gBfx, double* gU, T* __restrict__ gF,
                                                   T* __restrict__ gE, const T* __restrict__ Fs,
-                                                  const T* __restrict__ Es, int i, int j, int k) {
-  const long long N = g.N, c = cidx(g, i, j, k);
-  const long long cp[3] = {nb<0>(g, i, j, k, 1), nb<1>(g, i, j, k, 1), nb<2>(g, i, j, k, 1)};
+                                                  const T* __restrict__ Es, const Cell& p) {
+  const long long N = g.N;
+  const int c = p.c;
+  const int cp[3] = {c + p.p[0], c + p.p[1], c + p.p[2]};
   // hydro: U'_f(p) has -h/d_a F_a(p) and +h/d_a F_a(p - e_a), so
   // gF_a[comp](p) = -(h/d_a)(g_f(p) - g_f(p + e_a))
 #pragma unroll
@@ -166,18 +189,18 @@ __device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const
     }
   }
   // faces of this cell and of the upper neighbours needed by the edge cotangents
-  const double gf0 = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, j, k);
-  const double gf1 = face_cot<T, 1>(g, gUpF, gBcc, gBfx, i, j, k);
-  const double gf2 = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, j, k);
+  const double gf0 = face_cot<T, 0>(g, gUpF, gBcc, gBfx, c, p.p[0]);
+  const double gf1 = face_cot<T, 1>(g, gUpF, gBcc, gBfx, c, p.p[1]);
+  const double gf2 = face_cot<T, 2>(g, gUpF, gBcc, gBfx, c, p.p[2]);
   // E_k(q) enters B_{k+1}(q) with -h/d_{k+2}, B_{k+1}(q + e_{k+2}) with +h/d_{k+2},
   // B_{k+2}(q) with +h/d_{k+1}, B_{k+2}(q + e_{k+1}) with -h/d_{k+1}
   // neighbours' face cotangents
-  const double f0_y = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
-  const double f0_z = face_cot<T, 0>(g, gUpF, gBcc, gBfx, i, j, wrapi(k + 1, g.n[2]));
-  const double f1_x = face_cot<T, 1>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
-  const double f1_z = face_cot<T, 1>(g, gUpF, gBcc, gBfx, i, j, wrapi(k + 1, g.n[2]));
-  const double f2_x = face_cot<T, 2>(g, gUpF, gBcc, gBfx, wrapi(i + 1, g.n[0]), j, k);
-  const double f2_y = face_cot<T, 2>(g, gUpF, gBcc, gBfx, i, wrapi(j + 1, g.n[1]), k);
+  const double f0_y = face_cot<T, 0>(g, gUpF, gBcc, gBfx, cp[1], p.p[0]);
+  const double f0_z = face_cot<T, 0>(g, gUpF, gBcc, gBfx, cp[2], p.p[0]);
+  const double f1_x = face_cot<T, 1>(g, gUpF, gBcc, gBfx, cp[0], p.p[1]);
+  const double f1_z = face_cot<T, 1>(g, gUpF, gBcc, gBfx, cp[2], p.p[1]);
+  const double f2_x = face_cot<T, 2>(g, gUpF, gBcc, gBfx, cp[0], p.p[2]);
+  const double f2_y = face_cot<T, 2>(g, gUpF, gBcc, gBfx, cp[1], p.p[2]);
   const T hx = from_d<T>(h * g.id[0]), hy = from_d<T>(h * g.id[1]), hz = from_d<T>(h * g.id[2]);
   // k = 0 (E_x): B_y (a=1) with e_z, B_z (a=2) with e_y
   gE[c] = hy * from_d<T>(gf2 - f2_y) - hz * from_d<T>(gf1 - f1_z);
@@ -201,7 +224,7 @@ __device__ __forceinline__ double adj_update_cell(const Grid& g, double h, const
 #pragma unroll
     for (int f = 0; f < 5; ++f) g5[f] = g5src[f * N + c];
     const double gf[3] = {gf0, gf1, gf2};
-    return update_rate_dot<T>(g, Fs, Es, g5, gf, i, j, k);
+    return update_rate_dot<T>(g, Fs, Es, g5, gf, p);
   }
   return 0.0;
 }
@@ -217,9 +240,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
                                                        T* __restrict__ gF, T* __restrict__ gE,
                                                        const T* __restrict__ Fs, const T* __restrict__ Es,
                                                        double* __restrict__ part) {
-  const CellIdx ci = cell_of_thread(g);
+  const Cell p = thread_cell(g);
   double sens = 0.0;
-  if (ci.ok) sens = adj_update_cell<T, MODE, SENS>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, Fs, Es, ci.i, ci.j, ci.k);
+  if (p.ok) sens = adj_update_cell<T, MODE, SENS>(g, h, g5src, gUpF, gBcc, gBfx, gU, gF, gE, Fs, Es, p);
   if (SENS) block_sum_to(sens, part);
 }
 
@@ -233,19 +256,16 @@ template <class T> __device__ __forceinline__ T upw_lo_t(T m) {
 
 template <class T, int K>
 __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict__ W, const T* __restrict__ F,
-                                             const T* __restrict__ gE, int i, int j, int k, T* __restrict__ gF,
+                                             const T* __restrict__ gE, const Cell& p, T* __restrict__ gF,
                                              T* gW8) {
   constexpr int B = (K + 1) % 3, C = (K + 2) % 3;
   const long long N = g.N;
-  int q[3] = {i, j, k};
+  // cell p + db e_B + dc e_C (|db|, |dc| <= 1; the wraps along B and C are independent)
   auto at = [&](int db, int dc) {
-    int r[3] = {q[0], q[1], q[2]};
-    r[B] = wrapi(r[B] + db, g.n[B]);
-    r[C] = wrapi(r[C] + dc, g.n[C]);
-    return cidx(g, r[0], r[1], r[2]);
+    return p.c + (db < 0 ? p.m[B] : (db > 0 ? p.p[B] : 0)) + (dc < 0 ? p.m[C] : (dc > 0 ? p.p[C] : 0));
   };
-  const long long c00 = at(0, 0), cb = at(-1, 0), cc = at(0, -1), cbc = at(-1, -1);
-  const long long cpb = at(1, 0), cpc = at(0, 1), cmcpb = at(1, -1), cmbpc = at(-1, 1);
+  const int c00 = at(0, 0), cb = at(-1, 0), cc = at(0, -1), cbc = at(-1, -1);
+  const int cpb = at(1, 0), cpc = at(0, 1), cmcpb = at(1, -1), cmbpc = at(-1, 1);
   const T* Fb = F + (long long)B * 7 * N;  // mass flux of b-faces: Fb[x]
   const T* Fc = F + (long long)C * 7 * N;
   const T* gEk = gE + (long long)K * N;
@@ -276,13 +296,14 @@ __device__ __forceinline__ void emf_cot_edge(const Grid& g, const T* __restrict_
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_adj_emf(Grid g, const T* __restrict__ W, const T* __restrict__ F,
                                                     const T* __restrict__ gE, T* __restrict__ gF, T* __restrict__ gW) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const long long N = g.N;
+  const int c = p.c;
   T gw[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-  emf_cot_edge<T, 0>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
-  emf_cot_edge<T, 1>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
-  emf_cot_edge<T, 2>(g, W, F, gE, ci.i, ci.j, ci.k, gF, gw);
+  emf_cot_edge<T, 0>(g, W, F, gE, p, gF, gw);
+  emf_cot_edge<T, 1>(g, W, F, gE, p, gF, gw);
+  emf_cot_edge<T, 2>(g, W, F, gE, p, gF, gw);
 #pragma unroll
   for (int f = 0; f < 8; ++f) gW[f * N + c] = gw[f];
 }
@@ -534,23 +555,23 @@ template <class T, bool HALF>
 __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __restrict__ U, const double* __restrict__ Uh,
                                                      const T* __restrict__ Bh, const T* __restrict__ gW,
                                                      double* __restrict__ g5, T* __restrict__ gBcc) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const long long N = g.N, c = cidx(g, i, j, k);
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const long long N = g.N;
+  const int c = p.c;
   double h5[5], b[3];
   if (HALF) {
 #pragma unroll
     for (int f = 0; f < 5; ++f) h5[f] = Uh[f * N + c];
-    b[0] = 0.5 * (to_d<T>(Bh[nb<0>(g, i, j, k, -1)]) + to_d<T>(Bh[c]));
-    b[1] = 0.5 * (to_d<T>(Bh[N + nb<1>(g, i, j, k, -1)]) + to_d<T>(Bh[N + c]));
-    b[2] = 0.5 * (to_d<T>(Bh[2 * N + nb<2>(g, i, j, k, -1)]) + to_d<T>(Bh[2 * N + c]));
+    b[0] = 0.5 * (to_d<T>(Bh[c + p.m[0]]) + to_d<T>(Bh[c]));
+    b[1] = 0.5 * (to_d<T>(Bh[N + c + p.m[1]]) + to_d<T>(Bh[N + c]));
+    b[2] = 0.5 * (to_d<T>(Bh[2 * N + c + p.m[2]]) + to_d<T>(Bh[2 * N + c]));
   } else {
 #pragma unroll
     for (int f = 0; f < 5; ++f) h5[f] = U[f * N + c];
-    b[0] = 0.5 * (U[5 * N + nb<0>(g, i, j, k, -1)] + U[5 * N + c]);
-    b[1] = 0.5 * (U[6 * N + nb<1>(g, i, j, k, -1)] + U[6 * N + c]);
-    b[2] = 0.5 * (U[7 * N + nb<2>(g, i, j, k, -1)] + U[7 * N + c]);
+    b[0] = 0.5 * (U[5 * N + c + p.m[0]] + U[5 * N + c]);
+    b[1] = 0.5 * (U[6 * N + c + p.m[1]] + U[6 * N + c]);
+    b[2] = 0.5 * (U[7 * N + c + p.m[2]] + U[7 * N + c]);
   }
   if constexpr (std::is_same<T, float>::value) {
     float gw8[8];
@@ -581,15 +602,15 @@ __global__ void __launch_bounds__(BX* BY) k_adj_prim(Grid g, const double* __res
 template <class T>
 __global__ void __launch_bounds__(BX* BY) k_adj_faces_n(Grid g, const double* __restrict__ g5, const T* __restrict__ gBcc,
                                                         const T* __restrict__ gBf, double* __restrict__ gU) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const long long N = g.N, c = cidx(g, i, j, k);
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const long long N = g.N;
+  const int c = p.c;
 #pragma unroll
   for (int f = 0; f < 5; ++f) gU[f * N + c] += g5[f * N + c];
-  gU[5 * N + c] += face_cot<T, 0>(g, nullptr, gBcc, gBf, i, j, k);
-  gU[6 * N + c] += face_cot<T, 1>(g, nullptr, gBcc, gBf, i, j, k);
-  gU[7 * N + c] += face_cot<T, 2>(g, nullptr, gBcc, gBf, i, j, k);
+  gU[5 * N + c] += face_cot<T, 0>(g, nullptr, gBcc, gBf, c, p.p[0]);
+  gU[6 * N + c] += face_cot<T, 1>(g, nullptr, gBcc, gBf, c, p.p[1]);
+  gU[7 * N + c] += face_cot<T, 2>(g, nullptr, gBcc, gBf, c, p.p[2]);
 }
 
 // forward half update that also keeps the hydro half state (for R5)
@@ -597,29 +618,33 @@ template <class T>
 __global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* __restrict__ U0, const T* __restrict__ F,
                                                           const T* __restrict__ E, double dt, T* __restrict__ W,
                                                           T* __restrict__ Bh, double* __restrict__ Uh) {
-  const CellIdx ci = cell_of_thread(g);
-  if (!ci.ok) return;
-  const int i = ci.i, j = ci.j, k = ci.k;
-  const double h = 0.5 * dt;
-  const long long N = g.N, c = cidx(g, i, j, k);
+  const Cell p = thread_cell(g);
+  if (!p.ok) return;
+  const long long N = g.N;
+  const int c = p.c;
+  const Fields<const double, 8> Uf = fields_of<8>(U0, N);
+  const Fields<const T, 21> Ff = fields_of<21>(F, N);
+  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  const StepScalars S = step_scalars_of(g, dt);
+  const double h = S.h_half;
   constexpr bool X = sizeof(T) == 8 && Exact<T>::full;  // the arithmetic of k_update_half
   double u5[5];
-  hydro_update<T, X>(g, U0, F, h, i, j, k, u5);
-  const double bx = face_update<T, X, 0>(g, U0, E, h, i, j, k);
-  const double by = face_update<T, X, 1>(g, U0, E, h, i, j, k);
-  const double bz = face_update<T, X, 2>(g, U0, E, h, i, j, k);
-  const double bxm = face_update<T, X, 0>(g, U0, E, h, wrapi(i - 1, g.n[0]), j, k);
-  const double bym = face_update<T, X, 1>(g, U0, E, h, i, wrapi(j - 1, g.n[1]), k);
-  const double bzm = face_update<T, X, 2>(g, U0, E, h, i, j, wrapi(k - 1, g.n[2]));
+  hydro_update<T, X, true, true>(Uf, Ff, S, p, u5);
+  const double bx = face_update<T, X, true, 0>(g, Uf, Ef, h, c, p.m[1], p.m[2]);
+  const double by = face_update<T, X, true, 1>(g, Uf, Ef, h, c, p.m[2], p.m[0]);
+  const double bz = face_update<T, X, true, 2>(g, Uf, Ef, h, c, p.m[0], p.m[1]);
+  const double bxm = face_update<T, X, true, 0>(g, Uf, Ef, h, c + p.m[0], p.m[1], p.m[2]);
+  const double bym = face_update<T, X, true, 1>(g, Uf, Ef, h, c + p.m[1], p.m[2], p.m[0]);
+  const double bzm = face_update<T, X, true, 2>(g, Uf, Ef, h, c + p.m[2], p.m[0], p.m[1]);
   Bh[c] = from_d<T>(bx);
   Bh[N + c] = from_d<T>(by);
   Bh[2 * N + c] = from_d<T>(bz);
 #pragma unroll
   for (int f = 0; f < 5; ++f) Uh[f * N + c] = u5[f];
   const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
-  const PrimD p = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
+  const PrimD pw = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
   T w8[8];
-  store_w<T>(g, W, c, p, w8);
+  store_w<T>(fields_of<8>(W, N), c, pw, w8);
 }
 
 // ------------------------------------- the CFL dt as a function of U^n --

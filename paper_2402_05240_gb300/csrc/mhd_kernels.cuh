@@ -180,12 +180,6 @@ template <class T, int A> __device__ __forceinline__ T cell_ref(const T* w8) {
   constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
   return -(w8[1 + B] * w8[5 + C] - w8[1 + C] * w8[5 + B]);
 }
-template <class T> __device__ __forceinline__ void store_ref(T* __restrict__ Er, long long N, long long c, const T* w8) {
-  if (!Er) return;
-  Er[c] = cell_ref<T, 0>(w8);
-  Er[N + c] = cell_ref<T, 1>(w8);
-  Er[2 * N + c] = cell_ref<T, 2>(w8);
-}
 template <class T> __device__ __forceinline__ void store_ref(const Fields<T, 3>& Er, int c, const T* w8) {
   if (!Er.f[0]) return;
   Er.f[0][c] = cell_ref<T, 0>(w8);
@@ -204,12 +198,6 @@ template <class T> __device__ __forceinline__ void prim_to_w8(const PrimD& p, T*
   w8[7] = from_d<T>(p.b[2]);
 }
 
-template <class T>
-__device__ __forceinline__ void store_w(const Grid& g, T* __restrict__ W, long long c, const PrimD& p, T* w8) {
-  prim_to_w8<T>(p, w8);
-#pragma unroll
-  for (int f = 0; f < 8; ++f) W[f * g.N + c] = w8[f];
-}
 template <class T> __device__ __forceinline__ void store_w(const Fields<T, 8>& W, int c, const PrimD& p, T* w8) {
   prim_to_w8<T>(p, w8);
 #pragma unroll
@@ -616,92 +604,17 @@ __global__ void __launch_bounds__(BX* BY) k_emf_r(Grid g, const T* __restrict__ 
 }
 
 // ------------------------------------------------------------ Steps 5, 9 --
-// curl term of face A of cell (i,j,k): (E_C(p) - E_C(p-e_B))/d_B - (E_B(p) - E_B(p-e_C))/d_C.
-// EXACT: the edge values are widened to double before differencing, so the
-// discrete divergence of the update telescopes to double round-off whatever
-// the compute type (the FP32-bulk full update keeps div B at FP64 round-off).
-template <class T, bool EXACT, int A>
-__device__ __forceinline__ double face_curl(const Grid& g, const T* __restrict__ E, int i, int j, int k) {
-  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
-  const long long N = g.N, c = cidx(g, i, j, k);
-  const T* EB = E + (long long)B * N;
-  const T* EC = E + (long long)C * N;
-  if constexpr (EXACT && std::is_same<T, float>::value) {
-    // float edge values: each difference is exact as a float pair (TwoSum)
-    const df dc = two_sum(EC[c], -EC[nb<B>(g, i, j, k, -1)]);
-    const df db = two_sum(EB[c], -EB[nb<C>(g, i, j, k, -1)]);
-    return (double)(dc * df(g.id[B]) - db * df(g.id[C]));
-  } else if (EXACT) {
-    return (to_d<T>(EC[c]) - to_d<T>(EC[nb<B>(g, i, j, k, -1)])) * g.id[B] -
-           (to_d<T>(EB[c]) - to_d<T>(EB[nb<C>(g, i, j, k, -1)])) * g.id[C];
-  }
-  return to_d<T>((EC[c] - EC[nb<B>(g, i, j, k, -1)]) * from_d<T>(g.id[B]) -
-                 (EB[c] - EB[nb<C>(g, i, j, k, -1)]) * from_d<T>(g.id[C]));
-}
-
 // solver-frame component of the global field f (0 rho, 1-3 m, 4 E) in the flux of axis a
 __device__ __forceinline__ int comp_of(int f, int a) {
   return (f == 0 || f == 4) ? f : 1 + ((f - 1 - a + 3) % 3);
 }
 
-// new hydro state of one cell: U0 - h sum_a (F_a(p) - F_a(p - e_a)) / d_a.
-// EXACT: every flux difference is exact -- in double for double fluxes, as a
-// float pair (TwoSum, FP32 pipes) for float fluxes -- and the increment is
-// accumulated in double or float pairs, so sums over the periodic box
-// telescope to round-off: the FP32-bulk full update conserves rho, m, E at
-// the FP64 level.  Otherwise (FP32-bulk half step) the increment is formed in
-// T and added to the double state.
-template <class T, bool EXACT>
-__device__ __forceinline__ void hydro_update(const Grid& g, const double* __restrict__ U0, const T* __restrict__ F,
-                                             double h, int i, int j, int k, double* out5) {
-  const long long N = g.N, c = cidx(g, i, j, k);
-  const long long cm[3] = {nb<0>(g, i, j, k, -1), nb<1>(g, i, j, k, -1), nb<2>(g, i, j, k, -1)};
-  const double hd[3] = {h * g.id[0], h * g.id[1], h * g.id[2]};
-  df hdf[3];
-  if constexpr (EXACT && std::is_same<T, float>::value) {
-    for (int a = 0; a < 3; ++a) hdf[a] = df(hd[a]);
-  }
-#pragma unroll
-  for (int f = 0; f < 5; ++f) {
-    if constexpr (EXACT && std::is_same<T, float>::value) {
-      df inc(0.0f, 0.0f);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        inc += hdf[a] * two_sum(Fa[c], -Fa[cm[a]]);
-      }
-      out5[f] = U0[f * N + c] - (double)inc;
-    } else if (EXACT) {
-      double acc = U0[f * N + c];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        acc -= hd[a] * (to_d<T>(Fa[c]) - to_d<T>(Fa[cm[a]]));
-      }
-      out5[f] = acc;
-    } else {
-      T inc = T(0);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T* Fa = F + ((long long)a * 7 + comp_of(f, a)) * N;
-        inc -= from_d<T>(hd[a]) * (Fa[c] - Fa[cm[a]]);
-      }
-      out5[f] = U0[f * N + c] + to_d<T>(inc);
-    }
-  }
-}
-
-// new face B_A of cell (ii, jj, kk) (upper face): B0 - h curl
-template <class T, bool EXACT, int A>
-__device__ __forceinline__ double face_update(const Grid& g, const double* __restrict__ U0, const T* __restrict__ E,
-                                              double h, int ii, int jj, int kk) {
-  const double cu = face_curl<T, EXACT, A>(g, E, ii, jj, kk);
-  return U0[(5 + A) * g.N + cidx(g, ii, jj, kk)] - h * cu;
-}
-
-// The same three operations on the 32-bit addressing of the step kernels.
-// q: the cell whose upper face A is updated; oB, oC: the offsets from q to
-// q - e_B and q - e_C.  NC: U0 is read-only in the kernel (non-coherent loads).
+// curl term of face A of cell q: (E_C(q) - E_C(q - e_B))/d_B - (E_B(q) -
+// E_B(q - e_C))/d_C; oB, oC: the offsets from q to q - e_B and q - e_C.
+// EXACT: each edge difference is exact (float edges: as a float pair by
+// TwoSum; double edges: widened before differencing), so the discrete
+// divergence of the update telescopes to double round-off whatever the
+// compute type (the FP32-bulk full update keeps div B at FP64 round-off).
 template <class T, bool EXACT, int A>
 __device__ __forceinline__ double face_curl(const Grid& g, const Fields<const T, 3>& E, int q, int oB, int oC) {
   constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
@@ -736,6 +649,15 @@ template <class T, bool HALF> __device__ __forceinline__ T step_factor(const Ste
   }
 }
 
+// new hydro state of one cell: U0 - h sum_a (F_a(p) - F_a(p - e_a)) / d_a,
+// with h / d_a from the step scalars (HALF: h = dt / 2).  EXACT: every flux
+// difference is exact -- in double for double fluxes, as a float pair
+// (TwoSum, FP32 pipes) for float fluxes -- and the increment is accumulated
+// in double or float pairs, so sums over the periodic box telescope to
+// round-off: the FP32-bulk full update conserves rho, m, E at the FP64 level.
+// Otherwise (FP32-bulk and double-float half step) the increment is formed
+// in T and added to the double state.  NC: U0 is read-only in the kernel
+// (non-coherent loads).
 template <class T, bool EXACT, bool NC, bool HALF>
 __device__ __forceinline__ void hydro_update(const Fields<const double, 8>& U0, const Fields<const T, 21>& F,
                                              const StepScalars& S, const Cell& p, double* out5) {
@@ -772,6 +694,7 @@ __device__ __forceinline__ void hydro_update(const Fields<const double, 8>& U0, 
   }
 }
 
+// new upper face B_A of cell q: B0 - h curl
 template <class T, bool EXACT, bool NC, int A>
 __device__ __forceinline__ double face_update(const Grid& g, const Fields<const double, 8>& U0,
                                               const Fields<const T, 3>& E, double h, int q, int oB, int oC) {
@@ -862,8 +785,6 @@ template <class T> __global__ void k_narrow(const double* __restrict__ src, T* _
     dst[q] = (T)src[q];
 }
 
-#ifdef MHD_SCALAR_KERNELS
-// --------------------------------------------------------- small kernels --
 // the step scalars of step size dt (the factors formed exactly as the
 // update kernels would form them: (dt / 2) / d_a = (0.5 dt) id_a)
 __device__ __forceinline__ void set_step_scalars(const Grid& g, StepScalars* S, double dt) {
@@ -882,6 +803,8 @@ __device__ __forceinline__ void set_step_scalars(const Grid& g, StepScalars* S, 
   }
 }
 
+#ifdef MHD_SCALAR_KERNELS
+// --------------------------------------------------------- small kernels --
 __global__ void k_set_dt(Grid g, double* dt_cur, double value) {
   set_step_scalars(g, reinterpret_cast<StepScalars*>(dt_cur), value);
 }
