@@ -246,6 +246,16 @@ __global__ void __launch_bounds__(BX* BY) k_adj_update(Grid g, double h, const d
   if (SENS) block_sum_to(sens, part);
 }
 
+// Blocks per SM requested from the register allocator for the float-pair
+// reverse HLLD and PPMC kernels (3: at most 168 registers; the reverse HLLD
+// then spills about 1 KB per thread).  Measured, adjoint step of the 256^3
+// turbulent box: 207.5 ms against 220.7 ms without the bound and 238.3 ms
+// at 4 blocks; the float kernels are fastest without it (33.7 ms against
+// 36.6 ms at 3 and 35.9 ms at 4 blocks).  0: no bound (the allocation of a
+// plain __launch_bounds__(128)).
+template <class T> struct AdjMinBlocks { static constexpr int v = 0; };
+template <> struct AdjMinBlocks<df> { static constexpr int v = 3; };
+
 // ---------------------------------------------------- R3 / R8: edge EMF --
 // Gather-form reverse of Eq. emf-edge: writes gF[a][5], gF[a][6] and the
 // reference-field part of gW (v and B_cc components; rho, P zeroed).  The
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_emf(Grid g, const T* __restrict_
 // Writes gWL(p) (left state of face p), gWR(p + e_A) (right state of the
 // face, owned by cell p + e_A) and gBf_A(p).
 template <class T, int A, bool PCM>
-__global__ void __launch_bounds__(BX* BY) k_adj_hlld(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
+__global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_hlld(Grid g, const T* __restrict__ WL, const T* __restrict__ WR,
                                                      const T* __restrict__ Wn, const double* __restrict__ U,
                                                      const T* __restrict__ Bh, const T* __restrict__ gF,
                                                      T* __restrict__ gWL, T* __restrict__ gWR, T* __restrict__ gBf) {
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_recon(Grid g, const T* __restric
 // stencil cells' cotangents (each cell's slots are read and written by its
 // own thread only).  S has the slot layout of k_adj_recon.
 template <class T, int A>
-__global__ void __launch_bounds__(BX* BY) k_adj_ppmc1(Grid g, const T* __restrict__ W, const T* __restrict__ gWL,
+__global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_ppmc1(Grid g, const T* __restrict__ W, const T* __restrict__ gWL,
                                                       const T* __restrict__ gWR, Fields<T, kPpmcRevFields> X) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_ppmc1(Grid g, const T* __restric
 }
 
 template <class T, int A>
-__global__ void __launch_bounds__(BX* BY) k_adj_ppmc2(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
+__global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_ppmc2(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
                                                       T* __restrict__ S) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
@@ -498,7 +508,7 @@ __global__ void __launch_bounds__(BX* BY) k_adj_ppmc2(Grid g, const T* __restric
 }
 
 template <class T, int A>
-__global__ void __launch_bounds__(BX* BY) k_adj_ppmc3(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
+__global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_ppmc3(Grid g, const T* __restrict__ W, Fields<T, kPpmcRevFields> X,
                                                       T* __restrict__ S) {
   const CellIdx ci = cell_of_thread(g);
   if (!ci.ok) return;
