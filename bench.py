@@ -107,6 +107,12 @@ _STAGES = {
         "update_full": (16.0, 19.0, 1145.0 / 32, 268.1),
     },
 }
+# FP64-pipe busy fraction of the FP64 kernels from the same captures
+# (sm__pipe_fp64_cycles_active, % of peak sustained active): the pipe's
+# occupancy by every FP64 instruction issued -- arithmetic, compares, and the
+# lanes a divergent branch leaves idle -- beside the algorithmic count above
+FP64_PIPE_BUSY = {"prim": 0.858, "flux_pcm": 0.892, "emf": 0.838, "update_half": 0.870, "recon": 0.852,
+                  "flux_hlld": 0.892, "update_full": 0.879}
 _RECON_PPMC = {
     "fp64": (420.2, 529.6, 3675.0 / 32, 169.6),
     "fp32_bulk": (0.0, 0.0, 1260.9 / 32, 80.9),
@@ -312,6 +318,8 @@ def roofline_of(prof, precision, n3, hbm_peak, peak_kind, recon="plmc"):
                  "frac": round(gw / ISSUE_PEAK_GWARPINST, 4),
                  "peak_source": "nominal (4 issue slots per clock per SM, 152 SMs, 2.07 GHz)"}
         main = fp64 if fp64["frac"] >= issue["frac"] else issue
+        if precision == "fp64" and name in FP64_PIPE_BUSY:
+            fp64["busy_ncu"] = FP64_PIPE_BUSY[name]
         out.update({"bound": "alu", **main, "fp64_pipe": fp64, "issue": issue,
                     "traffic": round(cnt[3] * n3),
                     "traffic_note": "ncu DRAM bytes per cell at 192^3 scaled to this launch's cells"})
