@@ -538,6 +538,47 @@ __global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_ppmc3(Grid g
   S[5LL * 7 * N + c] = gbn;
 }
 
+// Passes 2 and 3 in one kernel, the deviation cotangents kept in registers
+// (for the float reverse, whose live state fits without spilling).
+template <class T, int A>
+__global__ void __launch_bounds__(BX* BY, AdjMinBlocks<T>::v) k_adj_ppmc23(Grid g, const T* __restrict__ W,
+                                                                          Fields<T, kPpmcRevFields> X,
+                                                                          T* __restrict__ S) {
+  const CellIdx ci = cell_of_thread(g);
+  if (!ci.ok) return;
+  const long long N = g.N, c = cidx(g, ci.i, ci.j, ci.k);
+  T gdm[7], gdp[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    gdm[q] = X.f[q][c];
+    gdp[q] = X.f[7 + q][c];
+  }
+  const T bn = W[(5 + A) * N + c];
+  auto wload = [&](int m, T* out) { load_dir<A>(W, N, nb<A>(g, ci.i, ci.j, ci.k, m - 2), out); };
+  T gq[4][7];
+  ppmc_vjp_pass2<T>(from_d<T>(g.gamma), wload, bn, gdm, gdp, gq);
+  T gw2[7], ge[17];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) gw2[q] = X.f[31 + q][c];
+#pragma unroll
+  for (int q = 0; q < 17; ++q) ge[q] = X.f[14 + q][c];
+  EigG<T> gE;
+  eigg_unpack<T>(ge, gE);
+  auto gqload = [&](int k, T* out) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) out[q] = gq[k][q];
+  };
+  auto put = [&](int m, const T* gm) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) S[((long long)m * 7 + q) * N + c] = gm[q];
+  };
+  T gbn = T(0);
+  ppmc_vjp_pass3<T>(from_d<T>(g.gamma), wload, bn, gqload, gE, gw2, put, gbn);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) S[(2LL * 7 + q) * N + c] = gw2[q];
+  S[5LL * 7 * N + c] = gbn;
+}
+
 // cell p gathers slot m from cell p - (m - h) along A, h = NS/2
 template <class T, int RECON, int A>
 __global__ void __launch_bounds__(BX* BY) k_adj_recon_gather(Grid g, const T* __restrict__ S, T* __restrict__ gW) {
@@ -866,8 +907,12 @@ static void launch_ppmc_rev(const Grid& g, const T* W, const T* gWL, const T* gW
                             const Fields<T, kPpmcRevFields>& X, cudaStream_t s) {
   const dim3 gr = grid_of(g), bl(BX, BY);
   k_adj_ppmc1<T, A><<<gr, bl, 0, s>>>(g, W, gWL, gWR, X);
-  k_adj_ppmc2<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
-  k_adj_ppmc3<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+  if constexpr (std::is_same<T, float>::value) {
+    k_adj_ppmc23<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+  } else {
+    k_adj_ppmc2<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+    k_adj_ppmc3<T, A><<<gr, bl, 0, s>>>(g, W, X, S);
+  }
   k_adj_recon_gather<T, 2, A><<<gr, bl, 0, s>>>(g, S, gW);
 }
 template <class T>
