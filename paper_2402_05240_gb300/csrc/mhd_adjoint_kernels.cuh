@@ -29,13 +29,8 @@ template <class T> struct AdjBufs {
 
 // The reverse kernels address cells like the step kernels: 32-bit cell
 // indices with the periodic neighbour offsets of thread_cell, and field
-// pointers formed once per thread from the restrict-qualified base pointers.
-template <int K, class T> __device__ __forceinline__ Fields<T, K> fields_of(T* base, long long N) {
-  Fields<T, K> r;
-#pragma unroll
-  for (int q = 0; q < K; ++q) r.f[q] = base + q * N;
-  return r;
-}
+// pointers (fields()) formed once per thread from the restrict-qualified
+// base pointers.
 // the step scalars of a step of size dt (as the dt kernels form them)
 __device__ __forceinline__ StepScalars step_scalars_of(const Grid& g, double dt) {
   StepScalars S;
@@ -55,9 +50,9 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   if (!p.ok) return;
   const long long N = g.N;
   const int c = p.c;
-  const Fields<const double, 8> Uf = fields_of<8>(U, N);
-  const Fields<const T, 21> Ff = fields_of<21>(F, N);
-  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  const Fields<const double, 8> Uf = fields<8>(U, N);
+  const Fields<const T, 21> Ff = fields<21>(F, N);
+  const Fields<const T, 3> Ef = fields<3>(E, N);
   const StepScalars S = step_scalars_of(g, dt);
   double u5[5];
   constexpr bool X = Exact<T>::full;  // the arithmetic of k_update_full
@@ -159,7 +154,7 @@ __device__ __forceinline__ double update_rate_dot(const Grid& g, const T* __rest
     }
     s += g5[f] * d;
   }
-  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  const Fields<const T, 3> Ef = fields<3>(E, N);
   s += gf[0] * face_curl<T, true, 0>(g, Ef, c, p.m[1], p.m[2]);
   s += gf[1] * face_curl<T, true, 1>(g, Ef, c, p.m[2], p.m[0]);
   s += gf[2] * face_curl<T, true, 2>(g, Ef, c, p.m[0], p.m[1]);
@@ -673,9 +668,9 @@ __global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* 
   if (!p.ok) return;
   const long long N = g.N;
   const int c = p.c;
-  const Fields<const double, 8> Uf = fields_of<8>(U0, N);
-  const Fields<const T, 21> Ff = fields_of<21>(F, N);
-  const Fields<const T, 3> Ef = fields_of<3>(E, N);
+  const Fields<const double, 8> Uf = fields<8>(U0, N);
+  const Fields<const T, 21> Ff = fields<21>(F, N);
+  const Fields<const T, 3> Ef = fields<3>(E, N);
   const StepScalars S = step_scalars_of(g, dt);
   const double h = S.h_half;
   constexpr bool X = sizeof(T) == 8 && Exact<T>::full;  // the arithmetic of k_update_half
@@ -695,7 +690,7 @@ __global__ void __launch_bounds__(BX* BY) k_fwd_half_keep(Grid g, const double* 
   const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
   const PrimD pw = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
   T w8[8];
-  store_w<T>(fields_of<8>(W, N), c, pw, w8);
+  store_w<T>(fields<8>(W, N), c, pw, w8);
 }
 
 // ------------------------------------- the CFL dt as a function of U^n --

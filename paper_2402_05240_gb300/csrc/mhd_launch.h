@@ -34,9 +34,11 @@ template <class T, int K> struct Fields {
   T* f[K];
 };
 
-// the K field pointers of a field-major array with N cells per field
-template <int K, class T> inline Fields<T, K> fields(T* base, long long N) {
+// the K field pointers of a field-major array with N cells per field (all
+// null for a null base)
+template <int K, class T> __host__ __device__ inline Fields<T, K> fields(T* base, long long N) {
   Fields<T, K> r;
+#pragma unroll
   for (int q = 0; q < K; ++q) r.f[q] = base ? base + q * N : nullptr;
   return r;
 }
