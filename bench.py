@@ -530,7 +530,7 @@ def main():
         # page-locked, huge-page backed host memory from the library
         # (mhd_host_alloc): the copies stay at the link rate between steps
         host = mhd.host_buffer(8, n, n, n)
-        host.copy_(U0.cpu())
+        host.copy_(U0)  # device -> host, no pageable temporary
         mhd.mhd_run_host(sim.ctx, host, 1)  # warm the host-state buffer
         mhd.mhd_profile_enable(sim.ctx, True)
         t0 = time.perf_counter()
