@@ -72,19 +72,21 @@ __global__ void __launch_bounds__(BX* BY) k_adj_floors(Grid g, const double* __r
   const double r = rfl ? g.rho_floor : u5[0];
   const double ir = __drcp_rn(r);
   // kinetic + magnetic energy and the pressure-floor test with the forward's
-  // arithmetic (k_prim; its FP32-bulk form in prim_store_f32)
+  // arithmetic (k_prim; its FP32-bulk form in p_recover_f32)
   double ke, me;
+  bool pfl;
   if constexpr (std::is_same<T, float>::value) {
     ke = 0.5 * ((u5[1] * u5[1] + u5[2] * u5[2] + u5[3] * u5[3]) * ir);
     me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const double bs[3] = {bxm + bx, bym + by, bzm + bz};
+    double t2, pe;
+    p_recover_f32(ir, u5[1], u5[2], u5[3], u5[4], bs, t2, pe);
+    pfl = lt_pos<double>(g.gm1 * pe, g.p_floor);
   } else {
     ke = 0.5 * (u5[1] * (u5[1] * ir) + u5[2] * (u5[2] * ir) + u5[3] * (u5[3] * ir));
     me = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    pfl = g.gm1 * (u5[4] - ke - me) < g.p_floor;
   }
-  const bool pfl = std::is_same<T, float>::value
-                       ? g.gm1 * (u5[4] - 0.5 * ((u5[1] * u5[1] + u5[2] * u5[2] + u5[3] * u5[3]) * ir +
-                                                 (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]))) < g.p_floor
-                       : g.gm1 * (u5[4] - ke - me) < g.p_floor;
   if (pfl) {  // E = p_floor/(gamma-1) + |m|^2/(2 r) + |B_cc|^2/2
     const double gE = g5[4];
     g5[4] = 0.0;

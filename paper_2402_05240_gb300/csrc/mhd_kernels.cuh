@@ -204,18 +204,47 @@ template <class T> __device__ __forceinline__ void store_w(const Fields<T, 8>& W
   for (int f = 0; f < 8; ++f) W.f[f][c] = w8[f];
 }
 
+// x / 4 for x >= 0, exact: on the exponent bits where x is a normal double of
+// exponent field >= 3 (a subtraction on the integer pipes), else (zero, tiny,
+// infinite or NaN x) a multiplication, taken only in warps where a lane
+// needs it
+__device__ __forceinline__ double quarter_nonneg(double x) {
+  const long long b = dbits(x);
+  const bool fast = b >= (3LL << 52) && b < 0x7ff0000000000000LL;
+  double r = __longlong_as_double(b - (2LL << 52));
+  if (__any_sync(__activemask(), !fast)) {
+    if (!fast) r = 0.25 * x;
+  }
+  return r;
+}
+
+// FP32-bulk gas-pressure recovery in double: t2 = |m|^2 / rho' + |B_cc|^2
+// (twice the kinetic plus magnetic energy) and pe = E - t2 / 2, so that
+// P = (gamma - 1) pe.  bsum = twice the cell-centred field (the sum of the
+// two face values).  Written with explicit multiply-adds, so the forward
+// step and its reverse (which repeats the floor decision) evaluate it alike;
+// E - t2/2 is one fused operation (t2/2 is exact).
+__device__ __forceinline__ void p_recover_f32(double ir, double m0, double m1, double m2, double e, const double* bsum,
+                                              double& t2, double& pe) {
+  const double mm = fma(m0, m0, fma(m1, m1, m2 * m2));
+  const double bb = fma(bsum[0], bsum[0], fma(bsum[1], bsum[1], bsum[2] * bsum[2]));
+  t2 = fma(mm, ir, quarter_nonneg(bb));
+  pe = fma(-0.5, t2, e);
+}
+
 // FP32-bulk primitives of one cell: the gas-pressure recovery
-// P = max((gamma - 1)(E - |m|^2 / (2 rho') - |B_cc|^2 / 2), P_floor) in double,
-// the outputs that are stored as float (v = m / rho', B_cc) formed on the FP32
-// pipes from the rounded inputs.  bsum = twice the cell-centred field (sum of
-// the two face values).  Returns ke + me in double for the floor reset.
-__device__ __forceinline__ double prim_store_f32(const Grid& g, const Fields<float, 8>& W, int c, double rho,
-                                                 double ir, double m0, double m1, double m2, double e,
-                                                 const double* bsum, float* w8) {
-  const double mm = m0 * m0 + m1 * m1 + m2 * m2;
-  const double bb = bsum[0] * bsum[0] + bsum[1] * bsum[1] + bsum[2] * bsum[2];
-  const double kem = 0.5 * (mm * ir + 0.25 * bb);  // ke + me
-  const double p = max_pos<double>(g.gm1 * (e - kem), g.p_floor);
+// P = max((gamma - 1)(E - |m|^2 / (2 rho') - |B_cc|^2 / 2), P_floor) in double
+// (p_recover_f32), the outputs that are stored as float (v = m / rho', B_cc)
+// formed on the FP32 pipes from the rounded inputs.  Returns t2 (twice
+// ke + me, for the floor reset) and pg = (gamma - 1)(E - ke - me) before the
+// floor.
+__device__ __forceinline__ void prim_store_f32(const Grid& g, const Fields<float, 8>& W, int c, double rho, double ir,
+                                               double m0, double m1, double m2, double e, const double* bsum,
+                                               float* w8, double& t2, double& pg) {
+  double pe;
+  p_recover_f32(ir, m0, m1, m2, e, bsum, t2, pe);
+  pg = g.gm1 * pe;
+  const double p = max_pos<double>(pg, g.p_floor);
   const float irf = d2f_bits(ir);
   w8[0] = d2f_bits(rho);
   w8[1] = d2f_bits(m0) * irf;
@@ -227,7 +256,6 @@ __device__ __forceinline__ double prim_store_f32(const Grid& g, const Fields<flo
   w8[7] = 0.5f * d2f_bits(bsum[2]);
 #pragma unroll
   for (int f = 0; f < 8; ++f) W.f[f][c] = w8[f];
-  return kem;
 }
 
 // ------------------------------------------------------------------ Step 1 --
@@ -267,10 +295,11 @@ __global__ void __launch_bounds__(BX* BY) k_prim(Grid g, Fields<double, 8> U, Fi
     T w8[8];
     if constexpr (std::is_same<T, float>::value) {
       const double bs[3] = {b0m + b0p, b1m + b1p, b2m + b2p};
-      const double kem = prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8);
+      double t2, pg;
+      prim_store_f32(g, W, c, rho, ir, m0, m1, m2, e, bs, w8, t2, pg);
       store_ref<T>(Er, c, w8);
-      if (floors && lt_pos<double>(g.gm1 * (e - kem), g.p_floor)) {
-        U.f[4][c] = g.p_floor * g.igm1 + kem;
+      if (floors && lt_pos<double>(pg, g.p_floor)) {
+        U.f[4][c] = g.p_floor * g.igm1 + 0.5 * t2;
         if (in) atomicAdd(&floors[1], 1ull);
       }
       if (dtbits && in) inv = cell_inv_crossing<T>(g, w8);
@@ -741,7 +770,8 @@ __global__ void __launch_bounds__(BX* BY) k_update_half(Grid g, Fields<const dou
   if constexpr (std::is_same<T, float>::value) {
     const double bs[3] = {bxm + bx, bym + by, bzm + bz};
     const double rho = max_pos<double>(u5[0], g.rho_floor);
-    prim_store_f32(g, W, c, rho, __drcp_rn(rho), u5[1], u5[2], u5[3], u5[4], bs, w8);
+    double t2, pg;
+    prim_store_f32(g, W, c, rho, __drcp_rn(rho), u5[1], u5[2], u5[3], u5[4], bs, w8, t2, pg);
   } else {
     const double bcc[3] = {0.5 * (bxm + bx), 0.5 * (bym + by), 0.5 * (bzm + bz)};
     const PrimD pw = prim_core(g, u5[0], u5[1], u5[2], u5[3], u5[4], bcc);
