@@ -184,9 +184,11 @@ int mhd_run_host(mhd_ctx* ctx, double* U_host, int nsteps, double* t_host);
 
 /* Library infrastructure, not in the paper.  Allocates bytes of
  * page-locked host memory for mhd_run_host (or any host<->device copy):
- * aligned to and rounded up to a multiple of the transparent huge page size
- * (2 MiB or 512 MiB, from the kernel; 2 MiB if it does not say), advised as
- * huge pages, then registered with cudaHostRegister on the current device.
+ * from a quarter of the transparent huge page size up (2 MiB or 512 MiB,
+ * from the kernel; 2 MiB if it does not say), aligned to and rounded up to a
+ * multiple of that size and advised as huge pages; smaller requests page
+ * aligned.  The memory is then registered with cudaHostRegister on the
+ * current device.
  * On hosts whose DMA reaches host memory through an IOMMU (the Grace host of
  * a GB300), copies from ordinary page-locked memory slow down to a fraction
  * of the link rate after GPU work has run in between (translation misses
