@@ -91,10 +91,10 @@ _STAGES = {
         "update_full": (45.0, 66.0, 352.0 / 32, 268.3),
     },
     "fp32_bulk": {
-        "prim": (19.0, 29.0, 707.0 / 32, 102.5),
+        "prim": (18.0, 29.0, 719.0 / 32, 102.5),
         "flux_pcm": (0.0, 0.0, 493.3 / 32, 58.8),
         "emf": (0.0, 0.0, 224.0 / 32, 58.0),
-        "update_half": (29.0, 46.0, 1094.0 / 32, 188.5),
+        "update_half": (29.0, 46.0, 1103.0 / 32, 188.5),
         "flux_hlld": (0.0, 0.0, 524.2 / 32, 84.3),
         "update_full": (16.0, 19.0, 1040.8 / 32, 194.4),
     },
