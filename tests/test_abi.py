@@ -77,6 +77,9 @@ def test_config_validation_without_gpu():
         mhd.mhd_config(65536, 32769, 4, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # nx ny above 2^31
         mhd.mhd_config(4, 4, 65530, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20,
                        (ctypes.c_int * 3)(0, 0, 1)),  # padded nz above the z limit
+        mhd.mhd_config(2048, 2048, 512, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20),  # 2^31 cells: 32-bit indices
+        mhd.mhd_config(2048, 2032, 512, 1, 1, 1, 5 / 3, 0.4, 1, 0, 1e-20, 1e-20,
+                       (ctypes.c_int * 3)(0, 1, 0)),  # 2^31 cells with the ghost cells of an outflow axis
     ]
     for cfg in bad:
         with pytest.raises(mhd.MHDError) as e:
@@ -87,6 +90,23 @@ def test_config_validation_without_gpu():
                          (ctypes.c_int * 3)(1, 0, 0))
     ratio = mhd.mhd_workspace_bytes(out) / mhd.mhd_workspace_bytes(ok)
     assert 48 / 32 < ratio < 48 / 32 * (1 + 8 * 8 / (49 * 8)) + 0.01
+    # the largest grid the 32-bit cell indices allow is accepted
+    big = mhd.mhd_config(2048, 2048, 511, 1, 1, 1, 5 / 3, 0.4, 1, 1, 1e-20, 1e-20)
+    assert mhd.mhd_workspace_bytes(big) > 2048 * 2048 * 511 * 64
+
+
+def test_host_alloc_argument_errors_without_gpu(lib):
+    """mhd_host_alloc refuses a zero size and a NULL output before any CUDA
+    call; mhd_host_free(NULL) is a no-op."""
+    vp = ctypes.c_void_p
+    lib.mhd_host_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.mhd_host_alloc.restype = ctypes.c_int
+    lib.mhd_host_free.argtypes = [vp]
+    lib.mhd_host_free.restype = ctypes.c_int
+    p = vp()
+    assert lib.mhd_host_alloc(0, ctypes.byref(p)) == -1 and p.value is None
+    assert lib.mhd_host_alloc(64, None) == -1
+    assert lib.mhd_host_free(None) == 0
 
 
 def test_null_arguments_rejected(lib):
