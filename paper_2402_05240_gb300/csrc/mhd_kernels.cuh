@@ -11,8 +11,9 @@
 //   k_emf           Step 8: edge fields with the half-step reference fields
 //   k_update_full   Step 9: U^{n+1}, B^{n+1} in place
 //   k_prim (floors) end of step: floors, W^{n+1} and the dt of the next step
-// Periodic boundaries are wrap-around indices inside every kernel; no ghost
-// cells exist.  Threads map to cells with x fastest (coalesced rows).
+// Periodic boundaries are wrapped neighbour offsets inside every kernel (each
+// thread forms its six once: thread_cell); no ghost cells exist.  Threads map
+// to cells with x fastest (coalesced rows), with 32-bit cell indices.
 #pragma once
 
 #include <type_traits>
